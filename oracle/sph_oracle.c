@@ -561,16 +561,17 @@ int oracle_pack(int loop, const oracle_fields *f, const int64_t *perm,
 }
 
 /* Unpack (Sec. 2.3): for every particle touched by tasks [t0, t1), fold its */
-/* slots in increasing task order (ci before cj) into its fields.  Sums are  */
-/* accumulated in FP64 starting from the stored value and rounded to f32     */
-/* once; the signal velocities take the max (fmaxf).                         */
+/* slots in increasing task order (ci before cj) into its fields.  Sums use  */
+/* Kahan's compensated summation in FP32, starting from the stored value     */
+/* with zero compensation (y = x - c; t = s + y; c = (t - s) - y; s = t);     */
+/* the signal velocities take the max (fmaxf).                               */
 typedef struct {
     int lane;      /* output lane */
     int col;       /* float index inside the lane element */
     float *field;  /* destination logical field */
     int ncomp;     /* components per particle of that field */
     int comp;      /* component written */
-    int is_max;    /* 1: max reduction, 0: FP64 sum */
+    int is_max;    /* 1: max reduction, 0: compensated sum */
 } unpack_col;
 
 static int unpack_columns(int loop, oracle_fields *f, unpack_col *c)
@@ -605,7 +606,9 @@ int oracle_unpack(int loop, oracle_fields *f, int64_t n, const int64_t *perm,
     lane_offsets(nl, sz, S, off);
     unpack_col col[8];
     int ncol = unpack_columns(loop, f, col);
-    double *acc = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * 8);
+    /* per particle and column: running sum s and compensation c */
+    float *sum = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1) * 8);
+    float *cmp = (float *)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1) * 8);
     uint8_t *touched = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
     int64_t slot = 0;
     for (int64_t t = t0; t < t1; ++t) {
@@ -616,8 +619,10 @@ int oracle_unpack(int loop, oracle_fields *f, int64_t n, const int64_t *perm,
                 int64_t p = perm[k];
                 if (!touched[p]) {
                     touched[p] = 1;
-                    for (int q = 0; q < ncol; ++q)
-                        acc[8 * p + q] = (double)col[q].field[col[q].ncomp * p + col[q].comp];
+                    for (int q = 0; q < ncol; ++q) {
+                        sum[8 * p + q] = col[q].field[col[q].ncomp * p + col[q].comp];
+                        cmp[8 * p + q] = 0.0f;
+                    }
                 }
                 for (int q = 0; q < ncol; ++q) {
                     float val;
@@ -626,7 +631,10 @@ int oracle_unpack(int loop, oracle_fields *f, int64_t n, const int64_t *perm,
                         float *d = &col[q].field[col[q].ncomp * p + col[q].comp];
                         *d = fmaxf(*d, val);
                     } else {
-                        acc[8 * p + q] += (double)val;
+                        volatile float y = val - cmp[8 * p + q];
+                        volatile float tsum = sum[8 * p + q] + y;
+                        cmp[8 * p + q] = (tsum - sum[8 * p + q]) - y;
+                        sum[8 * p + q] = tsum;
                     }
                 }
             }
@@ -636,9 +644,10 @@ int oracle_unpack(int loop, oracle_fields *f, int64_t n, const int64_t *perm,
         if (!touched[p]) continue;
         for (int q = 0; q < ncol; ++q)
             if (!col[q].is_max)
-                col[q].field[col[q].ncomp * p + col[q].comp] = (float)acc[8 * p + q];
+                col[q].field[col[q].ncomp * p + col[q].comp] = sum[8 * p + q];
     }
-    free(acc);
+    free(sum);
+    free(cmp);
     free(touched);
     return 0;
 }

@@ -452,7 +452,7 @@ def test_pack_gathers_views_with_periodic_shift():
         np.testing.assert_array_equal(a, b)
 
 
-def test_unpack_is_an_ordered_fp64_sum_and_max():
+def test_unpack_is_a_compensated_sum_and_a_max():
     f = ics.uniform_lattice(n_side=12, jitter=0.45, seed=91)
     nc, perm, cs = oracle.grid(f)
     ci, cj, sh = oracle.tasks(nc, cs)
@@ -465,6 +465,7 @@ def test_unpack_is_an_ordered_fp64_sum_and_max():
     p = np.concatenate(parts)
     S = len(p)
     n = f["x"].shape[0]
+    eps = 2.0 ** -24
     for loop, sizes in ((oracle.DENSITY, [16, 16]), (oracle.GRADIENT, [8]),
                         (oracle.FORCE, [16, 8])):
         nbytes = oracle.buffer_bytes(loop, 1, S)
@@ -474,10 +475,22 @@ def test_unpack_is_an_ordered_fp64_sum_and_max():
         oracle.unpack(loop, g, perm, cs, ci, cj, t0, t1, buf)
         lanes = _lane_views(buf, sizes, S)
         cols = np.concatenate([l.view(np.float32).reshape(S, -1) for l in lanes], 1)
+        nslot = np.bincount(p, minlength=n)
 
-        def ssum(col):   # np.bincount adds in input order, in float64
-            return np.bincount(p, weights=cols[:, col].astype(np.float64),
-                               minlength=n).astype(np.float32)
+        def check_sum(got, col):
+            # exact sum (float64 is exact for <= 27 floats in [-1,1)) against
+            # Kahan's bound (2u + O(n u^2)) sum|x|, u = 2^-24 (Higham, Acc. and
+            # Stab. of Num. Alg., 4.3) ...
+            exact = np.bincount(p, weights=cols[:, col].astype(np.float64), minlength=n)
+            mag = np.bincount(p, weights=np.abs(cols[:, col]).astype(np.float64), minlength=n)
+            err = np.abs(got.astype(np.float64) - exact)
+            assert np.all(err <= (2 * eps + 4 * nslot * eps * eps) * mag)
+            # ... and clearly better than a plain float32 running sum in the
+            # same order (numpy's unbuffered add.at adds in input order)
+            plain = np.zeros(n, np.float32)
+            np.add.at(plain, p, cols[:, col])
+            err_plain = np.abs(plain.astype(np.float64) - exact)
+            assert err.mean() < 0.5 * err_plain.mean()
 
         def smax(col):
             out = np.zeros(n, np.float32)
@@ -485,18 +498,45 @@ def test_unpack_is_an_ordered_fp64_sum_and_max():
             return out
         if loop == oracle.DENSITY:
             for col, k in enumerate(("rho", "rho_dh", "wcount", "wcount_dh", "div_v")):
-                np.testing.assert_array_equal(g[k], ssum(col))
+                check_sum(g[k], col)
             for c in range(3):
-                np.testing.assert_array_equal(g["rot_v"][:, c], ssum(5 + c))
+                check_sum(g["rot_v"][:, c], 5 + c)
         elif loop == oracle.GRADIENT:
             np.testing.assert_array_equal(g["v_sig_grad"], smax(0))
-            np.testing.assert_array_equal(g["laplace_u"], ssum(1))
+            check_sum(g["laplace_u"], 1)
         else:
             for c in range(3):
-                np.testing.assert_array_equal(g["a"][:, c], ssum(c))
-            np.testing.assert_array_equal(g["u_dt"], ssum(3))
-            np.testing.assert_array_equal(g["h_dt"], ssum(4))
+                check_sum(g["a"][:, c], c)
+            check_sum(g["u_dt"], 3)
+            check_sum(g["h_dt"], 4)
             np.testing.assert_array_equal(g["v_sig"], smax(5))
+
+
+def test_unpack_folds_from_the_stored_value():
+    # two bundles give the same sums as one when the second starts from the
+    # first's stored result (the fold restarts its compensation per bundle)
+    f = ics.uniform_lattice(n_side=12, jitter=0.45, seed=93)
+    nc, perm, cs = oracle.grid(f)
+    ci, cj, sh = oracle.tasks(nc, cs)
+    n = f["x"].shape[0]
+    bs = oracle.bundles(ci, cj, cs, 3000)
+    assert len(bs) > 2
+    g = ics.empty_fields(n)
+    g["x"] = f["x"]
+    total = np.zeros(n)
+    for b in range(len(bs) - 1):
+        S = oracle.bundle_slots(ci, cj, cs, bs[b], bs[b + 1])
+        buf = ics.random_result_lanes(oracle.buffer_bytes(oracle.GRADIENT, 1, S), seed=b)
+        oracle.unpack(oracle.GRADIENT, g, perm, cs, ci, cj, bs[b], bs[b + 1], buf)
+        parts = []
+        for t in range(bs[b], bs[b + 1]):
+            for c in (ci[t], cj[t]):
+                if c >= 0:
+                    parts.append(perm[cs[c]:cs[c + 1]])
+        pp = np.concatenate(parts)
+        vals = buf[: 8 * S].view(np.float32).reshape(S, 2)[:, 1]
+        total += np.bincount(pp, weights=vals.astype(np.float64), minlength=n)
+    assert np.max(np.abs(g["laplace_u"] - total)) < 1e-5
 
 
 # ----------------------------------------------------------------- layouts ---
