@@ -1,0 +1,454 @@
+#!/usr/bin/env python3
+"""Benchmark of the SPH cell-pair offload pipeline on one B300.
+
+Workload: the Gresho-vortex shaped set of 256^3 particles (jittered lattice,
+55/73/64/64 particles per cell, the paper's "Gresho256", Sec. 3.4), one step =
+density -> ghost -> gradient -> force, each loop = init + per bundle
+(pack -> interaction kernel -> unpack).  Metric: pair interactions per second
+of the whole step, plus pack+unpack GB/s per loop, for every store layout of
+Sec. 3.1 (sAoS vs AoS).  The headline value is the split (sAoS) layout
+BENCH_LAYOUT.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-interactions/s and pack+unpack GB/s per loop, sAoS vs AoS, 1 B300"
+UNIT = "pair-interactions/s"
+BENCH_LAYOUT = "pack_force_type"
+BUNDLE_SLOTS = 1 << 25
+N_SIDE = 256
+ALL_LAYOUTS = ("aos", "aos_random", "pack_grad", "pack_force", "pack_shared",
+               "pack_grad_type", "pack_force_type", "pack_shared_type", "soa")
+LOOP_NAMES = ("density", "gradient", "force")
+# algorithmic bytes: view read + written per slot (pack), result read per slot
+# plus output fields read + written per particle (unpack)
+VIEW_IN = (44, 52, 69)
+VIEW_OUT = (32, 8, 24)
+# FP32 operations (FMA = 2) of the implemented formula: per candidate test
+# and per accepted pair of each loop
+FLOPS_CANDIDATE = 8
+FLOPS_PAIR = (73, 52, 113)
+# FP32 CUDA-core peak: 148 SMs x 128 lanes x 2 flop x 2.032 GHz
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# DRAM bytes per launch of the interaction kernels from an ncu capture, valid
+# only for the kernel source with this digest (else reported as null)
+NCU_TRAFFIC = {}
+GPU_KERNEL_SRC = os.path.join(ROOT, "paper_2606_23891_b300", "csrc", "physics_kernels.cuh")
+
+
+def src_digest() -> str:
+    with open(GPU_KERNEL_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+# ---------------------------------------------------------------- clocks --
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------- distributed --
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def barrier_max(value: float, ws: int) -> float:
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------- CPU arms --
+def oracle_sample(f, nsample: int, seed: int):
+    """Time the oracle's full chain on `nsample` particles of the workload."""
+    import oracle
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sel = np.sort(rng.choice(f["x"].shape[0], nsample, replace=False)).astype(np.int64)
+    t = time.perf_counter()
+    out = oracle.chain(f, oracle.params(), sel)
+    dt = time.perf_counter() - t
+    pairs = sum(out["pairs"].values())
+    return pairs, dt
+
+
+def cpu_cores() -> int:
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    from paper_2606_23891_b300 import ics
+    f = ics.gresho(n_side=args.n_side)
+    for _ in range(args.warmup):
+        oracle_sample(f, 1, 1)
+    tot_pairs, tot_t = 0, 0.0
+    for k in range(args.steps):
+        p, t = oracle_sample(f, args.ref_sample, 100 + k)
+        tot_pairs += p
+        tot_t += t
+    value = tot_pairs / tot_t
+    sample = ("%d steps x %d particles of the %d^3 Gresho set; each particle's full "
+              "density->ghost->gradient->force chain by brute-force O(N) scans "
+              "(neighbour densities included)" % (args.steps, args.ref_sample, args.n_side))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "gresho256", "particles": int(f["x"].shape[0])},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm --
+def candidates(off) -> int:
+    ci, cj, sh, cs, bs = off.task_list()
+    cnt = np.diff(cs).astype(np.int64)
+    ni = cnt[ci]
+    nj = np.where(cj >= 0, cnt[np.maximum(cj, 0)], 0)
+    return int(np.where(cj >= 0, 2 * ni * nj, ni * (ni - 1)).sum())
+
+
+class StepTimer:
+    """Run one step with CUDA events around every stage on the launch stream."""
+
+    def __init__(self, off):
+        import torch
+        self.torch = torch
+        self.off = off
+        self.recs = []
+        self.launches = 0
+
+    def ev(self):
+        e = self.torch.cuda.Event(enable_timing=True)
+        e.record()
+        return e
+
+    def step(self, record: bool):
+        from paper_2606_23891_b300 import sph
+        off = self.off
+        nb = off.nbundles()
+        for loop in range(3):
+            sph.sph_init(off.store, loop, off.params, off.stream)
+            self.launches += 1
+            for b in range(nb):
+                e0 = self.ev() if record else None
+                off.pack(loop, b)
+                e1 = self.ev() if record else None
+                off.interact(loop, b)
+                e2 = self.ev() if record else None
+                off.unpack(loop, b)
+                e3 = self.ev() if record else None
+                self.launches += 3
+                if record:
+                    self.recs.append((loop, e0, e1, e2, e3))
+            if loop == 0:
+                sph.sph_ghost(off.store, 0, off.params, off.stream)
+                self.launches += 1
+
+    def stage_ms(self):
+        out = {(s, l): 0.0 for s in ("pack", "kernel", "unpack") for l in range(3)}
+        cnt = {l: 0 for l in range(3)}
+        for loop, e0, e1, e2, e3 in self.recs:
+            out[("pack", loop)] += e0.elapsed_time(e1)
+            out[("kernel", loop)] += e1.elapsed_time(e2)
+            out[("unpack", loop)] += e2.elapsed_time(e3)
+            cnt[loop] += 1
+        return out, cnt
+
+
+def run_layout(off, steps, warmup, ws, clocks=None):
+    import torch
+    timer = StepTimer(off)
+    for _ in range(warmup):
+        timer.step(record=False)
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    timer.launches = 0
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record()
+    for _ in range(steps):
+        timer.step(record=True)
+    end.record()
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    cl = clocks.stop() if clocks else None
+    total_ms = start.elapsed_time(end)
+    return total_ms, timer, cl
+
+
+def run_e2e(off, f, steps, warmup):
+    """Same step through the C-ABI from pinned host inputs to host results."""
+    import torch
+    from paper_2606_23891_b300 import sph
+    from paper_2606_23891_b300.pipeline import INPUTS, OUTPUTS, field_spec, fields_struct
+    pin_in, dev_in = {}, {}
+    for name in INPUTS:
+        dt, k = field_spec(name)
+        arr = np.ascontiguousarray(f[name], dt)
+        pin_in[name] = torch.from_numpy(arr).pin_memory()
+        dev_in[name] = torch.empty_like(pin_in[name], device=off.device)
+    dev_out = off.device_fields(OUTPUTS)
+    pin_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in dev_out.items()}
+    h2d = sum(t.numel() * t.element_size() for t in pin_in.values())
+    d2h = sum(t.numel() * t.element_size() for t in pin_out.values())
+    timer = StepTimer(off)
+    Fi, Fo = fields_struct(dev_in), fields_struct(dev_out)
+
+    def one():
+        for k in INPUTS:
+            dev_in[k].copy_(pin_in[k], non_blocking=True)
+        sph.sph_store_import(off.store, Fi, off.d_perm.data_ptr(), off.stream)
+        timer.step(record=False)
+        sph.sph_store_export(off.store, Fo, off.d_perm.data_ptr(), off.stream)
+        for k in OUTPUTS:
+            pin_out[k].copy_(dev_out[k], non_blocking=True)
+
+    for _ in range(warmup):
+        one()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record()
+    for _ in range(steps):
+        one()
+    end.record()
+    torch.cuda.synchronize()
+    sph.sph_sync(off.stream)
+    return start.elapsed_time(end) / steps, h2d, d2h
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2606_23891_b300 import ics, sph
+    from paper_2606_23891_b300.pipeline import Offload
+
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    f = ics.gresho(n_side=args.n_side)
+    t_build = time.perf_counter()
+    base = Offload(f, layout=args.layouts[0], bundle_max_slots=args.bundle_slots)
+    t_build = time.perf_counter() - t_build
+    pairs = [base.count_pairs(l) for l in range(3)]
+    ncand = candidates(base)
+    slots = base.info["slots"]
+    n = base.n
+    per_layout = {}
+    head = None
+    for lname in args.layouts:
+        off = base if lname == args.layouts[0] else Offload(
+            f, layout=lname, share=base)
+        clocks = ClockSampler(local) if lname == args.headline else None
+        total_ms, timer, cl = run_layout(off, args.steps, args.warmup, ws, clocks)
+        total_ms = barrier_max(total_ms, ws)
+        st, cnt = timer.stage_ms()
+        ms_step = total_ms / args.steps
+        loops = {}
+        for l in range(3):
+            pk, kr, up = (st[(s, l)] / args.steps for s in ("pack", "kernel", "unpack"))
+            pack_b = slots * 2 * VIEW_IN[l]
+            unpack_b = slots * VIEW_OUT[l] + n * 2 * VIEW_OUT[l]
+            loops[LOOP_NAMES[l]] = {
+                "pack_ms": pk, "kernel_ms": kr, "unpack_ms": up,
+                "pack_unpack_GBps": (pack_b + unpack_b) / ((pk + up) * 1e-3) / 1e9,
+                "pack_GBps": pack_b / (pk * 1e-3) / 1e9,
+                "unpack_GBps": unpack_b / (up * 1e-3) / 1e9,
+                "pair_interactions_per_s": pairs[l] / ((pk + kr + up) * 1e-3),
+                "kernel_fp32_TFLOPs": (ncand * FLOPS_CANDIDATE + pairs[l] * FLOPS_PAIR[l])
+                / (kr * 1e-3) / 1e12,
+            }
+        per_layout[lname] = {"ms_per_step": ms_step,
+                             "pair_interactions_per_s": sum(pairs) * ws / (ms_step * 1e-3),
+                             "loops": loops}
+        if lname == args.headline:
+            head = (off, total_ms, timer, cl, st, cnt)
+        elif off is not base:
+            off.close()
+            del off
+            torch.cuda.empty_cache()
+    off, total_ms, timer, cl, st, cnt = head
+    ms_step = total_ms / args.steps
+    value = sum(pairs) * ws / (ms_step * 1e-3)
+    # dominant kernel of the headline layout
+    top = max(st, key=lambda k: st[k])
+    stage, loop = top
+    launches = cnt[loop]
+    dur = st[top] / launches                      # ms per launch
+    peaks = measured_peaks()
+    if stage == "kernel":
+        flops = (ncand * FLOPS_CANDIDATE + pairs[loop] * FLOPS_PAIR[loop]) / launches
+        achieved = flops / (dur * 1e-3) / 1e12
+        tr = NCU_TRAFFIC.get((stage, loop))
+        traffic = tr["bytes"] if tr and tr["src"] == src_digest() else None
+        roof = {"kernel": "interaction/%s" % LOOP_NAMES[loop], "bound": "alu",
+                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"}
+    else:
+        bpl = (slots * 2 * VIEW_IN[loop] if stage == "pack"
+               else slots * VIEW_OUT[loop] + n * 2 * VIEW_OUT[loop]) / launches
+        achieved = bpl / (dur * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6400.0)
+        roof = {"kernel": "%s/%s" % (stage, LOOP_NAMES[loop]), "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": "measured" if peaks else "fallback"}
+    e2e_ms, h2d, d2h = run_e2e(off, f, max(1, args.steps // 2), 1)
+    e2e_ms = barrier_max(e2e_ms, ws)
+    cpu = None
+    if rank == 0 and ws == 1 and args.cpu_sample > 0:
+        p, t = oracle_sample(f, args.cpu_sample, 7)
+        cpu = {"value": p / t, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": "%d particles of the %d^3 Gresho set, each with its full "
+                         "density->ghost->gradient->force chain by brute-force O(N) "
+                         "scans (neighbour densities included), %.1f s"
+                         % (args.cpu_sample, args.n_side, t)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {
+            "workload": "gresho256: Gresho-vortex shaped jittered 256^3 lattice, "
+                        "64^3 cells of 55..73 particles, all loops",
+            "particles": n, "layout": args.headline, "tasks": base.info["ntasks"],
+            "bundles": base.info["nbundles"], "bundle_max_slots": args.bundle_slots,
+            "slots_per_loop": slots, "candidates_per_loop": ncand,
+            "pairs": dict(zip(LOOP_NAMES, pairs)),
+            "l2": "inputs larger than L2 (store %.2f GB, pack buffer %.2f GB)"
+                  % (off.nbytes / 1e9, off.buf_in.numel() / 1e9),
+            "parallelism": "replicas" if ws > 1 else "single GPU",
+            "task_build_s": t_build,
+        },
+        "e2e": {"value": sum(pairs) * ws / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_ms},
+        "gpu_launches": timer.launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": cl,
+        "layouts": per_layout,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--layouts", default=",".join(ALL_LAYOUTS))
+    ap.add_argument("--headline", default=BENCH_LAYOUT)
+    ap.add_argument("--bundle-slots", type=int, default=BUNDLE_SLOTS)
+    ap.add_argument("--n-side", type=int, default=N_SIDE)
+    ap.add_argument("--cpu-sample", type=int, default=16)
+    ap.add_argument("--ref-sample", type=int, default=2)
+    args = ap.parse_args(argv)
+    args.layouts = [s for s in args.layouts.split(",") if s]
+    if args.headline not in args.layouts:
+        args.layouts.append(args.headline)
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, ws, rank)
+    return run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,266 @@
+/*
+ * sph.h -- C-ABI of the B300 SPH cell-pair offload library (libsph.so).
+ *
+ * The library implements the GPU-offload cycle of Sec. 2.3: cell-pair tasks
+ * are gathered into bundles; for each bundle, "pack" gathers the particle
+ * fields a loop reads (its view, Table 1) into a compact buffer, applying
+ * the periodic shift to positions; the interaction kernel of the loop runs
+ * on the buffer; "unpack" reduces the per-slot results back into the
+ * particle store.  The particle store can use any of the memory layouts of
+ * Sec. 3.1 (AoS, random-order AoS, split AoS by kernel view and by type,
+ * SoA).  The loops are density, gradient and force, in that order
+ * (Sec. 2.1), with a linear "ghost" update after density.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an sph_status.  On failure sph_last_error() gives a
+ *    message (thread-local, valid until the next call on the same thread).
+ *  - GPU calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL is the legacy default stream).  Pointers named dev_* are device
+ *    pointers; pointers named host_* are host pointers.
+ *  - The library never allocates the large buffers: the particle store and
+ *    the pack/result buffers are caller memory, sized by the *_bytes
+ *    queries.  It allocates only the task metadata of an sph_tasks handle
+ *    (host and, after sph_tasks_upload, device memory; freed by
+ *    sph_tasks_destroy).
+ *  - Handles are not thread-safe; use one handle per thread or serialise.
+ *  - Particle indices are int64 on the host; on the device a store holds at
+ *    most 2^31 - 1 particles and a bundle at most 2^31 - 1 slots.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sph_store_s *sph_store;
+typedef struct sph_tasks_s *sph_tasks;
+
+/* Store layouts of Sec. 3.1. */
+enum sph_layout {
+    SPH_AOS = 0,                   /* one struct per particle, use order */
+    SPH_AOS_RANDOM = 1,            /* AoS with members shuffled (seeded) */
+    SPH_SAOS_PACK_GRAD = 2,        /* substruct = the gradient view */
+    SPH_SAOS_PACK_FORCE = 3,       /* substruct = the force view */
+    SPH_SAOS_PACK_SHARED = 4,      /* shared {x,v,m,h}, {u,rho}, force-only */
+    SPH_SAOS_PACK_GRAD_TYPE = 5,   /* pack-gradient split by double/float/int */
+    SPH_SAOS_PACK_FORCE_TYPE = 6,  /* pack-force split by type */
+    SPH_SAOS_PACK_SHARED_TYPE = 7, /* pack-shared split by type */
+    SPH_SOA = 8,                   /* one array per field component */
+    SPH_NUM_LAYOUTS = 9
+};
+
+/* Interaction loops of Sec. 2.1. */
+enum sph_loop { SPH_DENSITY = 0, SPH_GRADIENT = 1, SPH_FORCE = 2 };
+
+enum sph_status {
+    SPH_OK = 0,
+    SPH_EINVAL = 1,       /* bad argument (NULL handle, size, index, enum) */
+    SPH_ENOMEM = 2,       /* host or device metadata allocation failed */
+    SPH_ECUDA = 3,        /* a CUDA runtime call failed */
+    SPH_EBOUNDS = 4,      /* a kernel saw an index outside its buffers */
+    SPH_ETIMEOUT = 5,     /* a bounded device wait ran out */
+    SPH_EUNSUPPORTED = 6  /* valid request the library cannot serve */
+};
+
+/* Logical particle fields, one array per field in ORIGINAL particle order.
+ * Vector fields (x, v, a, rot_v) hold 3 consecutive components per particle.
+ * A NULL pointer means "not transferred". */
+typedef struct {
+    double *x;          /* positions, FP64 */
+    float *v;           /* velocities */
+    float *a;           /* accelerations (force loop output) */
+    float *mass;
+    float *h;           /* smoothing length; kernel support H = kernel_gamma h */
+    float *u;           /* internal energy per unit mass */
+    float *u_dt;        /* du/dt (force output) */
+    float *rho;         /* density (density output, gradient/force input) */
+    int8_t *time_bin;   /* force loop activity: active iff time_bin <= bin */
+    float *alpha_visc;  /* artificial viscosity coefficient */
+    float *alpha_diff;  /* artificial conduction coefficient */
+    float *rho_dh;      /* d rho / d H */
+    float *wcount;      /* weighted neighbour number (4 pi/3) H^3 sum W */
+    float *wcount_dh;   /* d wcount / d H */
+    float *div_v;       /* velocity divergence */
+    float *rot_v;       /* velocity curl (3 components) */
+    float *f_gradh;     /* grad-h factor 1/Omega */
+    float *pressure;
+    float *soundspeed;
+    float *balsara;     /* Balsara switch */
+    float *v_sig_grad;  /* signal velocity of the gradient loop */
+    float *laplace_u;   /* Laplacian of u */
+    float *h_dt;        /* dh/dt (force output) */
+    float *v_sig;       /* signal velocity of the force loop */
+    int64_t *id;        /* particle id (ballast for the loops) */
+} sph_fields;
+
+/* Physical parameters of the loops. */
+typedef struct {
+    double gamma;         /* adiabatic index, 5/3 */
+    double kernel_gamma;  /* H / h of the cubic spline, 1.825742 */
+    double beta_visc;     /* signal-velocity factor, 3 */
+    double balsara_eps;   /* Balsara regulariser (times c/h), 1e-4 */
+    int32_t active_bin;   /* force loop: particle active iff time_bin <= it */
+    int32_t reserved;     /* must be 0 */
+} sph_params;
+
+/* Cell grid and bundling parameters for sph_tasks_build. */
+typedef struct {
+    double box[3];             /* periodic box edges (> 0) */
+    double kernel_gamma;       /* H / h, as in sph_params */
+    int32_t ncell[3];          /* cells per dimension, 0 = octree rule:
+                                  halve the edge while the half is >= H_max */
+    int32_t reserved;          /* must be 0 */
+    int64_t bundle_max_slots;  /* bundle slot budget, <= 0: one bundle */
+} sph_grid_params;
+
+/* ---- library ---------------------------------------------------------- */
+const char *sph_version(void);
+const char *sph_last_error(void);
+
+/* ---- particle store (Sec. 3.1) ----------------------------------------
+ * A layout is a sequence of substructs; each substruct is a C struct of its
+ * members with natural alignment, and the substruct arrays follow each other
+ * in the caller's memory, each starting on a 256-byte boundary.
+ * SPH_AOS_RANDOM shuffles the AoS members with a Fisher-Yates shuffle driven
+ * by SplitMix64 seeded with `seed`; other layouts ignore `seed`. */
+
+/* Bytes of caller memory a store of n particles needs (0 on bad input). */
+size_t sph_store_bytes(int64_t n, int layout, uint64_t seed);
+
+/* Number of substructs of a layout, or -1.  Host only. */
+int sph_layout_group_count(int layout, uint64_t seed);
+
+/* Describe substruct `group`: member count, member field ids (the order of
+ * sph_fields, 25 = ballast bytes), component (SoA: 0..2, else -1), member
+ * byte offsets, record bytes.  Arrays hold >= 26 entries.  Host only. */
+int sph_layout_describe(int layout, uint64_t seed, int group, int32_t *nmem,
+                        int32_t *field_ids, int32_t *comps, int32_t *offsets,
+                        int32_t *record_bytes);
+
+/* Create a store over caller device memory dev_mem (>= sph_store_bytes,
+ * 256-byte aligned; owned by the caller and not freed by the library).
+ * The memory is zero-filled (synchronously). */
+int sph_store_create(int64_t n, int layout, uint64_t seed, void *dev_mem,
+                     size_t bytes, sph_store *out);
+int sph_store_destroy(sph_store s);
+
+/* Copy logical fields into / out of the store.  Store slot k holds original
+ * particle dev_perm[k] (device int64[n]; NULL = identity).  Fields whose
+ * pointer is NULL are skipped.  All field pointers are device pointers. */
+int sph_store_import(sph_store s, const sph_fields *dev_src,
+                     const int64_t *dev_perm, void *stream);
+int sph_store_export(sph_store s, const sph_fields *dev_dst,
+                     const int64_t *dev_perm, void *stream);
+
+/* ---- cells, tasks, bundles (Sec. 2.2-2.3) ------------------------------
+ * Host-side builder.  Cells: a uniform grid with edges >= H_max =
+ * kernel_gamma * max h (>= 3 cells per dimension).  Particles are sorted by
+ * cell (ix fastest) with a stable counting sort; host_perm_out[k] receives
+ * the original index of the k-th particle in cell order, to be passed to
+ * sph_store_import.  Tasks: per non-empty cell a self task, then a pair
+ * task for each of the 13 neighbour offsets after (0,0,0) in the (dz,dy,dx)
+ * enumeration of {-1,0,1}^3 whose cell is not empty, the second cell's
+ * particles shifted by -1/0/+1 box edges per dimension.  Bundles: greedy
+ * consecutive task ranges of at most bundle_max_slots slots. */
+int sph_tasks_build(int64_t n, const double *host_x, const float *host_h,
+                    const sph_grid_params *gp, int64_t *host_perm_out,
+                    sph_tasks *out);
+
+/* Copy the task metadata to the current device (synchronous).  Required
+ * before any GPU call that takes the handle. */
+int sph_tasks_upload(sph_tasks t);
+
+/* info[0..2] cells per dimension, [3] tasks, [4] bundles, [5] total slots,
+ * [6] largest bundle slots, [7] non-empty cells, [8] particles,
+ * [9] largest cell population.  Host only. */
+int sph_tasks_info(sph_tasks t, int64_t info[10]);
+
+/* Host copies of the task list: ci[ntasks], cj[ntasks] (-1 for self),
+ * shift[3 ntasks], cell_start[ncells + 1], bundle_start[nbundles + 1].
+ * Any pointer may be NULL.  Host only. */
+int sph_tasks_get(sph_tasks t, int32_t *ci, int32_t *cj, int8_t *shift,
+                  int64_t *cell_start, int64_t *bundle_start);
+
+/* Largest buffer any bundle needs for `loop`: in_or_out 0 = pack buffer,
+ * 1 = result buffer.  Lane k of a bundle of S slots starts at
+ * sum_{l<k} round_up(S * size_l, 256) bytes; slots are ordered by task and,
+ * inside a pair task, ci's particles then cj's.
+ *   density  in : x0 x1 x2 (f64) | {vx vy vz m} (4 f32) | h
+ *   gradient in : density in | u | rho
+ *   force    in : gradient in | f_gradh | balsara | alpha_visc | alpha_diff |
+ *                 time_bin (i8)
+ *   density  out: {rho rho_dh wcount wcount_dh} | {div_v rot_x rot_y rot_z}
+ *   gradient out: {v_sig_grad laplace_u}
+ *   force    out: {ax ay az u_dt} | {h_dt v_sig}
+ * Returns 0 on bad input. */
+size_t sph_buffer_bytes(sph_tasks t, int loop, int in_or_out);
+
+/* ---- the offload cycle (Sec. 2.3) --------------------------------------
+ * For one loop: sph_init, then for every bundle b in order sph_pack ->
+ * sph_density|gradient|force -> sph_unpack, then (after density) sph_ghost. */
+
+/* Zero the outputs of `loop` in the store (force: active particles only). */
+int sph_init(sph_store s, int loop, const sph_params *p, void *stream);
+
+/* Gather the view of `loop` for bundle b into dev_buf_in.  Positions of a
+ * pair task's second cell get x + shift * box in FP64 (Sec. 2.3). */
+int sph_pack(sph_store s, sph_tasks t, int loop, int bundle, void *dev_buf_in,
+             void *stream);
+
+/* Interaction kernels: one result record per slot.  Slot of particle i in
+ * task T holds the sums over the other cell of T (self task: over j != i of
+ * the same cell):
+ *   density : sum m_j W(r,H_i), sum m_j dW/dH(r,H_i), (4pi/3) H_i^3 sum W,
+ *             its H-derivative, -sum m_j v_ij.rhat dW/dr, sum m_j v_ij x rhat
+ *             dW/dr  (r < H_i; cubic spline, 8/pi normalisation)
+ *   gradient: max_j (c_i + c_j - beta min(0, v_ij.rhat)),
+ *             sum 2 m_j (u_i - u_j)/rho_j dW/dr(r,H_i)/r
+ *   force   : a_i, du_i/dt, dh_i/dt contributions and max signal velocity
+ *             over r < max(H_i, H_j); inactive i write zeros.
+ * Positions are FP64 in the buffer; separations are formed in compensated
+ * (two-float) arithmetic, the rest in FP32 with a compensated density sum. */
+int sph_density(sph_tasks t, int bundle, const void *dev_buf_in,
+                void *dev_buf_out, const sph_params *p, void *stream);
+int sph_gradient(sph_tasks t, int bundle, const void *dev_buf_in,
+                 void *dev_buf_out, const sph_params *p, void *stream);
+int sph_force(sph_tasks t, int bundle, const void *dev_buf_in,
+              void *dev_buf_out, const sph_params *p, void *stream);
+
+/* Reduce bundle b's result buffer into the store: per particle, its slots in
+ * increasing task order (ci before cj) are added to the stored value with
+ * Kahan-compensated FP32 summation (compensation starting at 0 for each
+ * call); signal velocities take the max.  Deterministic, no atomics. */
+int sph_unpack(sph_store s, sph_tasks t, int loop, int bundle,
+               const void *dev_buf_out, void *stream);
+
+/* Linear update after `loop` (only SPH_DENSITY has one): add the self
+ * contribution, divide div/curl by rho, and set f_gradh = 1/Omega,
+ * pressure, sound speed and the Balsara switch. */
+int sph_ghost(sph_store s, int after_loop, const sph_params *p, void *stream);
+
+/* Convenience: the whole cycle of one loop over all bundles (init, pack,
+ * kernel, unpack per bundle, ghost after density), on caller buffers of
+ * sph_buffer_bytes(t, loop, 0/1) bytes. */
+int sph_offload_loop(sph_store s, sph_tasks t, int loop, void *dev_buf_in,
+                     void *dev_buf_out, const sph_params *p, void *stream);
+
+/* Count the pair interactions of `loop` in bundle b (r < H_i for density and
+ * gradient, r < max(H_i, H_j) for force, i active), added to
+ * *dev_count (device uint64). */
+int sph_count_pairs(sph_tasks t, int loop, int bundle, const void *dev_buf_in,
+                    const sph_params *p, unsigned long long *dev_count,
+                    void *stream);
+
+/* Wait for `stream` and report errors latched by kernels (SPH_EBOUNDS). */
+int sph_sync(void *stream);
+
+int sph_tasks_destroy(sph_tasks t);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_H */

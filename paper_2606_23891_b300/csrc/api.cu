@@ -1,0 +1,514 @@
+// C-ABI entry points of libsph (include/sph.h): argument checks, descriptor
+// set-up and kernel launches.  All device code is compiled in this
+// translation unit.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.h"
+#include "device.cuh"
+#include "pack_kernels.cuh"
+#include "physics_kernels.cuh"
+#include "store_kernels.cuh"
+
+namespace sph {
+
+static thread_local char g_msg[512] = "";
+
+int fail(int status, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+static int cuda_check(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return SPH_OK;
+    return fail(SPH_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static int launch_check(const char *what) {
+    return cuda_check(cudaGetLastError(), what);
+}
+
+static int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b > 148LL * 16) b = 148LL * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+static bool aligned256(const void *p) { return ((uintptr_t)p & 255u) == 0; }
+
+static int check_store(sph_store s) {
+    if (!s) return fail(SPH_EINVAL, "NULL store handle");
+    return SPH_OK;
+}
+
+static int check_tasks(sph_tasks t, int bundle) {
+    if (!t) return fail(SPH_EINVAL, "NULL tasks handle");
+    if (!t->d_tasks && !t->tdev.empty())
+        return fail(SPH_EINVAL, "tasks not uploaded (call sph_tasks_upload)");
+    if (bundle < 0 || bundle >= (int64_t)t->bundle_slots.size())
+        return fail(SPH_EINVAL, "bundle %d out of range [0, %lld)", bundle,
+                    (long long)t->bundle_slots.size());
+    return SPH_OK;
+}
+
+static int check_loop(int loop) {
+    if (loop < SPH_DENSITY || loop > SPH_FORCE) return fail(SPH_EINVAL, "bad loop %d", loop);
+    return SPH_OK;
+}
+
+static int check_params(const sph_params *p) {
+    if (!p) return fail(SPH_EINVAL, "NULL params");
+    if (p->reserved != 0) return fail(SPH_EINVAL, "params.reserved must be 0");
+    if (!(p->kernel_gamma > 0.0) || !(p->gamma > 1.0))
+        return fail(SPH_EINVAL, "params: kernel_gamma > 0 and gamma > 1 required");
+    return SPH_OK;
+}
+
+// Store address of (field, comp); every field exists in every layout.
+static CompPtr at(sph_store s, int field, int comp) {
+    CompPtr c{nullptr, 0};
+    locate(s->layout, s->mem, field, comp, &c);
+    return c;
+}
+
+static void lanes(int loop, int in_or_out, int64_t S, char *buf, char **out, int *nl) {
+    int64_t off[16];
+    int64_t sz[16];
+    *nl = lane_sizes(loop, in_or_out, sz);
+    lane_offsets(loop, in_or_out, S, off);
+    for (int k = 0; k < *nl; ++k) out[k] = buf + off[k];
+}
+
+static int check_bundle_store(sph_store s, sph_tasks t) {
+    if (s->n != t->n)
+        return fail(SPH_EINVAL, "store has %lld particles, tasks %lld", (long long)s->n,
+                    (long long)t->n);
+    return SPH_OK;
+}
+
+}  // namespace sph
+
+using namespace sph;
+
+extern "C" {
+
+const char *sph_version(void) { return "sph-b300 0.1 (sm_103a)"; }
+
+const char *sph_last_error(void) { return g_msg; }
+
+size_t sph_store_bytes(int64_t n, int layout, uint64_t seed) {
+    if (n < 0) return 0;
+    Layout L;
+    if (build_layout(layout, seed, n, &L) != SPH_OK) return 0;
+    return (size_t)layout_bytes(L, n);
+}
+
+int sph_layout_group_count(int layout, uint64_t seed) {
+    Layout L;
+    if (build_layout(layout, seed, 0, &L) != SPH_OK) return -1;
+    return (int)L.groups.size();
+}
+
+int sph_layout_describe(int layout, uint64_t seed, int group, int32_t *nmem,
+                        int32_t *field_ids, int32_t *comps, int32_t *offsets,
+                        int32_t *record_bytes) {
+    Layout L;
+    if (build_layout(layout, seed, 0, &L) != SPH_OK)
+        return fail(SPH_EINVAL, "bad layout %d", layout);
+    if (group < 0 || group >= (int)L.groups.size())
+        return fail(SPH_EINVAL, "group %d out of range", group);
+    const Group &g = L.groups[group];
+    if (nmem) *nmem = (int32_t)g.mem.size();
+    for (size_t k = 0; k < g.mem.size(); ++k) {
+        if (field_ids) field_ids[k] = g.mem[k].field;
+        if (comps) comps[k] = g.mem[k].comp;
+        if (offsets) offsets[k] = g.mem[k].offset;
+    }
+    if (record_bytes) *record_bytes = g.record;
+    return SPH_OK;
+}
+
+int sph_store_create(int64_t n, int layout, uint64_t seed, void *dev_mem, size_t bytes,
+                     sph_store *out) {
+    if (!out) return fail(SPH_EINVAL, "NULL out");
+    *out = nullptr;
+    if (n < 0 || n > INT32_MAX) return fail(SPH_EINVAL, "bad particle count %lld", (long long)n);
+    Layout L;
+    if (build_layout(layout, seed, n, &L) != SPH_OK)
+        return fail(SPH_EINVAL, "bad layout %d", layout);
+    const int64_t need = layout_bytes(L, n);
+    if ((int64_t)bytes < need)
+        return fail(SPH_EINVAL, "store needs %lld bytes, got %zu", (long long)need, bytes);
+    if (need > 0 && (!dev_mem || !aligned256(dev_mem)))
+        return fail(SPH_EINVAL, "store memory must be a 256-byte aligned device pointer");
+    sph_store s = new (std::nothrow) sph_store_s;
+    if (!s) return fail(SPH_ENOMEM, "store handle");
+    s->n = n;
+    s->layout = L;
+    s->mem = (char *)dev_mem;
+    s->bytes = bytes;
+    if (need > 0) {
+        int rc = cuda_check(cudaMemset(dev_mem, 0, (size_t)need), "store zero-fill");
+        if (rc) {
+            delete s;
+            return rc;
+        }
+    }
+    *out = s;
+    return SPH_OK;
+}
+
+int sph_store_destroy(sph_store s) {
+    delete s;
+    return SPH_OK;
+}
+
+static int copy_fields(sph_store s, const sph_fields *f, const int64_t *perm, void *stream,
+                       int to_store) {
+    if (int rc = check_store(s)) return rc;
+    if (!f) return fail(SPH_EINVAL, "NULL fields");
+    if (s->n == 0) return SPH_OK;
+    void *const *ptrs = reinterpret_cast<void *const *>(f);
+    const int nfields = (int)(sizeof(sph_fields) / sizeof(void *));
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int fid = 0; fid < nfields && fid < F_BALLAST; ++fid) {
+        const char *p = (const char *)ptrs[fid];
+        if (!p) continue;
+        const int elem = kFields[fid].elem, cnt = kFields[fid].count;
+        for (int c = 0; c < cnt; ++c) {
+            CompPtr dst = at(s, fid, c);
+            k_copy_field<<<grid_for(s->n, 256), 256, 0, st>>>(p, elem * cnt, c * elem, elem, dst,
+                                                              perm, s->n, to_store);
+            if (int rc = launch_check("copy field")) return rc;
+        }
+    }
+    return SPH_OK;
+}
+
+int sph_store_import(sph_store s, const sph_fields *dev_src, const int64_t *dev_perm,
+                     void *stream) {
+    return copy_fields(s, dev_src, dev_perm, stream, 1);
+}
+
+int sph_store_export(sph_store s, const sph_fields *dev_dst, const int64_t *dev_perm,
+                     void *stream) {
+    return copy_fields(s, dev_dst, dev_perm, stream, 0);
+}
+
+int sph_tasks_build(int64_t n, const double *host_x, const float *host_h,
+                    const sph_grid_params *gp, int64_t *host_perm_out, sph_tasks *out) {
+    if (!out) return fail(SPH_EINVAL, "NULL out");
+    *out = nullptr;
+    sph_tasks t = new (std::nothrow) sph_tasks_s;
+    if (!t) return fail(SPH_ENOMEM, "tasks handle");
+    int rc;
+    try {
+        rc = build_tasks(n, host_x, host_h, gp, host_perm_out, t);
+    } catch (const std::bad_alloc &) {
+        rc = fail(SPH_ENOMEM, "tasks_build: host allocation failed");
+    }
+    if (rc) {
+        delete t;
+        return rc;
+    }
+    *out = t;
+    return SPH_OK;
+}
+
+static void free_device(sph_tasks t) {
+    if (t->d_tasks) cudaFree(t->d_tasks);
+    if (t->d_ucells) cudaFree(t->d_ucells);
+    if (t->d_entries) cudaFree(t->d_entries);
+    t->d_tasks = nullptr;
+    t->d_ucells = nullptr;
+    t->d_entries = nullptr;
+}
+
+int sph_tasks_upload(sph_tasks t) {
+    if (!t) return fail(SPH_EINVAL, "NULL tasks handle");
+    free_device(t);
+    int rc;
+    auto up = [&](void **dst, const void *src, size_t bytes, const char *what) -> int {
+        if (bytes == 0) return SPH_OK;
+        if (cudaMalloc(dst, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SPH_ENOMEM, "device allocation of %s (%zu bytes)", what, bytes);
+        }
+        return cuda_check(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), what);
+    };
+    if ((rc = up((void **)&t->d_tasks, t->tdev.data(), t->tdev.size() * sizeof(TaskDev),
+                 "tasks")) ||
+        (rc = up((void **)&t->d_ucells, t->ucells.data(), t->ucells.size() * sizeof(UCellDev),
+                 "unpack cells")) ||
+        (rc = up((void **)&t->d_entries, t->entries.data(), t->entries.size() * sizeof(int32_t),
+                 "unpack entries"))) {
+        free_device(t);
+        return rc;
+    }
+    cudaGetDevice(&t->device);
+    return SPH_OK;
+}
+
+int sph_tasks_info(sph_tasks t, int64_t info[10]) {
+    if (!t || !info) return fail(SPH_EINVAL, "NULL argument");
+    int64_t total = 0, big = 0, nonempty = 0;
+    for (int64_t s : t->bundle_slots) {
+        total += s;
+        if (s > big) big = s;
+    }
+    for (size_t c = 0; c + 1 < t->cell_start.size(); ++c)
+        if (t->cell_start[c + 1] > t->cell_start[c]) nonempty++;
+    info[0] = t->ncell[0];
+    info[1] = t->ncell[1];
+    info[2] = t->ncell[2];
+    info[3] = (int64_t)t->ci.size();
+    info[4] = (int64_t)t->bundle_slots.size();
+    info[5] = total;
+    info[6] = big;
+    info[7] = nonempty;
+    info[8] = t->n;
+    info[9] = t->max_cell;
+    return SPH_OK;
+}
+
+int sph_tasks_get(sph_tasks t, int32_t *ci, int32_t *cj, int8_t *shift, int64_t *cell_start,
+                  int64_t *bundle_start) {
+    if (!t) return fail(SPH_EINVAL, "NULL tasks handle");
+    if (ci) memcpy(ci, t->ci.data(), t->ci.size() * sizeof(int32_t));
+    if (cj) memcpy(cj, t->cj.data(), t->cj.size() * sizeof(int32_t));
+    if (shift) memcpy(shift, t->shift.data(), t->shift.size());
+    if (cell_start) memcpy(cell_start, t->cell_start.data(), t->cell_start.size() * sizeof(int64_t));
+    if (bundle_start)
+        memcpy(bundle_start, t->bundle_start.data(), t->bundle_start.size() * sizeof(int64_t));
+    return SPH_OK;
+}
+
+size_t sph_buffer_bytes(sph_tasks t, int loop, int in_or_out) {
+    if (!t || loop < SPH_DENSITY || loop > SPH_FORCE || (in_or_out != 0 && in_or_out != 1))
+        return 0;
+    int64_t big = 0;
+    for (int64_t s : t->bundle_slots) big = s > big ? s : big;
+    int64_t off[16];
+    return (size_t)lane_offsets(loop, in_or_out, big, off);
+}
+
+int sph_tasks_destroy(sph_tasks t) {
+    if (!t) return SPH_OK;
+    free_device(t);
+    delete t;
+    return SPH_OK;
+}
+
+int sph_init(sph_store s, int loop, const sph_params *p, void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (int rc = check_loop(loop)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (s->n == 0) return SPH_OK;
+    InitArgs a{};
+    int k = 0;
+    if (loop == SPH_DENSITY) {
+        a.out[k++] = at(s, F_RHO, 0);
+        a.out[k++] = at(s, F_RHODH, 0);
+        a.out[k++] = at(s, F_WCOUNT, 0);
+        a.out[k++] = at(s, F_WCOUNTDH, 0);
+        a.out[k++] = at(s, F_DIVV, 0);
+        for (int c = 0; c < 3; ++c) a.out[k++] = at(s, F_ROTV, c);
+    } else if (loop == SPH_GRADIENT) {
+        a.out[k++] = at(s, F_VSIGG, 0);
+        a.out[k++] = at(s, F_LAPU, 0);
+    } else {
+        for (int c = 0; c < 3; ++c) a.out[k++] = at(s, F_A, c);
+        a.out[k++] = at(s, F_UDT, 0);
+        a.out[k++] = at(s, F_HDT, 0);
+        a.out[k++] = at(s, F_VSIG, 0);
+        a.use_tb = 1;
+        a.tb = at(s, F_TBIN, 0);
+        a.active_bin = p->active_bin;
+    }
+    a.nout = k;
+    k_init<<<grid_for(s->n, 256), 256, 0, (cudaStream_t)stream>>>(a, s->n);
+    return launch_check("init");
+}
+
+int sph_pack(sph_store s, sph_tasks t, int loop, int bundle, void *dev_buf_in, void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (int rc = check_tasks(t, bundle)) return rc;
+    if (int rc = check_loop(loop)) return rc;
+    if (int rc = check_bundle_store(s, t)) return rc;
+    if (!dev_buf_in || !aligned256(dev_buf_in))
+        return fail(SPH_EINVAL, "pack buffer must be a 256-byte aligned device pointer");
+    const int64_t t0 = t->bundle_start[bundle], nt = t->bundle_start[bundle + 1] - t0;
+    PackArgs a{};
+    a.tasks = t->d_tasks + t0;
+    int nl;
+    lanes(loop, 0, t->bundle_slots[bundle], (char *)dev_buf_in, a.lane, &nl);
+    const int roles[R_NUM][2] = {{F_X, 0}, {F_X, 1}, {F_X, 2}, {F_V, 0}, {F_V, 1},
+                                 {F_V, 2}, {F_MASS, 0}, {F_H, 0}, {F_U, 0}, {F_RHO, 0},
+                                 {F_FGRADH, 0}, {F_BALS, 0}, {F_AVISC, 0}, {F_ADIFF, 0},
+                                 {F_TBIN, 0}};
+    for (int r = 0; r < R_NUM; ++r) a.src[r] = at(s, roles[r][0], roles[r][1]);
+    for (int d = 0; d < 3; ++d) a.box[d] = t->box[d];
+    cudaStream_t st = (cudaStream_t)stream;
+    if (nt == 0) return SPH_OK;
+    if (loop == SPH_DENSITY) k_pack<SPH_DENSITY><<<(unsigned)nt, 128, 0, st>>>(a);
+    else if (loop == SPH_GRADIENT) k_pack<SPH_GRADIENT><<<(unsigned)nt, 128, 0, st>>>(a);
+    else k_pack<SPH_FORCE><<<(unsigned)nt, 128, 0, st>>>(a);
+    return launch_check("pack");
+}
+
+static int interact(sph_tasks t, int loop, int bundle, const void *in, void *out,
+                    const sph_params *p, unsigned long long *count, void *stream) {
+    if (int rc = check_tasks(t, bundle)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (!in || !aligned256(in))
+        return fail(SPH_EINVAL, "pack buffer must be a 256-byte aligned device pointer");
+    if (!count && (!out || !aligned256(out)))
+        return fail(SPH_EINVAL, "result buffer must be a 256-byte aligned device pointer");
+    const int64_t t0 = t->bundle_start[bundle], nt = t->bundle_start[bundle + 1] - t0;
+    PhysArgs a{};
+    a.tasks = t->d_tasks + t0;
+    int nl;
+    char *inl[16];
+    lanes(loop, 0, t->bundle_slots[bundle], (char *)in, inl, &nl);
+    for (int k = 0; k < nl; ++k) a.in[k] = inl[k];
+    if (!count) lanes(loop, 1, t->bundle_slots[bundle], (char *)out, a.out, &nl);
+    a.kernel_gamma = (float)p->kernel_gamma;
+    a.gamma = (float)p->gamma;
+    a.beta = (float)p->beta_visc;
+    double bmax = t->box[0] > t->box[1] ? t->box[0] : t->box[1];
+    bmax = bmax > t->box[2] ? bmax : t->box[2];
+    a.delta = (float)(4e-6 * bmax);
+    a.active_bin = p->active_bin;
+    a.count = count;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (nt == 0) return SPH_OK;
+    const unsigned g = (unsigned)nt;
+    if (count) {
+        if (loop == SPH_DENSITY) k_interact<SPH_DENSITY, true><<<g, kThreads, 0, st>>>(a);
+        else if (loop == SPH_GRADIENT) k_interact<SPH_GRADIENT, true><<<g, kThreads, 0, st>>>(a);
+        else k_interact<SPH_FORCE, true><<<g, kThreads, 0, st>>>(a);
+    } else {
+        if (loop == SPH_DENSITY) k_interact<SPH_DENSITY, false><<<g, kThreads, 0, st>>>(a);
+        else if (loop == SPH_GRADIENT) k_interact<SPH_GRADIENT, false><<<g, kThreads, 0, st>>>(a);
+        else k_interact<SPH_FORCE, false><<<g, kThreads, 0, st>>>(a);
+    }
+    return launch_check("interaction kernel");
+}
+
+int sph_density(sph_tasks t, int bundle, const void *dev_buf_in, void *dev_buf_out,
+                const sph_params *p, void *stream) {
+    return interact(t, SPH_DENSITY, bundle, dev_buf_in, dev_buf_out, p, nullptr, stream);
+}
+
+int sph_gradient(sph_tasks t, int bundle, const void *dev_buf_in, void *dev_buf_out,
+                 const sph_params *p, void *stream) {
+    return interact(t, SPH_GRADIENT, bundle, dev_buf_in, dev_buf_out, p, nullptr, stream);
+}
+
+int sph_force(sph_tasks t, int bundle, const void *dev_buf_in, void *dev_buf_out,
+              const sph_params *p, void *stream) {
+    return interact(t, SPH_FORCE, bundle, dev_buf_in, dev_buf_out, p, nullptr, stream);
+}
+
+int sph_count_pairs(sph_tasks t, int loop, int bundle, const void *dev_buf_in,
+                    const sph_params *p, unsigned long long *dev_count, void *stream) {
+    if (int rc = check_loop(loop)) return rc;
+    if (!dev_count) return fail(SPH_EINVAL, "NULL count");
+    return interact(t, loop, bundle, dev_buf_in, nullptr, p, dev_count, stream);
+}
+
+int sph_unpack(sph_store s, sph_tasks t, int loop, int bundle, const void *dev_buf_out,
+               void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (int rc = check_tasks(t, bundle)) return rc;
+    if (int rc = check_loop(loop)) return rc;
+    if (int rc = check_bundle_store(s, t)) return rc;
+    if (!dev_buf_out || !aligned256(dev_buf_out))
+        return fail(SPH_EINVAL, "result buffer must be a 256-byte aligned device pointer");
+    UnpackArgs a{};
+    const int64_t c0 = t->ucell_begin[bundle], nc = t->ucell_begin[bundle + 1] - c0;
+    a.cells = t->d_ucells + c0;
+    a.entries = t->d_entries + t->entry_begin[bundle];
+    int nl;
+    char *ol[4] = {nullptr, nullptr, nullptr, nullptr};
+    lanes(loop, 1, t->bundle_slots[bundle], (char *)dev_buf_out, ol, &nl);
+    a.lane[0] = ol[0];
+    a.lane[1] = nl > 1 ? ol[1] : nullptr;
+    int k = 0;
+    if (loop == SPH_DENSITY) {
+        a.dst[k++] = at(s, F_RHO, 0);
+        a.dst[k++] = at(s, F_RHODH, 0);
+        a.dst[k++] = at(s, F_WCOUNT, 0);
+        a.dst[k++] = at(s, F_WCOUNTDH, 0);
+        a.dst[k++] = at(s, F_DIVV, 0);
+        for (int c = 0; c < 3; ++c) a.dst[k++] = at(s, F_ROTV, c);
+    } else if (loop == SPH_GRADIENT) {
+        a.dst[k++] = at(s, F_VSIGG, 0);
+        a.dst[k++] = at(s, F_LAPU, 0);
+    } else {
+        for (int c = 0; c < 3; ++c) a.dst[k++] = at(s, F_A, c);
+        a.dst[k++] = at(s, F_UDT, 0);
+        a.dst[k++] = at(s, F_HDT, 0);
+        a.dst[k++] = at(s, F_VSIG, 0);
+    }
+    if (nc == 0) return SPH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (loop == SPH_DENSITY) k_unpack<SPH_DENSITY><<<(unsigned)nc, 128, 0, st>>>(a);
+    else if (loop == SPH_GRADIENT) k_unpack<SPH_GRADIENT><<<(unsigned)nc, 128, 0, st>>>(a);
+    else k_unpack<SPH_FORCE><<<(unsigned)nc, 128, 0, st>>>(a);
+    return launch_check("unpack");
+}
+
+int sph_ghost(sph_store s, int after_loop, const sph_params *p, void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (int rc = check_loop(after_loop)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (after_loop != SPH_DENSITY || s->n == 0) return SPH_OK;
+    GhostArgs a{};
+    const int roles[14][2] = {{F_MASS, 0}, {F_H, 0}, {F_U, 0}, {F_RHO, 0}, {F_RHODH, 0},
+                              {F_WCOUNT, 0}, {F_DIVV, 0}, {F_ROTV, 0}, {F_ROTV, 1},
+                              {F_ROTV, 2}, {F_FGRADH, 0}, {F_PRES, 0}, {F_CS, 0},
+                              {F_BALS, 0}};
+    for (int r = 0; r < 14; ++r) a.f[r] = at(s, roles[r][0], roles[r][1]);
+    a.kernel_gamma = (float)p->kernel_gamma;
+    a.gamma = (float)p->gamma;
+    a.balsara_eps = (float)p->balsara_eps;
+    k_ghost<<<grid_for(s->n, 256), 256, 0, (cudaStream_t)stream>>>(a, s->n);
+    return launch_check("ghost");
+}
+
+int sph_offload_loop(sph_store s, sph_tasks t, int loop, void *dev_buf_in, void *dev_buf_out,
+                     const sph_params *p, void *stream) {
+    if (int rc = sph_init(s, loop, p, stream)) return rc;
+    if (!t) return fail(SPH_EINVAL, "NULL tasks handle");
+    const int nb = (int)t->bundle_slots.size();
+    for (int b = 0; b < nb; ++b) {
+        if (int rc = sph_pack(s, t, loop, b, dev_buf_in, stream)) return rc;
+        if (int rc = interact(t, loop, b, dev_buf_in, dev_buf_out, p, nullptr, stream)) return rc;
+        if (int rc = sph_unpack(s, t, loop, b, dev_buf_out, stream)) return rc;
+    }
+    return sph_ghost(s, loop, p, stream);
+}
+
+int sph_sync(void *stream) {
+    if (int rc = cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "stream sync"))
+        return rc;
+    unsigned int w = 0;
+    if (int rc = cuda_check(cudaMemcpyFromSymbol(&w, g_error_word, sizeof(w)), "error word"))
+        return rc;
+    if (w) {
+        unsigned int z = 0;
+        cudaMemcpyToSymbol(g_error_word, &z, sizeof(z));
+        return fail(SPH_EBOUNDS, "a kernel reported an out-of-range index (word 0x%x)", w);
+    }
+    return SPH_OK;
+}
+
+}  // extern "C"

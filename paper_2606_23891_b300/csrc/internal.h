@@ -1,0 +1,117 @@
+// Internal declarations of libsph: layout engine, task builder, device
+// records.  Not part of the public C-ABI (include/sph.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "sph.h"
+
+namespace sph {
+
+// Logical fields, in the order of the sph_fields struct; F_BALLAST stands for
+// the struct members no loop touches.
+enum FieldId {
+    F_X = 0, F_V, F_A, F_MASS, F_H, F_U, F_UDT, F_RHO, F_TBIN, F_AVISC,
+    F_ADIFF, F_RHODH, F_WCOUNT, F_WCOUNTDH, F_DIVV, F_ROTV, F_FGRADH, F_PRES,
+    F_CS, F_BALS, F_VSIGG, F_LAPU, F_HDT, F_VSIG, F_ID, F_BALLAST, F_NUM
+};
+
+enum TypeClass { T_DOUBLE = 0, T_FLOAT = 1, T_INT = 2 };
+
+struct FieldInfo {
+    int elem;   // bytes per component
+    int count;  // components
+    int cls;    // TypeClass
+};
+extern const FieldInfo kFields[F_NUM];
+
+struct Member {
+    int field;
+    int comp;    // -1: the whole field; >= 0: a single component (SoA)
+    int offset;  // byte offset inside the record
+};
+
+struct Group {
+    std::vector<Member> mem;
+    int record = 0;     // record bytes
+    int64_t base = 0;   // byte offset of the group's array inside the store
+};
+
+struct Layout {
+    int id = -1;
+    uint64_t seed = 0;
+    std::vector<Group> groups;
+};
+
+// Layout engine (layout.cpp).
+int build_layout(int layout, uint64_t seed, int64_t n, Layout *out);
+int64_t layout_bytes(const Layout &L, int64_t n);
+
+// Element address of (field, comp) of particle p: ptr + p * stride.
+struct CompPtr {
+    char *ptr;
+    long long stride;
+};
+bool locate(const Layout &L, char *mem, int field, int comp, CompPtr *out);
+
+// Error reporting (api.cu).
+int fail(int status, const char *fmt, ...);
+
+}  // namespace sph
+
+// One task as the kernels see it (24 bytes).  pi/ni: first particle (store
+// index) and count of cell ci; pj/nj the same for cj (nj = 0: self task).
+// slot: first slot of the task inside its bundle.  shift: periodic shift of
+// cj, per dimension (code + 1) in 2-bit fields (x: bits 0-1, y: 2-3, z: 4-5).
+struct TaskDev {
+    int32_t pi, ni, pj, nj, slot, shift;
+};
+
+// One cell of a bundle as the unpack kernel sees it: particles [p0, p0+n),
+// and ne entries at e0 (relative to the bundle's entry base), each the slot
+// of the cell's first particle in one task, in increasing task order.
+struct UCellDev {
+    int32_t p0, n, e0, ne;
+};
+
+struct sph_store_s {
+    int64_t n = 0;
+    sph::Layout layout;
+    char *mem = nullptr;
+    size_t bytes = 0;
+};
+
+struct sph_tasks_s {
+    int64_t n = 0;
+    int32_t ncell[3] = {0, 0, 0};
+    double box[3] = {0, 0, 0};
+    std::vector<int64_t> cell_start;    // ncells + 1
+    std::vector<int32_t> ci, cj;        // per task
+    std::vector<int8_t> shift;          // 3 per task
+    std::vector<int64_t> bundle_start;  // nbundles + 1
+    std::vector<int64_t> bundle_slots;  // per bundle
+    std::vector<TaskDev> tdev;          // per task (slot is bundle-relative)
+    std::vector<int64_t> ucell_begin;   // nbundles + 1, into ucells
+    std::vector<int64_t> entry_begin;   // nbundles + 1, into entries
+    std::vector<UCellDev> ucells;
+    std::vector<int32_t> entries;
+    int64_t max_cell = 0;
+    // device copies (sph_tasks_upload)
+    TaskDev *d_tasks = nullptr;
+    UCellDev *d_ucells = nullptr;
+    int32_t *d_entries = nullptr;
+    int device = -1;
+};
+
+namespace sph {
+int build_tasks(int64_t n, const double *x, const float *h,
+                const sph_grid_params *gp, int64_t *perm_out, sph_tasks_s *T);
+
+// Packed-buffer lanes of Sec. 2.3 buffers: sizes of each lane of `loop`
+// (in_or_out 0 = pack buffer, 1 = result buffer); returns the lane count.
+int lane_sizes(int loop, int in_or_out, int64_t *sizes);
+// Byte offsets of the lanes for S slots; returns the total bytes.
+int64_t lane_offsets(int loop, int in_or_out, int64_t S, int64_t *offsets);
+}  // namespace sph

@@ -1,0 +1,190 @@
+"""Drive the offload cycle of libsph over PyTorch-owned device memory.
+
+PyTorch only provides device memory, pinned host memory and streams; every
+step of the path (import into the store layout, pack, interaction kernels,
+unpack, ghost, export) is a libsph call.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import sph
+
+_TORCH_DT = {np.dtype(np.float64): torch.float64, np.dtype(np.float32): torch.float32,
+             np.dtype(np.int8): torch.int8, np.dtype(np.int64): torch.int64}
+_FIELD_DT = {"x": (np.float64, 3), "v": (np.float32, 3), "a": (np.float32, 3),
+             "rot_v": (np.float32, 3), "time_bin": (np.int8, 1), "id": (np.int64, 1)}
+INPUTS = ("x", "v", "mass", "h", "u", "alpha_visc", "alpha_diff", "time_bin", "id")
+OUTPUTS = ("rho", "rho_dh", "wcount", "wcount_dh", "div_v", "rot_v", "f_gradh",
+           "pressure", "soundspeed", "balsara", "v_sig_grad", "laplace_u", "a",
+           "u_dt", "h_dt", "v_sig")
+
+
+def field_spec(name: str):
+    dt, k = _FIELD_DT.get(name, (np.float32, 1))
+    return np.dtype(dt), k
+
+
+def fields_struct(tensors: dict) -> sph.Fields:
+    F = sph.Fields()
+    for name, t in tensors.items():
+        if t is None:
+            continue
+        if not t.is_contiguous():
+            raise ValueError("field %s must be contiguous" % name)
+        setattr(F, name, t.data_ptr())
+    return F
+
+
+class Offload:
+    """One particle set in a libsph store plus its task list and buffers."""
+
+    def __init__(self, fields: dict, layout="aos", seed: int = 0,
+                 box=(1.0, 1.0, 1.0), bundle_max_slots: int = 0,
+                 ncell=(0, 0, 0), params: sph.Params | None = None,
+                 device: str = "cuda", share: "Offload | None" = None):
+        """``share``: reuse another Offload's task list, permutation and
+        buffers (same particles, different store layout)."""
+        self.device = torch.device(device)
+        self.layout = sph.LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+        self.seed = seed
+        self.params = params or sph.params()
+        x = np.ascontiguousarray(fields["x"], np.float64)
+        self.n = n = x.shape[0]
+        self.box = tuple(float(b) for b in box)
+        self.owner = share is None
+        if share is None:
+            h = np.ascontiguousarray(fields["h"], np.float32)
+            gp = sph.grid_params(box, self.params.kernel_gamma, ncell, bundle_max_slots)
+            self.perm = np.empty(n, np.int64)
+            self.tasks = sph.sph_tasks_build(n, x.ctypes.data, h.ctypes.data, gp,
+                                             self.perm.ctypes.data)
+            sph.sph_tasks_upload(self.tasks)
+            self.info = sph.sph_tasks_info(self.tasks)
+            self.d_perm = torch.from_numpy(self.perm).to(self.device)
+            nin = max(sph.sph_buffer_bytes(self.tasks, l, 0) for l in range(3))
+            nout = max(sph.sph_buffer_bytes(self.tasks, l, 1) for l in range(3))
+            self.buf_in = torch.empty(max(nin, 256), dtype=torch.uint8, device=self.device)
+            self.buf_out = torch.empty(max(nout, 256), dtype=torch.uint8, device=self.device)
+        else:
+            self.perm, self.tasks, self.info = share.perm, share.tasks, share.info
+            self.d_perm, self.buf_in, self.buf_out = share.d_perm, share.buf_in, share.buf_out
+        self.nbytes = sph.sph_store_bytes(n, self.layout, seed)
+        self.mem = torch.empty(max(self.nbytes, 256), dtype=torch.uint8, device=self.device)
+        self.store = sph.sph_store_create(n, self.layout, seed, self.mem.data_ptr(),
+                                          self.nbytes)
+        self.import_fields(fields)
+
+    # -- plumbing --------------------------------------------------------
+    @property
+    def stream(self) -> int:
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def nbundles(self) -> int:
+        return self.info["nbundles"]
+
+    def import_fields(self, fields: dict, names=INPUTS) -> None:
+        dev = {}
+        for name in names:
+            if name not in fields:
+                continue
+            dt, k = field_spec(name)
+            arr = np.ascontiguousarray(fields[name], dt)
+            dev[name] = torch.from_numpy(arr).to(self.device)
+        sph.sph_store_import(self.store, fields_struct(dev), self.d_perm.data_ptr(),
+                             self.stream)
+        torch.cuda.synchronize(self.device)
+
+    def device_fields(self, names) -> dict:
+        out = {}
+        for name in names:
+            dt, k = field_spec(name)
+            shape = (self.n, k) if k > 1 else (self.n,)
+            out[name] = torch.empty(shape, dtype=_TORCH_DT[dt], device=self.device)
+        return out
+
+    def export(self, names=OUTPUTS) -> dict:
+        dev = self.device_fields(names)
+        sph.sph_store_export(self.store, fields_struct(dev), self.d_perm.data_ptr(),
+                             self.stream)
+        sph.sph_sync(self.stream)
+        return {k: v.cpu().numpy() for k, v in dev.items()}
+
+    def store_bytes(self) -> np.ndarray:
+        torch.cuda.synchronize(self.device)
+        return self.mem[: self.nbytes].cpu().numpy()
+
+    # -- the offload cycle ----------------------------------------------
+    def loop(self, loop: int) -> None:
+        sph.sph_offload_loop(self.store, self.tasks, loop, self.buf_in.data_ptr(),
+                             self.buf_out.data_ptr(), self.params, self.stream)
+
+    def step(self) -> None:
+        """density -> ghost -> gradient -> force over all bundles."""
+        for loop in (sph.SPH_DENSITY, sph.SPH_GRADIENT, sph.SPH_FORCE):
+            self.loop(loop)
+
+    def pack(self, loop: int, bundle: int) -> None:
+        sph.sph_pack(self.store, self.tasks, loop, bundle, self.buf_in.data_ptr(),
+                     self.stream)
+
+    def interact(self, loop: int, bundle: int) -> None:
+        fn = (sph.sph_density, sph.sph_gradient, sph.sph_force)[loop]
+        fn(self.tasks, bundle, self.buf_in.data_ptr(), self.buf_out.data_ptr(),
+           self.params, self.stream)
+
+    def unpack(self, loop: int, bundle: int) -> None:
+        sph.sph_unpack(self.store, self.tasks, loop, bundle, self.buf_out.data_ptr(),
+                       self.stream)
+
+    def count_pairs(self, loop: int) -> int:
+        """Pair interactions of `loop` (packs each bundle into buf_in)."""
+        cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
+        for b in range(self.nbundles()):
+            self.pack(loop, b)
+            sph.sph_count_pairs(self.tasks, loop, b, self.buf_in.data_ptr(), self.params,
+                                cnt.data_ptr(), self.stream)
+        sph.sph_sync(self.stream)
+        return int(cnt.item())
+
+    def bundle_slots(self, bundle: int) -> int:
+        bs = self.bundle_starts()
+        return int(self.slot_counts()[bs[bundle]:bs[bundle + 1]].sum())
+
+    def task_list(self):
+        nt = self.info["ntasks"]
+        ncell = self.info["ncell_x"] * self.info["ncell_y"] * self.info["ncell_z"]
+        ci = np.empty(nt, np.int32)
+        cj = np.empty(nt, np.int32)
+        sh = np.empty((nt, 3), np.int8)
+        cs = np.empty(ncell + 1, np.int64)
+        bs = np.empty(self.info["nbundles"] + 1, np.int64)
+        sph.sph_tasks_get(self.tasks, ci.ctypes.data, cj.ctypes.data, sh.ctypes.data,
+                          cs.ctypes.data, bs.ctypes.data)
+        return ci, cj, sh, cs, bs
+
+    def bundle_starts(self):
+        return self.task_list()[4]
+
+    def slot_counts(self):
+        ci, cj, sh, cs, bs = self.task_list()
+        cnt = np.diff(cs)
+        return cnt[ci] + np.where(cj >= 0, cnt[np.maximum(cj, 0)], 0)
+
+    def close(self) -> None:
+        if getattr(self, "store", None) is not None:
+            sph.sph_store_destroy(self.store)
+            self.store = None
+        if getattr(self, "tasks", None) is not None:
+            if self.owner:
+                sph.sph_tasks_destroy(self.tasks)
+            self.tasks = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,240 @@
+"""ctypes binding of libsph.so (include/sph.h): argument marshalling only.
+
+Every function has the C name and raises :class:`SphError` with the library's
+message when the status is not SPH_OK.  Device pointers are plain integers
+(e.g. ``tensor.data_ptr()``); streams are ``torch.cuda.Stream.cuda_stream``
+integers or 0.  There is no fallback: if the library is missing, importing
+fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsph.so")
+
+SPH_AOS, SPH_AOS_RANDOM, SPH_SAOS_PACK_GRAD, SPH_SAOS_PACK_FORCE, \
+    SPH_SAOS_PACK_SHARED, SPH_SAOS_PACK_GRAD_TYPE, SPH_SAOS_PACK_FORCE_TYPE, \
+    SPH_SAOS_PACK_SHARED_TYPE, SPH_SOA = range(9)
+LAYOUTS = {"aos": 0, "aos_random": 1, "pack_grad": 2, "pack_force": 3,
+           "pack_shared": 4, "pack_grad_type": 5, "pack_force_type": 6,
+           "pack_shared_type": 7, "soa": 8}
+SPH_DENSITY, SPH_GRADIENT, SPH_FORCE = 0, 1, 2
+LOOPS = {"density": 0, "gradient": 1, "force": 2}
+STATUS = {0: "SPH_OK", 1: "SPH_EINVAL", 2: "SPH_ENOMEM", 3: "SPH_ECUDA",
+          4: "SPH_EBOUNDS", 5: "SPH_ETIMEOUT", 6: "SPH_EUNSUPPORTED"}
+
+FIELD_NAMES = ("x", "v", "a", "mass", "h", "u", "u_dt", "rho", "time_bin",
+               "alpha_visc", "alpha_diff", "rho_dh", "wcount", "wcount_dh",
+               "div_v", "rot_v", "f_gradh", "pressure", "soundspeed", "balsara",
+               "v_sig_grad", "laplace_u", "h_dt", "v_sig", "id")
+
+
+class SphError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Fields(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in FIELD_NAMES]
+
+
+class Params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("kernel_gamma", C.c_double),
+                ("beta_visc", C.c_double), ("balsara_eps", C.c_double),
+                ("active_bin", C.c_int32), ("reserved", C.c_int32)]
+
+
+class GridParams(C.Structure):
+    _fields_ = [("box", C.c_double * 3), ("kernel_gamma", C.c_double),
+                ("ncell", C.c_int32 * 3), ("reserved", C.c_int32),
+                ("bundle_max_slots", C.c_int64)]
+
+
+def params(gamma=5.0 / 3.0, kernel_gamma=1.825742, beta_visc=3.0,
+           balsara_eps=1e-4, active_bin=0) -> Params:
+    return Params(gamma, kernel_gamma, beta_visc, balsara_eps, active_bin, 0)
+
+
+def grid_params(box=(1.0, 1.0, 1.0), kernel_gamma=1.825742, ncell=(0, 0, 0),
+                bundle_max_slots=0) -> GridParams:
+    g = GridParams()
+    g.box[:] = list(box)
+    g.kernel_gamma = kernel_gamma
+    g.ncell[:] = list(ncell)
+    g.reserved = 0
+    g.bundle_max_slots = bundle_max_slots
+    return g
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libsph.so is not built; run "
+                          "`python -m paper_2606_23891_b300.build`")
+    L = C.CDLL(LIB_PATH)
+    p, i, i64, u64, sz = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_size_t
+    sig = {
+        "sph_version": (C.c_char_p, []),
+        "sph_last_error": (C.c_char_p, []),
+        "sph_store_bytes": (sz, [i64, i, u64]),
+        "sph_layout_group_count": (i, [i, u64]),
+        "sph_layout_describe": (i, [i, u64, i, p, p, p, p, p]),
+        "sph_store_create": (i, [i64, i, u64, p, sz, p]),
+        "sph_store_destroy": (i, [p]),
+        "sph_store_import": (i, [p, p, p, p]),
+        "sph_store_export": (i, [p, p, p, p]),
+        "sph_tasks_build": (i, [i64, p, p, p, p, p]),
+        "sph_tasks_upload": (i, [p]),
+        "sph_tasks_info": (i, [p, p]),
+        "sph_tasks_get": (i, [p, p, p, p, p, p]),
+        "sph_buffer_bytes": (sz, [p, i, i]),
+        "sph_init": (i, [p, i, p, p]),
+        "sph_pack": (i, [p, p, i, i, p, p]),
+        "sph_density": (i, [p, i, p, p, p, p]),
+        "sph_gradient": (i, [p, i, p, p, p, p]),
+        "sph_force": (i, [p, i, p, p, p, p]),
+        "sph_unpack": (i, [p, p, i, i, p, p]),
+        "sph_ghost": (i, [p, i, p, p]),
+        "sph_offload_loop": (i, [p, p, i, p, p, p, p]),
+        "sph_count_pairs": (i, [p, i, i, p, p, p, p]),
+        "sph_sync": (i, [p]),
+        "sph_tasks_destroy": (i, [p]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ok(rc: int) -> None:
+    if rc != 0:
+        raise SphError(rc, lib().sph_last_error().decode())
+
+
+def sph_version() -> str:
+    return lib().sph_version().decode()
+
+
+def sph_last_error() -> str:
+    return lib().sph_last_error().decode()
+
+
+def sph_store_bytes(n: int, layout: int, seed: int = 0) -> int:
+    return lib().sph_store_bytes(n, layout, seed)
+
+
+def sph_layout_group_count(layout: int, seed: int = 0) -> int:
+    return lib().sph_layout_group_count(layout, seed)
+
+
+def sph_layout_describe(layout: int, seed: int, group: int):
+    """(record_bytes, [(field_id, comp, offset), ...])"""
+    nm = C.c_int32()
+    fl, co, of = (C.c_int32 * 32)(), (C.c_int32 * 32)(), (C.c_int32 * 32)()
+    rec = C.c_int32()
+    _ok(lib().sph_layout_describe(layout, seed, group, C.byref(nm), fl, co, of,
+                                  C.byref(rec)))
+    return rec.value, [(fl[k], co[k], of[k]) for k in range(nm.value)]
+
+
+def sph_store_create(n: int, layout: int, seed: int, dev_mem: int, nbytes: int):
+    h = C.c_void_p()
+    _ok(lib().sph_store_create(n, layout, seed, dev_mem, nbytes, C.byref(h)))
+    return h
+
+
+def sph_store_destroy(s) -> None:
+    _ok(lib().sph_store_destroy(s))
+
+
+def sph_store_import(s, fields: Fields, dev_perm: int, stream: int = 0) -> None:
+    _ok(lib().sph_store_import(s, C.byref(fields), dev_perm, stream))
+
+
+def sph_store_export(s, fields: Fields, dev_perm: int, stream: int = 0) -> None:
+    _ok(lib().sph_store_export(s, C.byref(fields), dev_perm, stream))
+
+
+def sph_tasks_build(n: int, host_x: int, host_h: int, gp: GridParams,
+                    host_perm_out: int):
+    h = C.c_void_p()
+    _ok(lib().sph_tasks_build(n, host_x, host_h, C.byref(gp), host_perm_out,
+                              C.byref(h)))
+    return h
+
+
+def sph_tasks_upload(t) -> None:
+    _ok(lib().sph_tasks_upload(t))
+
+
+def sph_tasks_info(t) -> dict:
+    info = (C.c_int64 * 10)()
+    _ok(lib().sph_tasks_info(t, info))
+    keys = ("ncell_x", "ncell_y", "ncell_z", "ntasks", "nbundles", "slots",
+            "max_bundle_slots", "nonempty_cells", "n", "max_cell")
+    return dict(zip(keys, list(info)))
+
+
+def sph_tasks_get(t, ci=0, cj=0, shift=0, cell_start=0, bundle_start=0) -> None:
+    _ok(lib().sph_tasks_get(t, ci or None, cj or None, shift or None,
+                            cell_start or None, bundle_start or None))
+
+
+def sph_buffer_bytes(t, loop: int, in_or_out: int) -> int:
+    return lib().sph_buffer_bytes(t, loop, in_or_out)
+
+
+def sph_init(s, loop: int, p: Params, stream: int = 0) -> None:
+    _ok(lib().sph_init(s, loop, C.byref(p), stream))
+
+
+def sph_pack(s, t, loop: int, bundle: int, dev_buf_in: int, stream: int = 0) -> None:
+    _ok(lib().sph_pack(s, t, loop, bundle, dev_buf_in, stream))
+
+
+def sph_density(t, bundle: int, dev_in: int, dev_out: int, p: Params, stream: int = 0):
+    _ok(lib().sph_density(t, bundle, dev_in, dev_out, C.byref(p), stream))
+
+
+def sph_gradient(t, bundle: int, dev_in: int, dev_out: int, p: Params, stream: int = 0):
+    _ok(lib().sph_gradient(t, bundle, dev_in, dev_out, C.byref(p), stream))
+
+
+def sph_force(t, bundle: int, dev_in: int, dev_out: int, p: Params, stream: int = 0):
+    _ok(lib().sph_force(t, bundle, dev_in, dev_out, C.byref(p), stream))
+
+
+def sph_unpack(s, t, loop: int, bundle: int, dev_buf_out: int, stream: int = 0) -> None:
+    _ok(lib().sph_unpack(s, t, loop, bundle, dev_buf_out, stream))
+
+
+def sph_ghost(s, after_loop: int, p: Params, stream: int = 0) -> None:
+    _ok(lib().sph_ghost(s, after_loop, C.byref(p), stream))
+
+
+def sph_offload_loop(s, t, loop: int, dev_in: int, dev_out: int, p: Params,
+                     stream: int = 0) -> None:
+    _ok(lib().sph_offload_loop(s, t, loop, dev_in, dev_out, C.byref(p), stream))
+
+
+def sph_count_pairs(t, loop: int, bundle: int, dev_in: int, p: Params,
+                    dev_count: int, stream: int = 0) -> None:
+    _ok(lib().sph_count_pairs(t, loop, bundle, dev_in, C.byref(p), dev_count, stream))
+
+
+def sph_sync(stream: int = 0) -> None:
+    _ok(lib().sph_sync(stream))
+
+
+def sph_tasks_destroy(t) -> None:
+    _ok(lib().sph_tasks_destroy(t))
