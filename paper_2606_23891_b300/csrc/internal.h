@@ -64,7 +64,8 @@ int fail(int status, const char *fmt, ...);
 // One task as the kernels see it (24 bytes).  pi/ni: first particle (store
 // index) and count of cell ci; pj/nj the same for cj (nj = 0: self task).
 // slot: first slot of the task inside its bundle.  shift: periodic shift of
-// cj, per dimension (code + 1) in 2-bit fields (x: bits 0-1, y: 2-3, z: 4-5).
+// cj, per dimension (code + 1) in 2-bit fields (x: bits 0-1, y: 2-3, z: 4-5);
+// bits 6-11 hold the cell offset d from ci to cj the same way (0 for self).
 struct TaskDev {
     int32_t pi, ni, pj, nj, slot, shift;
 };

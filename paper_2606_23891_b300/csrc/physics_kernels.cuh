@@ -28,8 +28,25 @@ struct PhysArgs {
     unsigned long long *count;
 };
 
-constexpr int kThreads = 128;
+// Compile-time tuning knobs (defaults are the tuned configuration).
+#ifndef SPH_KTHREADS
+#define SPH_KTHREADS 128
+#endif
+#ifndef SPH_MINB_DENSITY
+#define SPH_MINB_DENSITY 1
+#endif
+#ifndef SPH_MINB_GRADIENT
+#define SPH_MINB_GRADIENT 1
+#endif
+#ifndef SPH_MINB_FORCE
+#define SPH_MINB_FORCE 8
+#endif
+#ifndef SPH_KCHUNK
+#define SPH_KCHUNK 128
+#endif
+constexpr int kThreads = SPH_KTHREADS;
 constexpr int kCap = 256;
+constexpr int kPad = 32;
 
 template <int LOOP>
 struct NF {
@@ -231,34 +248,55 @@ struct Acc<SPH_FORCE> {
 // separations and records hits as a per-lane bitmask; pass 2 visits only the
 // hits, so a warp runs the pair body about max-over-lanes-of-hits times
 // instead of once for every j that any lane accepts.
-constexpr int kChunk = 128;  // candidates per bitmask pass
+constexpr int kChunk = SPH_KCHUNK;  // candidates per bitmask pass (<= 4 words)
+static_assert(kChunk % 32 == 0 && kChunk <= 128, "bitmask chunk is 1..4 words");
 
+// Pass-1 test of one word (up to 32 candidates j0 .. j0+jn-1): bit b set if
+// the hi-only separation passes the widened support test.
+// The shared arrays carry one spare word (kPad) so a word may always be read
+// whole; bits past jn are masked (their values are never used).
+template <int LOOP>
+__device__ __forceinline__ unsigned int test_word(const float4 (*sm)[kCap + kPad], int j0,
+                                                  int jn, const float4 *own,
+                                                  const Acc<LOOP> &acc) {
+    unsigned int m = 0;
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+        const float4 pj = sm[0][j0 + b];
+        const float dx = own[0].x - pj.x, dy = own[0].y - pj.y, dz = own[0].z - pj.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        m |= acc.pre(r2, pj) ? (1u << b) : 0u;
+    }
+    return jn < 32 ? m & ((1u << jn) - 1u) : m;
+}
+
+// One i against j in [jb, je) (at most kChunk) of a staged tile, skipping
+// tile index `skip` (self task).  Pass 1 tests every candidate on hi-only
+// separations and records hits as a per-lane bitmask; pass 2 visits only the
+// hits, so a warp runs the pair body about max-over-lanes-of-hits times
+// instead of once for every j that any lane accepts.  Loops over the mask
+// words are not unrolled so the pair body is emitted once (instruction-cache
+// footprint).
 template <int LOOP, bool COUNT>
-__device__ __forceinline__ void sweep_chunk(const float4 (*sm)[kCap], int jb, int je, int skip,
+__device__ __forceinline__ void sweep_chunk(const float4 (*sm)[kCap + kPad], int jb, int je, int skip,
                                             const float4 *own, Acc<LOOP> &acc,
                                             unsigned int &cnt, const PhysArgs &a) {
     constexpr int nf = NF<LOOP>::value;
-    constexpr int kWords = kChunk / 32;
-    unsigned int mask[kWords];
-#pragma unroll
-    for (int w = 0; w < kWords; ++w) {
-        unsigned int m = 0;
+    unsigned int m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+#pragma unroll 1
+    for (int w = 0; w < kChunk / 32; ++w) {
         const int j0 = jb + 32 * w;
-        if (j0 < je) {
-            const int jn = min(32, je - j0);
-            for (int b = 0; b < jn; ++b) {
-                const float4 pj = sm[0][j0 + b];
-                const float dx = own[0].x - pj.x, dy = own[0].y - pj.y, dz = own[0].z - pj.z;
-                const float r2 = dx * dx + dy * dy + dz * dz;
-                if (acc.pre(r2, pj)) m |= 1u << b;
-            }
-            if (skip >= j0 && skip < j0 + 32) m &= ~(1u << (skip - j0));
-        }
-        mask[w] = m;
+        if (j0 >= je) break;
+        unsigned int m = test_word<LOOP>(sm, j0, min(32, je - j0), own, acc);
+        if (skip >= j0 && skip < j0 + 32) m &= ~(1u << (skip - j0));
+        if (w == 0) m0 = m;
+        else if (w == 1) m1 = m;
+        else if (w == 2) m2 = m;
+        else m3 = m;
     }
-#pragma unroll
-    for (int w = 0; w < kWords; ++w) {
-        unsigned int m = mask[w];
+#pragma unroll 1
+    for (int w = 0; w < kChunk / 32; ++w) {
+        unsigned int m = w == 0 ? m0 : (w == 1 ? m1 : (w == 2 ? m2 : m3));
         while (m) {
             const int j = jb + 32 * w + (__ffs(m) - 1);
             m &= m - 1;
@@ -280,11 +318,21 @@ __device__ __forceinline__ void sweep_chunk(const float4 (*sm)[kCap], int jb, in
 }
 
 template <int LOOP, bool COUNT>
-__device__ __forceinline__ void sweep(const float4 (*sm)[kCap], int jb, int je, int skip,
+__device__ __forceinline__ void sweep(const float4 (*sm)[kCap + kPad], int jb, int je, int skip,
                                       const float4 *own, Acc<LOOP> &acc,
                                       unsigned int &cnt, const PhysArgs &a) {
+#pragma unroll 1
     for (int j0 = jb; j0 < je; j0 += kChunk)
         sweep_chunk<LOOP, COUNT>(sm, j0, min(j0 + kChunk, je), skip, own, acc, cnt, a);
+}
+
+// Out-of-line copy for the rare tiled path (cells of more than kCap / 2
+// particles), so the common path keeps the only inlined pair body.
+template <int LOOP, bool COUNT>
+__device__ __noinline__ void sweep_tiled(const float4 (*sm)[kCap + kPad], int jn, int skip,
+                                         const float4 *own, Acc<LOOP> *acc,
+                                         unsigned int *cnt, const PhysArgs *a) {
+    sweep<LOOP, COUNT>(sm, 0, jn, skip, own, *acc, *cnt, *a);
 }
 
 template <int LOOP, bool COUNT>
@@ -305,42 +353,225 @@ __device__ __forceinline__ bool is_active(const PhysArgs &a, long long s) {
     return (int)reinterpret_cast<const int8_t *>(a.in[11])[s] <= a.active_bin;
 }
 
+// ---- projection binning of pair tasks -------------------------------------
+// In a pair task every accepted j lies within |d| R of i along the cell
+// offset d (R the support bound), and cj lies strictly beyond ci along every
+// non-zero component of d.  Both cells are therefore sorted by their
+// projection s = d . x into kBins bins (stable counting sort with warp
+// ballots: deterministic), lanes take particles in sorted order, and each
+// warp sweeps only a prefix of cj (lanes of ci: s_j <= s_i + R) or a suffix
+// of ci (lanes of cj: s_j >= s_i - R).
+constexpr int kBins = 16;
+static_assert(kCap <= 2 * kThreads, "staging holds two slots per thread");
+
+constexpr int kChunks = kCap / 32;   // 32-element chunks of a staged task
+constexpr int kKeys = 2 * kBins;     // (side, bin)
+
+struct SortSmem {
+    float smin[kThreads / 32], smax[kThreads / 32], hmax[2][kThreads / 32];
+    int hist[kKeys * kChunks];       // count of key in chunk, then its start
+    short pos[kCap];
+    short orig[kCap];
+    int binstart[2][kBins + 1];
+};
+
+__device__ __forceinline__ int bin_of(float s, float s0, float inv_w) {
+    const float f = (s - s0) * inv_w;
+    return f <= 0.f ? 0 : (f >= (float)(kBins - 1) ? kBins - 1 : (int)f);
+}
+
+// Stable counting sort of the task's slots by key = (side, bin), all warps:
+// chunk c = k / 32 is handled by the warp holding it; equal keys inside a
+// chunk are ranked by lane with __match_any_sync, and chunk counts are
+// scanned in (key, chunk) order.  Deterministic; side 0 lands in [0, ni),
+// side 1 in [ni, n).
+__device__ __forceinline__ void block_sort(SortSmem &S, int n, int ni, int nj,
+                                           const int *key, int nk) {
+    const int lane = threadIdx.x & 31;
+    const unsigned int lt = (1u << lane) - 1u;
+    int rank[2] = {0, 0};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (q >= nk) break;
+        const int k = threadIdx.x + q * kThreads;
+        if (k - lane >= n) continue;  // whole chunk empty (warp-uniform)
+        const int kk = k < n ? key[q] : kKeys + lane;  // unique sentinel
+        const unsigned int peers = __match_any_sync(0xffffffffu, kk);
+        rank[q] = __popc(peers & lt);
+        if (k < n && rank[q] == 0) S.hist[kk * kChunks + (k >> 5)] = __popc(peers);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // exclusive scan of hist (kKeys * kChunks entries, 8 per lane)
+        constexpr int per = kKeys * kChunks / 32;
+        int v[per], t = 0;
+#pragma unroll
+        for (int e = 0; e < per; ++e) {
+            v[e] = S.hist[lane * per + e];
+            t += v[e];
+        }
+        int incl = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        int run = incl - t;
+#pragma unroll
+        for (int e = 0; e < per; ++e) {
+            S.hist[lane * per + e] = run;
+            run += v[e];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kKeys) {
+        const int side = threadIdx.x / kBins, b = threadIdx.x % kBins;
+        S.binstart[side][b] = S.hist[threadIdx.x * kChunks] - (side ? ni : 0);
+    }
+    if (threadIdx.x == 0) {
+        S.binstart[0][kBins] = ni;
+        S.binstart[1][kBins] = nj;
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (q >= nk) break;
+        const int k = threadIdx.x + q * kThreads;
+        if (k < n) S.pos[k] = (short)(S.hist[key[q] * kChunks + (k >> 5)] + rank[q]);
+    }
+}
+
 template <int LOOP, bool COUNT>
-__global__ void __launch_bounds__(kThreads) k_interact(PhysArgs a) {
+__global__ void __launch_bounds__(kThreads, LOOP == SPH_FORCE ? SPH_MINB_FORCE
+                                            : (LOOP == SPH_GRADIENT ? SPH_MINB_GRADIENT
+                                                                    : SPH_MINB_DENSITY))
+    k_interact(PhysArgs a) {
     constexpr int nf = NF<LOOP>::value;
-    __shared__ float4 sm[nf][kCap];
+    __shared__ float4 sm[nf][kCap + kPad];
+    __shared__ SortSmem S;
     const TaskDev T = a.tasks[blockIdx.x];
     const int ni = T.ni, nj = T.nj, n = ni + nj;
     const long long base = T.slot;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned int cnt = 0;
 
     if (n <= kCap) {
+        // ---- pair tasks: projection keys and a stable sort by bin ----------
+        // (a light pass: positions and h only; each thread owns slots k0, k1)
+        const int k0 = threadIdx.x, k1 = threadIdx.x + kThreads;
+        float dn = 0.f, s_lo = 0.f, inv_w = 0.f, hm0 = 0.f, hm1 = 0.f;
+        float dx = 0.f, dy = 0.f, dz = 0.f;
+        if (nj > 0) {
+            const int code = T.shift >> 6;
+            dx = (float)((code & 3) - 1);
+            dy = (float)(((code >> 2) & 3) - 1);
+            dz = (float)(((code >> 4) & 3) - 1);
+            dn = sqrtf(dx * dx + dy * dy + dz * dz);
+            float sk[2] = {0.f, 0.f};
+            float mn = INFINITY, mx = -INFINITY, h0 = 0.f, h1 = 0.f;
+            for (int e = threadIdx.x; e < kKeys * kChunks; e += kThreads) S.hist[e] = 0;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int k = q ? k1 : k0;
+                if (k >= n) continue;
+                float hx, hy, hz, lo;
+                split_f64(reinterpret_cast<const double *>(a.in[0])[base + k], hx, lo);
+                split_f64(reinterpret_cast<const double *>(a.in[1])[base + k], hy, lo);
+                split_f64(reinterpret_cast<const double *>(a.in[2])[base + k], hz, lo);
+                sk[q] = dx * hx + dy * hy + dz * hz;
+                mn = fminf(mn, sk[q]);
+                mx = fmaxf(mx, sk[q]);
+                if (LOOP == SPH_FORCE) {
+                    const float H = a.kernel_gamma * reinterpret_cast<const float *>(a.in[4])[base + k];
+                    if (k < ni) h0 = fmaxf(h0, H); else h1 = fmaxf(h1, H);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+                h0 = fmaxf(h0, __shfl_xor_sync(0xffffffffu, h0, o));
+                h1 = fmaxf(h1, __shfl_xor_sync(0xffffffffu, h1, o));
+            }
+            if (lane == 0) {
+                S.smin[warp] = mn; S.smax[warp] = mx;
+                S.hmax[0][warp] = h0; S.hmax[1][warp] = h1;
+            }
+            __syncthreads();
+            mn = S.smin[0]; mx = S.smax[0]; h0 = S.hmax[0][0]; h1 = S.hmax[1][0];
+#pragma unroll
+            for (int w = 1; w < kThreads / 32; ++w) {
+                mn = fminf(mn, S.smin[w]); mx = fmaxf(mx, S.smax[w]);
+                h0 = fmaxf(h0, S.hmax[0][w]); h1 = fmaxf(h1, S.hmax[1][w]);
+            }
+            s_lo = mn;
+            inv_w = mx > mn ? (float)kBins / (mx - mn) : 0.f;
+            hm0 = h0;
+            hm1 = h1;
+            int key[2];
+            key[0] = (k0 < ni ? 0 : kBins) + bin_of(sk[0], s_lo, inv_w);
+            key[1] = (k1 < ni ? 0 : kBins) + bin_of(sk[1], s_lo, inv_w);
+            block_sort(S, n, ni, nj, key, 2);
+            __syncthreads();
+        }
+        // ---- stage full records at their sorted positions -----------------
         for (int k = threadIdx.x; k < n; k += kThreads) {
             float4 r[nf];
             load_slot<LOOP>(a, base + k, r);
+            const int pk = nj > 0 ? S.pos[k] : k;
 #pragma unroll
-            for (int f = 0; f < nf; ++f) sm[f][k] = r[f];
+            for (int f = 0; f < nf; ++f) sm[f][pk] = r[f];
+            S.orig[pk] = (short)k;
         }
         __syncthreads();
+
+        // ---- sweep: lanes over sorted positions, warp-uniform sides --------
         const int ri = (ni + 31) & ~31;
         const int V = nj ? ri + ((nj + 31) & ~31) : ri;
         for (int v = threadIdx.x; v < V; v += kThreads) {
             const bool side = v >= ri;
             const int k = side ? v - ri : v;
-            if (k >= (side ? nj : ni)) continue;
+            const bool valid = k < (side ? nj : ni);
             const int i = side ? ni + k : k;
-            const bool active = is_active<LOOP>(a, base + i);
             float4 own[nf];
-#pragma unroll
-            for (int f = 0; f < nf; ++f) own[f] = sm[f][i];
             Acc<LOOP> acc;
-            acc.init(own, a.delta);
-            if (active) {
-                if (nj == 0) sweep<LOOP, COUNT>(sm, 0, ni, i, own, acc, cnt, a);
-                else if (side) sweep<LOOP, COUNT>(sm, 0, ni, -1, own, acc, cnt, a);
-                else sweep<LOOP, COUNT>(sm, ni, n, -1, own, acc, cnt, a);
+            bool active = false;
+            long long slot = 0;
+            int jb, je;
+            if (nj == 0) {
+                jb = 0;
+                je = ni;
+            } else {
+                jb = side ? 0 : ni;
+                je = side ? ni : n;
             }
-            finish<LOOP, COUNT>(a, base + i, own, acc, active);
+            if (valid) {
+#pragma unroll
+                for (int f = 0; f < nf; ++f) own[f] = sm[f][i];
+                slot = base + (nj ? S.orig[i] : i);
+                active = is_active<LOOP>(a, slot);
+                acc.init(own, a.delta);
+            }
+            if (nj > 0) {
+                // window of this lane along d, then the warp's union
+                int lim = side ? ni : ni;  // empty for invalid / inactive lanes
+                if (valid && active) {
+                    const float Hs = LOOP == SPH_FORCE ? fmaxf(1.f / own[4].z, side ? hm0 : hm1)
+                                                       : own[0].w;
+                    const float R = dn * (Hs + a.delta);
+                    const float si = dx * own[0].x + dy * own[0].y + dz * own[0].z;
+                    if (!side) {
+                        lim = ni + S.binstart[1][bin_of(si + R, s_lo, inv_w) + 1];
+                    } else {
+                        lim = S.binstart[0][bin_of(si - R, s_lo, inv_w)];
+                    }
+                }
+                if (!side) je = __reduce_max_sync(0xffffffffu, lim);
+                else jb = __reduce_min_sync(0xffffffffu, lim);
+            }
+            if (valid && active) {
+                sweep<LOOP, COUNT>(sm, jb, je, nj == 0 ? i : -1, own, acc, cnt, a);
+            }
+            if (valid) finish<LOOP, COUNT>(a, slot, own, acc, active);
         }
     } else {
         // tiled path: phases (i-range, j-range), j streamed in kCap tiles
@@ -370,7 +601,7 @@ __global__ void __launch_bounds__(kThreads) k_interact(PhysArgs a) {
                     }
                     __syncthreads();
                     if (valid && active)
-                        sweep<LOOP, COUNT>(sm, 0, jn, nj ? -1 : i - j0, own, acc, cnt, a);
+                        sweep_tiled<LOOP, COUNT>(sm, jn, nj ? -1 : i - j0, own, &acc, &cnt, &a);
                 }
                 if (valid) finish<LOOP, COUNT>(a, base + i, own, acc, active);
             }

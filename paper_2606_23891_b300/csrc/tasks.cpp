@@ -146,6 +146,20 @@ int build_tasks(int64_t n, const double *x, const float *h,
         td.slot = (int32_t)slots;
         td.shift = (T->shift[3 * t] + 1) | ((T->shift[3 * t + 1] + 1) << 2) |
                    ((T->shift[3 * t + 2] + 1) << 4);
+        if (T->cj[t] >= 0) {
+            // offset from ci to cj in cells (unwrapped): bits 6-11
+            const int64_t a = T->ci[t], b = T->cj[t];
+            const int64_t ca[3] = {a % nc[0], (a / nc[0]) % nc[1], a / ((int64_t)nc[0] * nc[1])};
+            const int64_t cb[3] = {b % nc[0], (b / nc[0]) % nc[1], b / ((int64_t)nc[0] * nc[1])};
+            int code = 0;
+            for (int d = 0; d < 3; ++d) {
+                const int64_t off = cb[d] - ca[d] + (int64_t)T->shift[3 * t + d] * nc[d];
+                code |= (int)(off + 1) << (2 * d);
+            }
+            td.shift |= code << 6;
+        } else {
+            td.shift |= (1 | (1 << 2) | (1 << 4)) << 6;
+        }
         slots += s;
     }
     if (ntasks > 0) {
