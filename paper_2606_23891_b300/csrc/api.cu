@@ -506,6 +506,9 @@ int sph_sync(void *stream) {
     if (w) {
         unsigned int z = 0;
         cudaMemcpyToSymbol(g_error_word, &z, sizeof(z));
+        if (w & 2u)
+            return fail(SPH_ETIMEOUT, "a kernel's bounded wait for its copies ran out (word 0x%x)",
+                        w);
         return fail(SPH_EBOUNDS, "a kernel reported an out-of-range index (word 0x%x)", w);
     }
     return SPH_OK;

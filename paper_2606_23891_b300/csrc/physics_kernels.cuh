@@ -33,16 +33,16 @@ struct PhysArgs {
 #define SPH_KTHREADS 128
 #endif
 #ifndef SPH_MINB_DENSITY
-#define SPH_MINB_DENSITY 1
+#define SPH_MINB_DENSITY 8
 #endif
 #ifndef SPH_MINB_GRADIENT
-#define SPH_MINB_GRADIENT 1
+#define SPH_MINB_GRADIENT 8
 #endif
 #ifndef SPH_MINB_FORCE
 #define SPH_MINB_FORCE 8
 #endif
 #ifndef SPH_KCHUNK
-#define SPH_KCHUNK 128
+#define SPH_KCHUNK 64
 #endif
 constexpr int kThreads = SPH_KTHREADS;
 constexpr int kCap = 256;
