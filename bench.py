@@ -45,9 +45,10 @@ FLOPS_CANDIDATE = 8
 FLOPS_PAIR = (73, 52, 113)
 # FP32 CUDA-core peak: 148 SMs x 128 lanes x 2 flop x 2.032 GHz
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
-# DRAM bytes per launch of the interaction kernels from an ncu capture, valid
-# only for the kernel source with this digest (else reported as null)
-NCU_TRAFFIC = {}
+# DRAM bytes per slot of the interaction kernels from an ncu capture of a
+# smaller case (traffic grows with the slots a launch processes), valid only
+# for the kernel source with this digest (else reported as null)
+NCU_TRAFFIC = {("kernel", 2): {"bytes_per_slot": 92.1, "src": "e4b699e728bdf76e"}}
 GPU_KERNEL_SRC = os.path.join(ROOT, "paper_2606_23891_b300", "csrc", "physics_kernels.cuh")
 
 
@@ -345,8 +346,7 @@ def run_ours(args, ws, rank, local):
                 "pack_GBps": pack_b / (pk * 1e-3) / 1e9,
                 "unpack_GBps": unpack_b / (up * 1e-3) / 1e9,
                 "pair_interactions_per_s": pairs[l] / ((pk + kr + up) * 1e-3),
-                "kernel_fp32_TFLOPs": (ncand * FLOPS_CANDIDATE + pairs[l] * FLOPS_PAIR[l])
-                / (kr * 1e-3) / 1e12,
+                "kernel_useful_fp32_TFLOPs": pairs[l] * FLOPS_PAIR[l] / (kr * 1e-3) / 1e12,
             }
         per_layout[lname] = {"ms_per_step": ms_step,
                              "pair_interactions_per_s": sum(pairs) * ws / (ms_step * 1e-3),
@@ -363,21 +363,29 @@ def run_ours(args, ws, rank, local):
     # dominant kernel of the headline layout
     top = max(st, key=lambda k: st[k])
     stage, loop = top
-    launches = cnt[loop]
-    dur = st[top] / launches                      # ms per launch
+    per_step = cnt[loop] / args.steps             # launches per step (bundles)
+    dur = st[top] / cnt[loop]                     # ms per launch
     peaks = measured_peaks()
     if stage == "kernel":
-        flops = (ncand * FLOPS_CANDIDATE + pairs[loop] * FLOPS_PAIR[loop]) / launches
+        # useful FP32 work only: accepted pairs x the pair body; the candidate
+        # tests of the cell pairs (most skipped by the projection windows) are
+        # reported beside it, not counted as achieved work
+        flops = pairs[loop] * FLOPS_PAIR[loop] / per_step
         achieved = flops / (dur * 1e-3) / 1e12
         tr = NCU_TRAFFIC.get((stage, loop))
-        traffic = tr["bytes"] if tr and tr["src"] == src_digest() else None
+        traffic = (tr["bytes_per_slot"] * slots / per_step
+                   if tr and tr["src"] == src_digest() else None)
         roof = {"kernel": "interaction/%s" % LOOP_NAMES[loop], "bound": "alu",
                 "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"}
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
+                "with_cell_pair_candidates_TFLOPs":
+                    (ncand * FLOPS_CANDIDATE + pairs[loop] * FLOPS_PAIR[loop]) / per_step
+                    / (dur * 1e-3) / 1e12,
+                "hbm_GBps": (traffic / (dur * 1e-3) / 1e9) if traffic else None}
     else:
         bpl = (slots * 2 * VIEW_IN[loop] if stage == "pack"
-               else slots * VIEW_OUT[loop] + n * 2 * VIEW_OUT[loop]) / launches
+               else slots * VIEW_OUT[loop] + n * 2 * VIEW_OUT[loop]) / per_step
         achieved = bpl / (dur * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6400.0)
         roof = {"kernel": "%s/%s" % (stage, LOOP_NAMES[loop]), "bound": "hbm",
