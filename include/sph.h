@@ -258,6 +258,39 @@ int sph_count_pairs(sph_tasks t, int loop, int bundle, const void *dev_buf_in,
 /* Wait for `stream` and report errors latched by kernels (SPH_EBOUNDS). */
 int sph_sync(void *stream);
 
+/* ---- offload cycle without any allocation ------------------------------
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot allocate device memory while they run: for example a host
+ * application whose device memory is entirely reserved by its own pool
+ * allocator, or a loop that may not pay the latency and implicit
+ * synchronisation of cudaMalloc/cudaFree after start-up.
+ *
+ * It does what sph_offload_loop does, but the pack and result buffers live in
+ * one scratch array of SPH_NOALLOC_SCRATCH_BYTES that the library defines in
+ * device memory; every GPU that loads the library holds this array until the
+ * process exits.  The caller still provides the store and the uploaded tasks.
+ * The call allocates nothing (no cudaMalloc, no cudaFree, no allocating
+ * library routine).
+ *
+ * Limits and behaviour:
+ *  - The buffers of the largest bundle of `loop` (sph_buffer_bytes(t, loop,
+ *    0) and (t, loop, 1), each rounded up to 256 bytes) must fit in
+ *    SPH_NOALLOC_SCRATCH_BYTES together; otherwise the call returns
+ *    SPH_EUNSUPPORTED without launching anything.  Choose bundle_max_slots
+ *    in sph_tasks_build accordingly (e.g. 300000 slots fit every loop).
+ *  - The first call on a device looks up that device's address of the array
+ *    (with that device current); make this first call before any stream
+ *    capture is started on the device.
+ *  - All calls share the one array and it keeps whatever the last call left
+ *    in it.  Nothing in it needs to start at zero: each bundle's pack buffer
+ *    is written in full before it is read, and so is its result buffer.
+ *  - Calls whose work overlaps on the GPU (for example on two streams, or
+ *    from two threads) race on the array and give wrong results; serialise
+ *    them. */
+#define SPH_NOALLOC_SCRATCH_BYTES (32u << 20)
+int sph_offload_loop_noalloc(sph_store s, sph_tasks t, int loop, const sph_params *p,
+                             void *stream);
+
 int sph_tasks_destroy(sph_tasks t);
 
 #ifdef __cplusplus

@@ -3,6 +3,7 @@
 // translation unit.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -495,6 +496,43 @@ int sph_offload_loop(sph_store s, sph_tasks t, int loop, void *dev_buf_in, void 
         if (int rc = sph_unpack(s, t, loop, b, dev_buf_out, stream)) return rc;
     }
     return sph_ghost(s, loop, p, stream);
+}
+
+}  // extern "C"
+
+// Scratch for sph_offload_loop_noalloc: one file-scope device array shared by
+// every call on a device; its device address is looked up once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SPH_NOALLOC_SCRATCH_BYTES];
+static std::atomic<void *> g_noalloc_addr[64];
+
+extern "C" {
+
+int sph_offload_loop_noalloc(sph_store s, sph_tasks t, int loop, const sph_params *p,
+                             void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (!t) return fail(SPH_EINVAL, "NULL tasks handle");
+    if (int rc = check_loop(loop)) return rc;
+    const size_t in_b = (sph_buffer_bytes(t, loop, 0) + 255) / 256 * 256;
+    const size_t out_b = (sph_buffer_bytes(t, loop, 1) + 255) / 256 * 256;
+    if (in_b + out_b > (size_t)SPH_NOALLOC_SCRATCH_BYTES)
+        return fail(SPH_EUNSUPPORTED,
+                    "noalloc: the largest bundle needs %zu + %zu bytes of buffers, more than "
+                    "the %u-byte scratch array; rebuild the tasks with a smaller "
+                    "bundle_max_slots",
+                    in_b, out_b, (unsigned)SPH_NOALLOC_SCRATCH_BYTES);
+    int dev = 0;
+    if (int rc = cuda_check(cudaGetDevice(&dev), "noalloc: current device")) return rc;
+    if (dev < 0 || dev >= 64) return fail(SPH_EUNSUPPORTED, "noalloc: device %d >= 64", dev);
+    void *base = g_noalloc_addr[dev].load();
+    if (!base) {
+        if (int rc = cuda_check(cudaGetSymbolAddress(&base, g_noalloc_scratch),
+                                "noalloc: scratch address"))
+            return rc;
+        g_noalloc_addr[dev].store(base);
+    }
+    char *buf_in = (char *)base;
+    char *buf_out = buf_in + in_b;
+    return sph_offload_loop(s, t, loop, buf_in, buf_out, p, stream);
 }
 
 int sph_sync(void *stream) {

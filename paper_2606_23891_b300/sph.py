@@ -106,6 +106,7 @@ def lib() -> C.CDLL:
         "sph_offload_loop": (i, [p, p, i, p, p, p, p]),
         "sph_count_pairs": (i, [p, i, i, p, p, p, p]),
         "sph_sync": (i, [p]),
+        "sph_offload_loop_noalloc": (i, [p, p, i, p, p]),
         "sph_tasks_destroy": (i, [p]),
     }
     for name, (res, args) in sig.items():
@@ -230,6 +231,15 @@ def sph_offload_loop(s, t, loop: int, dev_in: int, dev_out: int, p: Params,
 def sph_count_pairs(t, loop: int, bundle: int, dev_in: int, p: Params,
                     dev_count: int, stream: int = 0) -> None:
     _ok(lib().sph_count_pairs(t, loop, bundle, dev_in, C.byref(p), dev_count, stream))
+
+
+SPH_NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def sph_offload_loop_noalloc(s, t, loop: int, p: Params, stream: int = 0) -> None:
+    """sph_offload_loop with the library's own fixed scratch array instead of
+    caller buffers; allocates nothing (see include/sph.h for the limits)."""
+    _ok(lib().sph_offload_loop_noalloc(s, t, loop, C.byref(p), stream))
 
 
 def sph_sync(stream: int = 0) -> None:
