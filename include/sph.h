@@ -258,6 +258,38 @@ int sph_count_pairs(sph_tasks t, int loop, int bundle, const void *dev_buf_in,
 /* Wait for `stream` and report errors latched by kernels (SPH_EBOUNDS). */
 int sph_sync(void *stream);
 
+/* ---- host-staged offload (Sec. 2.3, the paper's own setting) ------------
+ * The store lives in host memory; pack gathers each bundle's view on the
+ * host into a (pinned) host buffer, the buffer crosses the host link, the
+ * interaction kernel runs, the results cross back and unpack reduces them
+ * into the host store.  Host pack/unpack produce exactly the bytes / values
+ * of sph_pack / sph_unpack.  `nthreads` <= 0 uses all OpenMP threads.
+ * Device calls (sph_pack, sph_unpack, sph_init, sph_ghost, import/export)
+ * reject a host store and the calls below reject a device store. */
+int sph_store_create_host(int64_t n, int layout, uint64_t seed, void *host_mem,
+                          size_t bytes, sph_store *out);
+int sph_store_import_host(sph_store s, const sph_fields *host_src,
+                          const int64_t *host_perm, int nthreads);
+int sph_store_export_host(sph_store s, const sph_fields *host_dst,
+                          const int64_t *host_perm, int nthreads);
+int sph_pack_host(sph_store s, sph_tasks t, int loop, int bundle, void *host_buf_in,
+                  int nthreads);
+int sph_unpack_host(sph_store s, sph_tasks t, int loop, int bundle,
+                    const void *host_buf_out, int nthreads);
+int sph_init_host(sph_store s, int loop, const sph_params *p, int nthreads);
+int sph_ghost_host(sph_store s, int after_loop, const sph_params *p, int nthreads);
+
+/* One loop of the host-staged cycle over all bundles, double-buffered on two
+ * streams: while bundle b's H2D copy, kernel and D2H copy run on streams[b%2],
+ * the host packs bundle b+1 and unpacks bundle b-1.  host_in/host_out/dev_in/
+ * dev_out each hold two buffers of sph_buffer_bytes(t, loop, 0 / 1) bytes
+ * (host buffers should be pinned for the copies to be asynchronous).
+ * Returns after the last unpack (and the ghost after density) on the host. */
+int sph_offload_loop_host(sph_store s, sph_tasks t, int loop, void *const host_in[2],
+                          void *const host_out[2], void *const dev_in[2],
+                          void *const dev_out[2], const sph_params *p,
+                          void *const streams[2], int nthreads);
+
 /* ---- offload cycle without any allocation ------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that
  * cannot allocate device memory while they run: for example a host

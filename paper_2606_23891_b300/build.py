@@ -17,7 +17,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-         "-Xcompiler", "-Wall", "-I" + os.path.join(ROOT, "include"),
+         "-Xcompiler", "-Wall", "-Xcompiler", "-fopenmp", "-I" + os.path.join(ROOT, "include"),
          "-I" + CSRC, "--expt-relaxed-constexpr"]
 
 
@@ -55,7 +55,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         subprocess.check_call(cmd)
         objs.append(obj)
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs
+    cmd = [NVCC] + ARCH + ["-shared", "-Xcompiler", "-fopenmp", "-o", tmp] + objs + ["-lgomp"]
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
     return LIB

@@ -46,6 +46,13 @@ static bool aligned256(const void *p) { return ((uintptr_t)p & 255u) == 0; }
 
 static int check_store(sph_store s) {
     if (!s) return fail(SPH_EINVAL, "NULL store handle");
+    if (s->host) return fail(SPH_EINVAL, "store is in host memory: use the *_host calls");
+    return SPH_OK;
+}
+
+static int check_host_store(sph_store s) {
+    if (!s) return fail(SPH_EINVAL, "NULL store handle");
+    if (!s->host) return fail(SPH_EINVAL, "store is in device memory: use the device calls");
     return SPH_OK;
 }
 
@@ -552,4 +559,140 @@ int sph_sync(void *stream) {
     return SPH_OK;
 }
 
+
+int sph_store_create_host(int64_t n, int layout, uint64_t seed, void *host_mem, size_t bytes,
+                          sph_store *out) {
+    if (!out) return fail(SPH_EINVAL, "NULL out");
+    *out = nullptr;
+    if (n < 0 || n > INT32_MAX) return fail(SPH_EINVAL, "bad particle count %lld", (long long)n);
+    Layout L;
+    if (build_layout(layout, seed, n, &L) != SPH_OK)
+        return fail(SPH_EINVAL, "bad layout %d", layout);
+    const int64_t need = layout_bytes(L, n);
+    if ((int64_t)bytes < need)
+        return fail(SPH_EINVAL, "store needs %lld bytes, got %zu", (long long)need, bytes);
+    if (need > 0 && (!host_mem || !aligned256(host_mem)))
+        return fail(SPH_EINVAL, "store memory must be a 256-byte aligned host pointer");
+    sph_store s = new (std::nothrow) sph_store_s;
+    if (!s) return fail(SPH_ENOMEM, "store handle");
+    s->n = n;
+    s->layout = L;
+    s->mem = (char *)host_mem;
+    s->bytes = bytes;
+    s->host = true;
+    if (need > 0) memset(host_mem, 0, (size_t)need);
+    *out = s;
+    return SPH_OK;
+}
+
+int sph_store_import_host(sph_store s, const sph_fields *host_src, const int64_t *host_perm,
+                          int nthreads) {
+    if (int rc = check_host_store(s)) return rc;
+    if (!host_src) return fail(SPH_EINVAL, "NULL fields");
+    return host_copy_fields(s, host_src, host_perm, 1, nthreads);
+}
+
+int sph_store_export_host(sph_store s, const sph_fields *host_dst, const int64_t *host_perm,
+                          int nthreads) {
+    if (int rc = check_host_store(s)) return rc;
+    if (!host_dst) return fail(SPH_EINVAL, "NULL fields");
+    return host_copy_fields(s, host_dst, host_perm, 0, nthreads);
+}
+
+static int check_host_bundle(sph_store s, sph_tasks t, int loop, int bundle) {
+    if (int rc = check_host_store(s)) return rc;
+    if (!t) return fail(SPH_EINVAL, "NULL tasks handle");
+    if (int rc = check_loop(loop)) return rc;
+    if (bundle < 0 || bundle >= (int64_t)t->bundle_slots.size())
+        return fail(SPH_EINVAL, "bundle %d out of range", bundle);
+    if (s->n != t->n) return fail(SPH_EINVAL, "store and tasks disagree on particle count");
+    return SPH_OK;
+}
+
+int sph_pack_host(sph_store s, sph_tasks t, int loop, int bundle, void *host_buf_in,
+                  int nthreads) {
+    if (int rc = check_host_bundle(s, t, loop, bundle)) return rc;
+    if (!host_buf_in || !aligned256(host_buf_in))
+        return fail(SPH_EINVAL, "pack buffer must be a 256-byte aligned host pointer");
+    return host_pack(s, t, loop, bundle, (char *)host_buf_in, nthreads);
+}
+
+int sph_unpack_host(sph_store s, sph_tasks t, int loop, int bundle, const void *host_buf_out,
+                    int nthreads) {
+    if (int rc = check_host_bundle(s, t, loop, bundle)) return rc;
+    if (!host_buf_out || !aligned256(host_buf_out))
+        return fail(SPH_EINVAL, "result buffer must be a 256-byte aligned host pointer");
+    return host_unpack(s, t, loop, bundle, (const char *)host_buf_out, nthreads);
+}
+
+int sph_init_host(sph_store s, int loop, const sph_params *p, int nthreads) {
+    if (int rc = check_host_store(s)) return rc;
+    if (int rc = check_loop(loop)) return rc;
+    if (int rc = check_params(p)) return rc;
+    return host_init(s, loop, p->active_bin, nthreads);
+}
+
+int sph_ghost_host(sph_store s, int after_loop, const sph_params *p, int nthreads) {
+    if (int rc = check_host_store(s)) return rc;
+    if (int rc = check_loop(after_loop)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (after_loop != SPH_DENSITY) return SPH_OK;
+    return host_ghost(s, (float)p->kernel_gamma, (float)p->gamma, (float)p->balsara_eps, nthreads);
+}
+
+int sph_offload_loop_host(sph_store s, sph_tasks t, int loop, void *const host_in[2],
+                          void *const host_out[2], void *const dev_in[2], void *const dev_out[2],
+                          const sph_params *p, void *const streams[2], int nthreads) {
+    if (int rc = check_host_store(s)) return rc;
+    if (!t) return fail(SPH_EINVAL, "NULL tasks handle");
+    if (int rc = check_loop(loop)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (!host_in || !host_out || !dev_in || !dev_out || !streams)
+        return fail(SPH_EINVAL, "NULL buffer or stream array");
+    for (int k = 0; k < 2; ++k)
+        if (!aligned256(host_in[k]) || !aligned256(host_out[k]) || !aligned256(dev_in[k]) ||
+            !aligned256(dev_out[k]) || !host_in[k] || !host_out[k] || !dev_in[k] || !dev_out[k])
+            return fail(SPH_EINVAL, "buffers must be non-NULL and 256-byte aligned");
+    if (int rc = host_init(s, loop, p->active_bin, nthreads)) return rc;
+    const int nb = (int)t->bundle_slots.size();
+    cudaStream_t st[2] = {(cudaStream_t)streams[0], (cudaStream_t)streams[1]};
+    cudaEvent_t done[2] = {nullptr, nullptr};
+    int rc = SPH_OK;
+    for (int k = 0; k < 2 && rc == SPH_OK; ++k)
+        rc = cuda_check(cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming), "event");
+    for (int b = 0; b < nb && rc == SPH_OK; ++b) {
+        const int k = b & 1;
+        int64_t off[16];
+        const size_t in_b = (size_t)lane_offsets(loop, 0, t->bundle_slots[b], off);
+        const size_t out_b = (size_t)lane_offsets(loop, 1, t->bundle_slots[b], off);
+        // buffers k were last used by bundle b-2, whose results were unpacked
+        // after its event completed in the previous iteration
+        if ((rc = sph_pack_host(s, t, loop, b, host_in[k], nthreads))) break;
+        if ((rc = cuda_check(cudaMemcpyAsync(dev_in[k], host_in[k], in_b,
+                                             cudaMemcpyHostToDevice, st[k]), "H2D")))
+            break;
+        if ((rc = interact(t, loop, b, dev_in[k], dev_out[k], p, nullptr, st[k]))) break;
+        if ((rc = cuda_check(cudaMemcpyAsync(host_out[k], dev_out[k], out_b,
+                                             cudaMemcpyDeviceToHost, st[k]), "D2H")))
+            break;
+        if ((rc = cuda_check(cudaEventRecord(done[k], st[k]), "event record"))) break;
+        if (b >= 1) {
+            if ((rc = cuda_check(cudaEventSynchronize(done[k ^ 1]), "event wait"))) break;
+            if ((rc = sph_unpack_host(s, t, loop, b - 1, host_out[k ^ 1], nthreads))) break;
+        }
+    }
+    if (rc == SPH_OK && nb > 0) {
+        const int k = (nb - 1) & 1;
+        rc = cuda_check(cudaEventSynchronize(done[k]), "event wait");
+        if (rc == SPH_OK) rc = sph_unpack_host(s, t, loop, nb - 1, host_out[k], nthreads);
+    }
+    if (rc != SPH_OK) {
+        cudaStreamSynchronize(st[0]);
+        cudaStreamSynchronize(st[1]);
+    }
+    for (int k = 0; k < 2; ++k)
+        if (done[k]) cudaEventDestroy(done[k]);
+    if (rc == SPH_OK && loop == SPH_DENSITY) rc = sph_ghost_host(s, SPH_DENSITY, p, nthreads);
+    return rc;
+}
 }  // extern "C"

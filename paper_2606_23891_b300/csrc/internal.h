@@ -82,6 +82,7 @@ struct sph_store_s {
     sph::Layout layout;
     char *mem = nullptr;
     size_t bytes = 0;
+    bool host = false;  // store in host memory (host-staged path)
 };
 
 struct sph_tasks_s {
@@ -109,6 +110,14 @@ struct sph_tasks_s {
 namespace sph {
 int build_tasks(int64_t n, const double *x, const float *h,
                 const sph_grid_params *gp, int64_t *perm_out, sph_tasks_s *T);
+
+// Host-staged path (host_path.cpp): OpenMP over tasks / cells / particles.
+int host_pack(sph_store s, sph_tasks t, int loop, int b, char *buf, int nthreads);
+int host_unpack(sph_store s, sph_tasks t, int loop, int b, const char *buf, int nthreads);
+int host_init(sph_store s, int loop, int active_bin, int nthreads);
+int host_ghost(sph_store s, float kernel_gamma, float gamma, float balsara_eps, int nthreads);
+int host_copy_fields(sph_store s, const sph_fields *f, const int64_t *perm, int to_store,
+                     int nthreads);
 
 // Packed-buffer lanes of Sec. 2.3 buffers: sizes of each lane of `loop`
 // (in_or_out 0 = pack buffer, 1 = result buffer); returns the lane count.

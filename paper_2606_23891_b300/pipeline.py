@@ -188,3 +188,124 @@ class Offload:
             self.close()
         except Exception:
             pass
+
+
+def aligned_host(nbytes: int, pinned: bool = False):
+    """A 256-byte aligned host byte buffer: (array view, owner).  Pinned
+    memory comes from torch (needs a CUDA device); otherwise numpy."""
+    nbytes = max(int(nbytes), 256)
+    if pinned:
+        t = torch.empty(nbytes + 256, dtype=torch.uint8).pin_memory()
+        off = (-t.data_ptr()) % 256
+        return t[off:off + nbytes].numpy(), t
+    a = np.empty(nbytes + 256, np.uint8)
+    off = (-a.ctypes.data) % 256
+    return a[off:off + nbytes], a
+
+
+def host_fields_struct(arrays: dict) -> sph.Fields:
+    F = sph.Fields()
+    for name, a in arrays.items():
+        if a is None:
+            continue
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("field %s must be C-contiguous" % name)
+        setattr(F, name, a.ctypes.data)
+    return F
+
+
+class HostOffload:
+    """A particle set in a host-memory store (the paper's host side) with the
+    host-staged double-buffered cycle.  Without a GPU only the host calls
+    (import/export, pack, unpack, init, ghost) are usable."""
+
+    def __init__(self, fields: dict, layout="aos", seed: int = 0, box=(1.0, 1.0, 1.0),
+                 bundle_max_slots: int = 0, ncell=(0, 0, 0),
+                 params: sph.Params | None = None, gpu: bool = True, nthreads: int = 0):
+        self.layout = sph.LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+        self.params = params or sph.params()
+        self.nthreads = nthreads
+        self.gpu = gpu
+        x = np.ascontiguousarray(fields["x"], np.float64)
+        h = np.ascontiguousarray(fields["h"], np.float32)
+        self.n = n = x.shape[0]
+        gp = sph.grid_params(box, self.params.kernel_gamma, ncell, bundle_max_slots)
+        self.perm = np.empty(n, np.int64)
+        self.tasks = sph.sph_tasks_build(n, x.ctypes.data, h.ctypes.data, gp,
+                                         self.perm.ctypes.data)
+        self.info = sph.sph_tasks_info(self.tasks)
+        self.nbytes = sph.sph_store_bytes(n, self.layout, seed)
+        self.mem, self._mem_owner = aligned_host(self.nbytes, pinned=gpu)
+        self.store = sph.sph_store_create_host(n, self.layout, seed, self.mem.ctypes.data,
+                                               self.nbytes)
+        nin = max(sph.sph_buffer_bytes(self.tasks, l, 0) for l in range(3))
+        nout = max(sph.sph_buffer_bytes(self.tasks, l, 1) for l in range(3))
+        self.nin, self.nout = nin, nout
+        self.host_in = [aligned_host(nin, pinned=gpu) for _ in range(2)]
+        self.host_out = [aligned_host(nout, pinned=gpu) for _ in range(2)]
+        if gpu:
+            sph.sph_tasks_upload(self.tasks)
+            self.dev_in = [torch.empty(max(nin, 256), dtype=torch.uint8, device="cuda")
+                           for _ in range(2)]
+            self.dev_out = [torch.empty(max(nout, 256), dtype=torch.uint8, device="cuda")
+                            for _ in range(2)]
+            self.streams = [torch.cuda.Stream() for _ in range(2)]
+        self.import_fields(fields)
+
+    def import_fields(self, fields: dict, names=INPUTS) -> None:
+        keep = {}
+        for name in names:
+            if name in fields:
+                dt, k = field_spec(name)
+                keep[name] = np.ascontiguousarray(fields[name], dt)
+        sph.sph_store_import_host(self.store, host_fields_struct(keep), self.perm.ctypes.data,
+                                  self.nthreads)
+
+    def export(self, names=OUTPUTS) -> dict:
+        out = {}
+        for name in names:
+            dt, k = field_spec(name)
+            out[name] = np.empty((self.n, k) if k > 1 else (self.n,), dt)
+        sph.sph_store_export_host(self.store, host_fields_struct(out), self.perm.ctypes.data,
+                                  self.nthreads)
+        return out
+
+    def store_bytes(self) -> np.ndarray:
+        return self.mem[: self.nbytes].copy()
+
+    def loop(self, loop: int) -> None:
+        sph.sph_offload_loop_host(
+            self.store, self.tasks, loop, [b[0].ctypes.data for b in self.host_in],
+            [b[0].ctypes.data for b in self.host_out], [d.data_ptr() for d in self.dev_in],
+            [d.data_ptr() for d in self.dev_out], self.params,
+            [s.cuda_stream for s in self.streams], self.nthreads)
+
+    def step(self) -> None:
+        for loop in (sph.SPH_DENSITY, sph.SPH_GRADIENT, sph.SPH_FORCE):
+            self.loop(loop)
+
+    def task_list(self):
+        nt = self.info["ntasks"]
+        ncell = self.info["ncell_x"] * self.info["ncell_y"] * self.info["ncell_z"]
+        ci = np.empty(nt, np.int32)
+        cj = np.empty(nt, np.int32)
+        sh = np.empty((nt, 3), np.int8)
+        cs = np.empty(ncell + 1, np.int64)
+        bs = np.empty(self.info["nbundles"] + 1, np.int64)
+        sph.sph_tasks_get(self.tasks, ci.ctypes.data, cj.ctypes.data, sh.ctypes.data,
+                          cs.ctypes.data, bs.ctypes.data)
+        return ci, cj, sh, cs, bs
+
+    def close(self) -> None:
+        if getattr(self, "store", None) is not None:
+            sph.sph_store_destroy(self.store)
+            self.store = None
+        if getattr(self, "tasks", None) is not None:
+            sph.sph_tasks_destroy(self.tasks)
+            self.tasks = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

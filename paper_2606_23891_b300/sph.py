@@ -107,6 +107,14 @@ def lib() -> C.CDLL:
         "sph_count_pairs": (i, [p, i, i, p, p, p, p]),
         "sph_sync": (i, [p]),
         "sph_offload_loop_noalloc": (i, [p, p, i, p, p]),
+        "sph_store_create_host": (i, [i64, i, u64, p, sz, p]),
+        "sph_store_import_host": (i, [p, p, p, i]),
+        "sph_store_export_host": (i, [p, p, p, i]),
+        "sph_pack_host": (i, [p, p, i, i, p, i]),
+        "sph_unpack_host": (i, [p, p, i, i, p, i]),
+        "sph_init_host": (i, [p, i, p, i]),
+        "sph_ghost_host": (i, [p, i, p, i]),
+        "sph_offload_loop_host": (i, [p, p, i, p, p, p, p, p, p, i]),
         "sph_tasks_destroy": (i, [p]),
     }
     for name, (res, args) in sig.items():
@@ -240,6 +248,44 @@ def sph_offload_loop_noalloc(s, t, loop: int, p: Params, stream: int = 0) -> Non
     """sph_offload_loop with the library's own fixed scratch array instead of
     caller buffers; allocates nothing (see include/sph.h for the limits)."""
     _ok(lib().sph_offload_loop_noalloc(s, t, loop, C.byref(p), stream))
+
+
+def sph_store_create_host(n: int, layout: int, seed: int, host_mem: int, nbytes: int):
+    h = C.c_void_p()
+    _ok(lib().sph_store_create_host(n, layout, seed, host_mem, nbytes, C.byref(h)))
+    return h
+
+
+def sph_store_import_host(s, fields: Fields, host_perm: int, nthreads: int = 0) -> None:
+    _ok(lib().sph_store_import_host(s, C.byref(fields), host_perm, nthreads))
+
+
+def sph_store_export_host(s, fields: Fields, host_perm: int, nthreads: int = 0) -> None:
+    _ok(lib().sph_store_export_host(s, C.byref(fields), host_perm, nthreads))
+
+
+def sph_pack_host(s, t, loop: int, bundle: int, host_buf_in: int, nthreads: int = 0) -> None:
+    _ok(lib().sph_pack_host(s, t, loop, bundle, host_buf_in, nthreads))
+
+
+def sph_unpack_host(s, t, loop: int, bundle: int, host_buf_out: int, nthreads: int = 0) -> None:
+    _ok(lib().sph_unpack_host(s, t, loop, bundle, host_buf_out, nthreads))
+
+
+def sph_init_host(s, loop: int, p: Params, nthreads: int = 0) -> None:
+    _ok(lib().sph_init_host(s, loop, C.byref(p), nthreads))
+
+
+def sph_ghost_host(s, after_loop: int, p: Params, nthreads: int = 0) -> None:
+    _ok(lib().sph_ghost_host(s, after_loop, C.byref(p), nthreads))
+
+
+def sph_offload_loop_host(s, t, loop: int, host_in, host_out, dev_in, dev_out, p: Params,
+                          streams, nthreads: int = 0) -> None:
+    """host_in, host_out, dev_in, dev_out, streams: pairs of pointers."""
+    arr = lambda v: (C.c_void_p * 2)(*[int(x) for x in v])
+    _ok(lib().sph_offload_loop_host(s, t, loop, arr(host_in), arr(host_out), arr(dev_in),
+                                    arr(dev_out), C.byref(p), arr(streams), nthreads))
 
 
 def sph_sync(stream: int = 0) -> None:
