@@ -48,7 +48,9 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes per slot of the interaction kernels from an ncu capture of a
 # smaller case (traffic grows with the slots a launch processes), valid only
 # for the kernel source with this digest (else reported as null)
-NCU_TRAFFIC = {("kernel", 2): {"bytes_per_slot": 92.1, "src": "e4b699e728bdf76e"}}
+NCU_TRAFFIC = {("plain", "kernel", 2): {"bytes_per_unit": 92.1, "src": "e4b699e728bdf76e"}}
+# bytes per particle of the batched pack records (nf float4 + index lanes)
+BATCH_REC = (3 * 16 + 4, 4 * 16 + 4, 5 * 16 + 9)
 GPU_KERNEL_SRC = os.path.join(ROOT, "paper_2606_23891_b300", "csrc", "physics_kernels.cuh")
 
 
@@ -195,12 +197,15 @@ def candidates(off) -> int:
 
 
 class StepTimer:
-    """Run one step with CUDA events around every stage on the launch stream."""
+    """Run one step with CUDA events around every stage on the launch stream.
+    pipeline "plain": per-task bundles (pack -> kernel -> unpack per bundle);
+    "batched": cell-dedup bundles (one persistent launch per bundle)."""
 
-    def __init__(self, off):
+    def __init__(self, off, pipeline: str = "plain"):
         import torch
         self.torch = torch
         self.off = off
+        self.pipeline = pipeline
         self.recs = []
         self.launches = 0
 
@@ -212,23 +217,37 @@ class StepTimer:
     def step(self, record: bool):
         from paper_2606_23891_b300 import sph
         off = self.off
-        nb = off.nbundles()
+        batched = self.pipeline == "batched"
+        nb = off.binfo["nbundles"] if batched else off.nbundles()
+        st = off.stream
         for loop in range(3):
-            sph.sph_init(off.store, loop, off.params, off.stream)
+            sph.sph_init(off.store, loop, off.params, st)
             self.launches += 1
             for b in range(nb):
                 e0 = self.ev() if record else None
-                off.pack(loop, b)
+                if batched:
+                    sph.sph_batch_pack(off.store, off.bplan, loop, b, off.bbuf_in.data_ptr(),
+                                       off.params, st)
+                else:
+                    off.pack(loop, b)
                 e1 = self.ev() if record else None
-                off.interact(loop, b)
+                if batched:
+                    sph.sph_batch_interact(off.bplan, loop, b, off.bbuf_in.data_ptr(),
+                                           off.bbuf_out.data_ptr(), off.params, st)
+                else:
+                    off.interact(loop, b)
                 e2 = self.ev() if record else None
-                off.unpack(loop, b)
+                if batched:
+                    sph.sph_batch_unpack(off.store, off.bplan, loop, b, off.bbuf_out.data_ptr(),
+                                         off.bbuf_in.data_ptr(), st)
+                else:
+                    off.unpack(loop, b)
                 e3 = self.ev() if record else None
                 self.launches += 3
                 if record:
                     self.recs.append((loop, e0, e1, e2, e3))
             if loop == 0:
-                sph.sph_ghost(off.store, 0, off.params, off.stream)
+                sph.sph_ghost(off.store, 0, off.params, st)
                 self.launches += 1
 
     def stage_ms(self):
@@ -242,9 +261,9 @@ class StepTimer:
         return out, cnt
 
 
-def run_layout(off, steps, warmup, ws, clocks=None):
+def run_layout(off, steps, warmup, ws, clocks=None, pipeline="plain"):
     import torch
-    timer = StepTimer(off)
+    timer = StepTimer(off, pipeline)
     for _ in range(warmup):
         timer.step(record=False)
     torch.cuda.synchronize()
@@ -267,7 +286,7 @@ def run_layout(off, steps, warmup, ws, clocks=None):
     return total_ms, timer, cl
 
 
-def run_e2e(off, f, steps, warmup):
+def run_e2e(off, f, steps, warmup, pipeline="plain"):
     """Same step through the C-ABI from pinned host inputs to host results."""
     import torch
     from paper_2606_23891_b300 import sph
@@ -282,7 +301,7 @@ def run_e2e(off, f, steps, warmup):
     pin_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in dev_out.items()}
     h2d = sum(t.numel() * t.element_size() for t in pin_in.values())
     d2h = sum(t.numel() * t.element_size() for t in pin_out.values())
-    timer = StepTimer(off)
+    timer = StepTimer(off, pipeline)
     Fi, Fo = fields_struct(dev_in), fields_struct(dev_out)
 
     def one():
@@ -370,19 +389,19 @@ def run_ours(args, ws, rank, local):
     n = base.n
     per_layout = {}
     head = None
-    for lname in args.layouts:
-        off = base if lname == args.layouts[0] else Offload(
-            f, layout=lname, share=base)
-        clocks = ClockSampler(local) if lname == args.headline else None
-        total_ms, timer, cl = run_layout(off, args.steps, args.warmup, ws, clocks)
-        total_ms = barrier_max(total_ms, ws)
-        st, cnt = timer.stage_ms()
-        ms_step = total_ms / args.steps
+    base.batch(threads=args.batch_threads)
+    bslots = base.binfo["max_slots"]
+
+    def loop_stats(st, ms_step, pipeline):
         loops = {}
         for l in range(3):
-            pk, kr, up = (st[(s, l)] / args.steps for s in ("pack", "kernel", "unpack"))
-            pack_b = slots * 2 * VIEW_IN[l]
-            unpack_b = slots * VIEW_OUT[l] + n * 2 * VIEW_OUT[l]
+            pk, kr, up = (st[(s_, l)] / args.steps for s_ in ("pack", "kernel", "unpack"))
+            if pipeline == "plain":
+                pack_b = slots * 2 * VIEW_IN[l]
+                unpack_b = slots * VIEW_OUT[l] + n * 2 * VIEW_OUT[l]
+            else:  # each particle packed once; one result per particle
+                pack_b = bslots * (VIEW_IN[l] + BATCH_REC[l])
+                unpack_b = n * VIEW_OUT[l] + n * 2 * VIEW_OUT[l]
             loops[LOOP_NAMES[l]] = {
                 "pack_ms": pk, "kernel_ms": kr, "unpack_ms": up,
                 "pack_unpack_GBps": (pack_b + unpack_b) / ((pk + up) * 1e-3) / 1e9,
@@ -391,15 +410,29 @@ def run_ours(args, ws, rank, local):
                 "pair_interactions_per_s": pairs[l] / ((pk + kr + up) * 1e-3),
                 "kernel_useful_fp32_TFLOPs": pairs[l] * FLOPS_PAIR[l] / (kr * 1e-3) / 1e12,
             }
-        per_layout[lname] = {"ms_per_step": ms_step,
-                             "pair_interactions_per_s": sum(pairs) * ws / (ms_step * 1e-3),
-                             "loops": loops}
-        if lname == args.headline:
-            head = (off, total_ms, timer, cl, st, cnt)
-        elif off is not base:
-            off.close()
-            del off
-            torch.cuda.empty_cache()
+        return {"ms_per_step": ms_step,
+                "pair_interactions_per_s": sum(pairs) * ws / (ms_step * 1e-3), "loops": loops}
+
+    for lname in args.layouts:
+        off = base if lname == args.layouts[0] else Offload(
+            f, layout=lname, share=base)
+        if off is not base:
+            off.use_batch_of(base)
+        per_layout[lname] = {}
+        for pipeline in args.pipelines:
+            is_head = lname == args.headline and pipeline == args.head_pipeline
+            clocks = ClockSampler(local) if is_head else None
+            total_ms, timer, cl = run_layout(off, args.steps, args.warmup, ws, clocks, pipeline)
+            total_ms = barrier_max(total_ms, ws)
+            st, cnt = timer.stage_ms()
+            per_layout[lname][pipeline] = loop_stats(st, total_ms / args.steps, pipeline)
+            if is_head:
+                head = (off, total_ms, timer, cl, st, cnt)
+        if head is None or head[0] is not off:
+            if off is not base:
+                off.close()
+                del off
+                torch.cuda.empty_cache()
     off, total_ms, timer, cl, st, cnt = head
     ms_step = total_ms / args.steps
     value = sum(pairs) * ws / (ms_step * 1e-3)
@@ -415,10 +448,12 @@ def run_ours(args, ws, rank, local):
         # reported beside it, not counted as achieved work
         flops = pairs[loop] * FLOPS_PAIR[loop] / per_step
         achieved = flops / (dur * 1e-3) / 1e12
-        tr = NCU_TRAFFIC.get((stage, loop))
-        traffic = (tr["bytes_per_slot"] * slots / per_step
+        tr = NCU_TRAFFIC.get((args.head_pipeline, stage, loop))
+        units = slots if args.head_pipeline == "plain" else n
+        traffic = (tr["bytes_per_unit"] * units / per_step
                    if tr and tr["src"] == src_digest() else None)
-        roof = {"kernel": "interaction/%s" % LOOP_NAMES[loop], "bound": "alu",
+        roof = {"kernel": "%s interaction/%s" % (args.head_pipeline, LOOP_NAMES[loop]),
+                "bound": "alu",
                 "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
@@ -427,14 +462,18 @@ def run_ours(args, ws, rank, local):
                     / (dur * 1e-3) / 1e12,
                 "hbm_GBps": (traffic / (dur * 1e-3) / 1e9) if traffic else None}
     else:
-        bpl = (slots * 2 * VIEW_IN[loop] if stage == "pack"
-               else slots * VIEW_OUT[loop] + n * 2 * VIEW_OUT[loop]) / per_step
+        if args.head_pipeline == "plain":
+            bpl = (slots * 2 * VIEW_IN[loop] if stage == "pack"
+                   else slots * VIEW_OUT[loop] + n * 2 * VIEW_OUT[loop]) / per_step
+        else:
+            bpl = (bslots * (VIEW_IN[loop] + BATCH_REC[loop]) if stage == "pack"
+                   else n * 3 * VIEW_OUT[loop]) / per_step
         achieved = bpl / (dur * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6400.0)
         roof = {"kernel": "%s/%s" % (stage, LOOP_NAMES[loop]), "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": None, "peak_source": "measured" if peaks else "fallback"}
-    e2e_ms, h2d, d2h = run_e2e(off, f, max(1, args.steps // 2), 1)
+    e2e_ms, h2d, d2h = run_e2e(off, f, max(1, args.steps // 2), 1, args.head_pipeline)
     e2e_ms = barrier_max(e2e_ms, ws)
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_sample > 0:
@@ -463,7 +502,8 @@ def run_ours(args, ws, rank, local):
         "config": {
             "workload": "gresho256: Gresho-vortex shaped jittered 256^3 lattice, "
                         "64^3 cells of 55..73 particles, all loops",
-            "particles": n, "layout": args.headline, "tasks": cfg_vals["tasks"],
+            "particles": n, "layout": args.headline, "pipeline": args.head_pipeline,
+            "batch_threads": args.batch_threads, "tasks": cfg_vals["tasks"],
             "bundles": cfg_vals["bundles"], "bundle_max_slots": args.bundle_slots,
             "slots_per_loop": slots, "candidates_per_loop": ncand,
             "pairs": dict(zip(LOOP_NAMES, pairs)),
@@ -502,12 +542,18 @@ def main(argv=None):
     ap.add_argument("--n-side", type=int, default=N_SIDE)
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--ref-sample", type=int, default=2)
+    ap.add_argument("--pipelines", default="plain,batched")
+    ap.add_argument("--head-pipeline", default="batched")
+    ap.add_argument("--batch-threads", type=int, default=128)
     ap.add_argument("--host-steps", type=int, default=2)
     ap.add_argument("--host-layouts", default="aos,pack_force_type,soa")
     ap.add_argument("--host-bundle-slots", type=int, default=1 << 24)
     args = ap.parse_args(argv)
     args.layouts = [s for s in args.layouts.split(",") if s]
     args.host_layouts = [s for s in args.host_layouts.split(",") if s]
+    args.pipelines = [s for s in args.pipelines.split(",") if s]
+    if args.head_pipeline not in args.pipelines:
+        args.pipelines.append(args.head_pipeline)
     if args.headline not in args.layouts:
         args.layouts.append(args.headline)
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup

@@ -38,6 +38,7 @@ extern "C" {
 
 typedef struct sph_store_s *sph_store;
 typedef struct sph_tasks_s *sph_tasks;
+typedef struct sph_batch_s *sph_batch;
 
 /* Store layouts of Sec. 3.1. */
 enum sph_layout {
@@ -320,6 +321,43 @@ int sph_offload_loop_host(sph_store s, sph_tasks t, int loop, void *const host_i
  *    from two threads) race on the array and give wrong results; serialise
  *    them. */
 #define SPH_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* ---- batched (cell-dedup) offload ---------------------------------------
+ * The same interactions as the per-task cycle, with the bundling of Sec. 2.3
+ * taken further: a bundle is a range of target cells; each cell the range
+ * needs (targets and their periodic neighbours) is packed once per bundle
+ * (positions already split for the FP32 kernels), and one persistent launch
+ * works through (target cell, particle chunk) items in longest-first order,
+ * each computing its particles' sums over all 27 neighbour cells.  Unpack
+ * adds each target particle's single result into the store (no per-slot
+ * reduction).  Outputs agree with the per-task cycle to rounding (the sum
+ * order over neighbours differs). */
+typedef struct {
+    int64_t max_target_cells;  /* target cells per bundle, <= 0: all */
+    int32_t threads;           /* CTA size and particle chunk: 64, 128, 256 */
+    int32_t reserved;          /* must be 0 */
+} sph_batch_params;
+
+/* Build a batch plan from a task handle's cells (host) and upload it to the
+ * current device (allocates the plan's device metadata). */
+int sph_batch_build(sph_tasks t, const sph_batch_params *bp, sph_batch *out);
+/* info[0] bundles, [1] largest bundle slots, [2] work items, [3] threads,
+ * [4] largest bundle target slots, [5] packed cells (all bundles). */
+int sph_batch_info(sph_batch b, int64_t info[6]);
+/* Largest buffer of any bundle for `loop` (0 pack, 1 result). */
+size_t sph_batch_buffer_bytes(sph_batch b, int loop, int in_or_out);
+int sph_batch_pack(sph_store s, sph_batch b, int loop, int bundle, void *dev_buf_in,
+                   const sph_params *p, void *stream);
+int sph_batch_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in,
+                       void *dev_buf_out, const sph_params *p, void *stream);
+int sph_batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const void *dev_buf_out,
+                     const void *dev_buf_in, void *stream);
+/* init, then per bundle pack -> interact -> unpack, then the ghost after
+ * density; enqueues only (no host synchronisation), so it can be recorded
+ * into a CUDA graph after a first call. */
+int sph_batch_offload_loop(sph_store s, sph_batch b, int loop, void *dev_buf_in,
+                           void *dev_buf_out, const sph_params *p, void *stream);
+int sph_batch_destroy(sph_batch b);
 int sph_offload_loop_noalloc(sph_store s, sph_tasks t, int loop, const sph_params *p,
                              void *stream);
 

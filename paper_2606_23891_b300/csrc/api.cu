@@ -14,6 +14,7 @@
 #include "pack_kernels.cuh"
 #include "physics_kernels.cuh"
 #include "store_kernels.cuh"
+#include "batch_kernels.cuh"
 
 namespace sph {
 
@@ -99,6 +100,36 @@ static int check_bundle_store(sph_store s, sph_tasks t) {
         return fail(SPH_EINVAL, "store has %lld particles, tasks %lld", (long long)s->n,
                     (long long)t->n);
     return SPH_OK;
+}
+
+template <int LOOP, int T>
+int launch_binteract(const BInteractArgs &a, cudaStream_t st) {
+    static int cached_dev = -1, grid_max = 0;
+    int dev = 0;
+    if (int rc = cuda_check(cudaGetDevice(&dev), "get device")) return rc;
+    if (cached_dev != dev) {
+        int per_sm = 0, sms = 0;
+        if (int rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &per_sm, k_binteract<LOOP, T>, T, 0),
+                                "occupancy"))
+            return rc;
+        if (int rc = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev),
+                                "SM count"))
+            return rc;
+        grid_max = (per_sm > 0 ? per_sm : 1) * sms;
+        cached_dev = dev;
+    }
+    const int g = a.nitems < grid_max ? a.nitems : grid_max;
+    if (g <= 0) return SPH_OK;
+    k_binteract<LOOP, T><<<g, T, 0, st>>>(a);
+    return launch_check("batch interaction kernel");
+}
+
+template <int LOOP>
+int dispatch_binteract(int threads, const BInteractArgs &a, cudaStream_t st) {
+    if (threads == 64) return launch_binteract<LOOP, 64>(a, st);
+    if (threads == 256) return launch_binteract<LOOP, 256>(a, st);
+    return launch_binteract<LOOP, 128>(a, st);
 }
 
 }  // namespace sph
@@ -694,5 +725,224 @@ int sph_offload_loop_host(sph_store s, sph_tasks t, int loop, void *const host_i
         if (done[k]) cudaEventDestroy(done[k]);
     if (rc == SPH_OK && loop == SPH_DENSITY) rc = sph_ghost_host(s, SPH_DENSITY, p, nthreads);
     return rc;
+}
+
+// ---- batched (cell-dedup) pipeline ---------------------------------------
+static int check_batch(sph_batch b, int bundle) {
+    if (!b) return fail(SPH_EINVAL, "NULL batch handle");
+    if (bundle < 0 || bundle >= (int64_t)b->bundles.size())
+        return fail(SPH_EINVAL, "bundle %d out of range", bundle);
+    return SPH_OK;
+}
+
+static void batch_free(sph_batch b) {
+    if (b->d_cells) cudaFree(b->d_cells);
+    if (b->d_targets) cudaFree(b->d_targets);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_counter) cudaFree(b->d_counter);
+    b->d_cells = nullptr;
+    b->d_targets = nullptr;
+    b->d_items = nullptr;
+    b->d_counter = nullptr;
+}
+
+int sph_batch_build(sph_tasks t, const sph_batch_params *bp, sph_batch *out) {
+    if (!out) return fail(SPH_EINVAL, "NULL out");
+    *out = nullptr;
+    if (!t || !bp) return fail(SPH_EINVAL, "NULL tasks or params");
+    if (bp->reserved != 0) return fail(SPH_EINVAL, "batch params: reserved must be 0");
+    sph_batch b = new (std::nothrow) sph_batch_s;
+    if (!b) return fail(SPH_ENOMEM, "batch handle");
+    int rc;
+    try {
+        rc = build_batch(t, bp, b);
+    } catch (const std::bad_alloc &) {
+        rc = fail(SPH_ENOMEM, "batch_build: host allocation failed");
+    }
+    auto up = [&](void **dst, const void *src, size_t bytes, const char *what) -> int {
+        if (bytes == 0) return SPH_OK;
+        if (cudaMalloc(dst, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SPH_ENOMEM, "device allocation of %s (%zu bytes)", what, bytes);
+        }
+        if (!src) return cuda_check(cudaMemset(*dst, 0, bytes), what);
+        return cuda_check(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), what);
+    };
+    if (rc == SPH_OK &&
+        ((rc = up((void **)&b->d_cells, b->cells.data(), b->cells.size() * sizeof(BCellDev),
+                  "batch cells")) ||
+         (rc = up((void **)&b->d_targets, b->targets.data(),
+                  b->targets.size() * sizeof(BTargetDev), "batch targets")) ||
+         (rc = up((void **)&b->d_items, b->items.data(), b->items.size() * sizeof(BItemDev),
+                  "batch items")) ||
+         (rc = up((void **)&b->d_counter, nullptr,
+                  (b->bundles.size() + 1) * sizeof(unsigned int), "batch counters")))) {
+    }
+    if (rc) {
+        batch_free(b);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return SPH_OK;
+}
+
+int sph_batch_info(sph_batch b, int64_t info[6]) {
+    if (!b || !info) return fail(SPH_EINVAL, "NULL argument");
+    info[0] = (int64_t)b->bundles.size();
+    info[1] = b->max_slots;
+    info[2] = (int64_t)b->items.size();
+    info[3] = b->threads;
+    info[4] = b->max_targets;
+    info[5] = (int64_t)b->cells.size();
+    return SPH_OK;
+}
+
+static int64_t batch_max_cells(sph_batch b) {
+    int64_t m = 0;
+    for (const BatchBundle &bb : b->bundles) m = bb.ncells > m ? bb.ncells : m;
+    return m;
+}
+
+size_t sph_batch_buffer_bytes(sph_batch b, int loop, int in_or_out) {
+    if (!b || loop < SPH_DENSITY || loop > SPH_FORCE || (in_or_out != 0 && in_or_out != 1))
+        return 0;
+    const int64_t S = b->max_slots, C = batch_max_cells(b);
+    if (in_or_out == 1) return (size_t)bout_bytes(loop, S);
+    if (loop == SPH_DENSITY) return (size_t)BLayout<SPH_DENSITY>::bytes(S, C);
+    if (loop == SPH_GRADIENT) return (size_t)BLayout<SPH_GRADIENT>::bytes(S, C);
+    return (size_t)BLayout<SPH_FORCE>::bytes(S, C);
+}
+
+int sph_batch_pack(sph_store s, sph_batch b, int loop, int bundle, void *dev_buf_in,
+                   const sph_params *p, void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (int rc = check_batch(b, bundle)) return rc;
+    if (int rc = check_loop(loop)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (s->n != b->n) return fail(SPH_EINVAL, "store and batch disagree on particle count");
+    if (!dev_buf_in || !aligned256(dev_buf_in))
+        return fail(SPH_EINVAL, "pack buffer must be a 256-byte aligned device pointer");
+    const BatchBundle &bb = b->bundles[bundle];
+    BPackArgs a{};
+    a.cells = b->d_cells + bb.cell0;
+    a.buf = (char *)dev_buf_in;
+    a.S = bb.slots;
+    const int roles[R_NUM][2] = {{F_X, 0}, {F_X, 1}, {F_X, 2}, {F_V, 0}, {F_V, 1},
+                                 {F_V, 2}, {F_MASS, 0}, {F_H, 0}, {F_U, 0}, {F_RHO, 0},
+                                 {F_FGRADH, 0}, {F_BALS, 0}, {F_AVISC, 0}, {F_ADIFF, 0},
+                                 {F_TBIN, 0}};
+    for (int r = 0; r < R_NUM; ++r) a.src[r] = at(s, roles[r][0], roles[r][1]);
+    a.kernel_gamma = (float)p->kernel_gamma;
+    a.gamma = (float)p->gamma;
+    double bmax = b->box[0] > b->box[1] ? b->box[0] : b->box[1];
+    bmax = bmax > b->box[2] ? bmax : b->box[2];
+    a.delta = (float)(4e-6 * bmax);
+    if (bb.ncells == 0) return SPH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned g = (unsigned)bb.ncells;
+    if (loop == SPH_DENSITY) k_bpack<SPH_DENSITY><<<g, 128, 0, st>>>(a);
+    else if (loop == SPH_GRADIENT) k_bpack<SPH_GRADIENT><<<g, 128, 0, st>>>(a);
+    else k_bpack<SPH_FORCE><<<g, 128, 0, st>>>(a);
+    return launch_check("batch pack");
+}
+
+int sph_batch_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in,
+                       void *dev_buf_out, const sph_params *p, void *stream) {
+    if (int rc = check_batch(b, bundle)) return rc;
+    if (int rc = check_loop(loop)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_buf_out || !aligned256(dev_buf_out))
+        return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
+    const BatchBundle &bb = b->bundles[bundle];
+    BInteractArgs a{};
+    a.cells = b->d_cells + bb.cell0;
+    a.targets = b->d_targets + bb.target0;
+    a.items = b->d_items + bb.item0;
+    a.counter = b->d_counter + bundle;
+    a.nitems = (int)bb.nitems;
+    a.in = (const char *)dev_buf_in;
+    a.out = (char *)dev_buf_out;
+    a.S = bb.slots;
+    a.kernel_gamma = (float)p->kernel_gamma;
+    a.gamma = (float)p->gamma;
+    a.beta = (float)p->beta_visc;
+    double bmax = b->box[0] > b->box[1] ? b->box[0] : b->box[1];
+    bmax = bmax > b->box[2] ? bmax : b->box[2];
+    a.delta = (float)(4e-6 * bmax);
+    for (int d = 0; d < 3; ++d) {
+        a.shift_hi[d] = (float)b->box[d];
+        a.shift_lo[d] = (float)(b->box[d] - (double)a.shift_hi[d]);
+    }
+    a.active_bin = p->active_bin;
+    a.pa.beta = a.beta;
+    a.pa.kernel_gamma = a.kernel_gamma;
+    a.pa.gamma = a.gamma;
+    a.pa.delta = a.delta;
+    a.pa.active_bin = a.active_bin;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (bb.nitems == 0) return SPH_OK;
+    if (int rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st),
+                            "reset work queue"))
+        return rc;
+    if (loop == SPH_DENSITY) return dispatch_binteract<SPH_DENSITY>(b->threads, a, st);
+    if (loop == SPH_GRADIENT) return dispatch_binteract<SPH_GRADIENT>(b->threads, a, st);
+    return dispatch_binteract<SPH_FORCE>(b->threads, a, st);
+}
+
+int sph_batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const void *dev_buf_out,
+                     const void *dev_buf_in, void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (int rc = check_batch(b, bundle)) return rc;
+    if (int rc = check_loop(loop)) return rc;
+    if (!dev_buf_in || !dev_buf_out) return fail(SPH_EINVAL, "NULL buffer");
+    const BatchBundle &bb = b->bundles[bundle];
+    BUnpackArgs a{};
+    a.cells = b->d_cells + bb.cell0;
+    a.targets = b->d_targets + bb.target0;
+    a.out = (const char *)dev_buf_out;
+    const int64_t S = bb.slots;
+    int64_t perm_off = loop == SPH_DENSITY ? BLayout<SPH_DENSITY>::perm(S)
+                       : loop == SPH_GRADIENT ? BLayout<SPH_GRADIENT>::perm(S)
+                                              : BLayout<SPH_FORCE>::perm(S);
+    a.perm = reinterpret_cast<const int32_t *>((const char *)dev_buf_in + perm_off);
+    a.S = S;
+    int k = 0;
+    if (loop == SPH_DENSITY) {
+        for (int f : {F_RHO, F_RHODH, F_WCOUNT, F_WCOUNTDH, F_DIVV}) a.dst[k++] = at(s, f, 0);
+        for (int c = 0; c < 3; ++c) a.dst[k++] = at(s, F_ROTV, c);
+    } else if (loop == SPH_GRADIENT) {
+        a.dst[k++] = at(s, F_VSIGG, 0);
+        a.dst[k++] = at(s, F_LAPU, 0);
+    } else {
+        for (int c = 0; c < 3; ++c) a.dst[k++] = at(s, F_A, c);
+        for (int f : {F_UDT, F_HDT, F_VSIG}) a.dst[k++] = at(s, f, 0);
+    }
+    if (bb.ntargets == 0) return SPH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned g = (unsigned)bb.ntargets;
+    if (loop == SPH_DENSITY) k_bunpack<SPH_DENSITY><<<g, 128, 0, st>>>(a);
+    else if (loop == SPH_GRADIENT) k_bunpack<SPH_GRADIENT><<<g, 128, 0, st>>>(a);
+    else k_bunpack<SPH_FORCE><<<g, 128, 0, st>>>(a);
+    return launch_check("batch unpack");
+}
+
+int sph_batch_offload_loop(sph_store s, sph_batch b, int loop, void *dev_buf_in,
+                           void *dev_buf_out, const sph_params *p, void *stream) {
+    if (int rc = sph_init(s, loop, p, stream)) return rc;
+    if (!b) return fail(SPH_EINVAL, "NULL batch handle");
+    for (int k = 0; k < (int)b->bundles.size(); ++k) {
+        if (int rc = sph_batch_pack(s, b, loop, k, dev_buf_in, p, stream)) return rc;
+        if (int rc = sph_batch_interact(b, loop, k, dev_buf_in, dev_buf_out, p, stream)) return rc;
+        if (int rc = sph_batch_unpack(s, b, loop, k, dev_buf_out, dev_buf_in, stream)) return rc;
+    }
+    return sph_ghost(s, loop, p, stream);
+}
+
+int sph_batch_destroy(sph_batch b) {
+    if (!b) return SPH_OK;
+    batch_free(b);
+    delete b;
+    return SPH_OK;
 }
 }  // extern "C"

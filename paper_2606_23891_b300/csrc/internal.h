@@ -2,6 +2,7 @@
 // records.  Not part of the public C-ABI (include/sph.h).
 #pragma once
 
+#include <array>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -107,7 +108,49 @@ struct sph_tasks_s {
     int device = -1;
 };
 
+// ---- batched (cell-dedup) pipeline records --------------------------------
+// A cell of a batched bundle: particles [p0, p0+n) of the store, packed at
+// bundle slots [slot, slot+n) (octant-sorted inside the cell).
+struct BCellDev {
+    int32_t p0, n, slot, pad;
+};
+// A target cell: its local cell index and its 27 neighbours (local index or
+// -1 for an empty cell) in (dz, dy, dx) order, each with the periodic shift
+// of the neighbour's particles (code + 1 per dimension in 2-bit fields).
+struct BTargetDev {
+    int32_t cell;
+    int32_t nbr[27];
+    uint8_t shift[27];
+    uint8_t pad[5];
+};
+// A work item (one warp): particles [i0, i0 + 32) of target `target`.
+struct BItemDev {
+    int32_t target, i0;
+};
+struct BatchBundle {
+    int64_t cell0 = 0, ncells = 0, slots = 0;
+    int64_t target0 = 0, ntargets = 0;
+    int64_t item0 = 0, nitems = 0;
+};
+
+struct sph_batch_s {
+    int64_t n = 0;
+    int threads = 128;
+    double box[3] = {0, 0, 0};
+    std::vector<BatchBundle> bundles;
+    std::vector<BCellDev> cells;
+    std::vector<BTargetDev> targets;
+    std::vector<BItemDev> items;
+    int64_t max_slots = 0, max_targets = 0;
+    BCellDev *d_cells = nullptr;
+    BTargetDev *d_targets = nullptr;
+    BItemDev *d_items = nullptr;
+    unsigned int *d_counter = nullptr;  // work-queue head, one per bundle
+};
+
 namespace sph {
+int build_batch(const sph_tasks_s *T, const sph_batch_params *bp, sph_batch_s *B);
+
 int build_tasks(int64_t n, const double *x, const float *h,
                 const sph_grid_params *gp, int64_t *perm_out, sph_tasks_s *T);
 

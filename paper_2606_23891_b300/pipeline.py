@@ -174,7 +174,39 @@ class Offload:
         cnt = np.diff(cs)
         return cnt[ci] + np.where(cj >= 0, cnt[np.maximum(cj, 0)], 0)
 
+    # -- batched (cell-dedup) cycle --------------------------------------
+    def batch(self, max_target_cells: int = 0, threads: int = 128) -> None:
+        """Build the batched plan for this particle set and its buffers."""
+        self.close_batch()
+        self.bplan = sph.sph_batch_build(self.tasks, max_target_cells, threads)
+        self.binfo = sph.sph_batch_info(self.bplan)
+        nin = max(sph.sph_batch_buffer_bytes(self.bplan, l, 0) for l in range(3))
+        nout = max(sph.sph_batch_buffer_bytes(self.bplan, l, 1) for l in range(3))
+        self.bbuf_in = torch.empty(max(nin, 256), dtype=torch.uint8, device=self.device)
+        self.bbuf_out = torch.empty(max(nout, 256), dtype=torch.uint8, device=self.device)
+
+    def use_batch_of(self, other: "Offload") -> None:
+        """Share another Offload's batched plan and buffers."""
+        self.bplan, self.binfo = other.bplan, other.binfo
+        self.bbuf_in, self.bbuf_out = other.bbuf_in, other.bbuf_out
+        self.bshared = True
+
+    def batch_loop(self, loop: int) -> None:
+        sph.sph_batch_offload_loop(self.store, self.bplan, loop, self.bbuf_in.data_ptr(),
+                                   self.bbuf_out.data_ptr(), self.params, self.stream)
+
+    def batch_step(self) -> None:
+        for loop in (sph.SPH_DENSITY, sph.SPH_GRADIENT, sph.SPH_FORCE):
+            self.batch_loop(loop)
+
+    def close_batch(self) -> None:
+        if getattr(self, "bplan", None) is not None:
+            if not getattr(self, "bshared", False):
+                sph.sph_batch_destroy(self.bplan)
+            self.bplan = None
+
     def close(self) -> None:
+        self.close_batch()
         if getattr(self, "store", None) is not None:
             sph.sph_store_destroy(self.store)
             self.store = None

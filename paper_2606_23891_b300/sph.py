@@ -53,6 +53,11 @@ class GridParams(C.Structure):
                 ("bundle_max_slots", C.c_int64)]
 
 
+class BatchParams(C.Structure):
+    _fields_ = [("max_target_cells", C.c_int64), ("threads", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 def params(gamma=5.0 / 3.0, kernel_gamma=1.825742, beta_visc=3.0,
            balsara_eps=1e-4, active_bin=0) -> Params:
     return Params(gamma, kernel_gamma, beta_visc, balsara_eps, active_bin, 0)
@@ -107,6 +112,14 @@ def lib() -> C.CDLL:
         "sph_count_pairs": (i, [p, i, i, p, p, p, p]),
         "sph_sync": (i, [p]),
         "sph_offload_loop_noalloc": (i, [p, p, i, p, p]),
+        "sph_batch_build": (i, [p, p, p]),
+        "sph_batch_info": (i, [p, p]),
+        "sph_batch_buffer_bytes": (sz, [p, i, i]),
+        "sph_batch_pack": (i, [p, p, i, i, p, p, p]),
+        "sph_batch_interact": (i, [p, i, i, p, p, p, p]),
+        "sph_batch_unpack": (i, [p, p, i, i, p, p, p]),
+        "sph_batch_offload_loop": (i, [p, p, i, p, p, p, p]),
+        "sph_batch_destroy": (i, [p]),
         "sph_store_create_host": (i, [i64, i, u64, p, sz, p]),
         "sph_store_import_host": (i, [p, p, p, i]),
         "sph_store_export_host": (i, [p, p, p, i]),
@@ -286,6 +299,46 @@ def sph_offload_loop_host(s, t, loop: int, host_in, host_out, dev_in, dev_out, p
     arr = lambda v: (C.c_void_p * 2)(*[int(x) for x in v])
     _ok(lib().sph_offload_loop_host(s, t, loop, arr(host_in), arr(host_out), arr(dev_in),
                                     arr(dev_out), C.byref(p), arr(streams), nthreads))
+
+
+def sph_batch_build(t, max_target_cells: int = 0, threads: int = 128):
+    h = C.c_void_p()
+    bp = BatchParams(max_target_cells, threads, 0)
+    _ok(lib().sph_batch_build(t, C.byref(bp), C.byref(h)))
+    return h
+
+
+def sph_batch_info(b) -> dict:
+    info = (C.c_int64 * 6)()
+    _ok(lib().sph_batch_info(b, info))
+    return dict(zip(("nbundles", "max_slots", "items", "threads", "max_targets", "cells"),
+                    list(info)))
+
+
+def sph_batch_buffer_bytes(b, loop: int, in_or_out: int) -> int:
+    return lib().sph_batch_buffer_bytes(b, loop, in_or_out)
+
+
+def sph_batch_pack(s, b, loop: int, bundle: int, dev_in: int, p: Params, stream: int = 0):
+    _ok(lib().sph_batch_pack(s, b, loop, bundle, dev_in, C.byref(p), stream))
+
+
+def sph_batch_interact(b, loop: int, bundle: int, dev_in: int, dev_out: int, p: Params,
+                       stream: int = 0):
+    _ok(lib().sph_batch_interact(b, loop, bundle, dev_in, dev_out, C.byref(p), stream))
+
+
+def sph_batch_unpack(s, b, loop: int, bundle: int, dev_out: int, dev_in: int, stream: int = 0):
+    _ok(lib().sph_batch_unpack(s, b, loop, bundle, dev_out, dev_in, stream))
+
+
+def sph_batch_offload_loop(s, b, loop: int, dev_in: int, dev_out: int, p: Params,
+                           stream: int = 0):
+    _ok(lib().sph_batch_offload_loop(s, b, loop, dev_in, dev_out, C.byref(p), stream))
+
+
+def sph_batch_destroy(b) -> None:
+    _ok(lib().sph_batch_destroy(b))
 
 
 def sph_sync(stream: int = 0) -> None:
