@@ -389,7 +389,13 @@ def run_ours(args, ws, rank, local):
     n = base.n
     per_layout = {}
     head = None
-    base.batch(threads=args.batch_threads)
+    tuning = None
+    if "batched" in args.pipelines and args.autotune:
+        from paper_2606_23891_b300.autotune import tune
+        tuning = tune(base, reps=1)
+        args.batch_threads = tuning["threads"]
+    else:
+        base.batch(threads=args.batch_threads)
     bslots = base.binfo["max_slots"]
 
     def loop_stats(st, ms_step, pipeline):
@@ -436,6 +442,24 @@ def run_ours(args, ws, rank, local):
     off, total_ms, timer, cl, st, cnt = head
     ms_step = total_ms / args.steps
     value = sum(pairs) * ws / (ms_step * 1e-3)
+    graph = None
+    if args.head_pipeline == "batched":
+        # the same step recorded once into a CUDA graph and replayed
+        from paper_2606_23891_b300.autotune import GraphStep
+        gs = GraphStep(off)
+        for _ in range(args.warmup):
+            gs.replay()
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record()
+        for _ in range(args.steps):
+            gs.replay()
+        g1.record()
+        torch.cuda.synchronize()
+        gms = barrier_max(g0.elapsed_time(g1), ws) / args.steps
+        graph = {"ms_per_step": gms, "pair_interactions_per_s": sum(pairs) * ws / (gms * 1e-3)}
+        del gs
     # dominant kernel of the headline layout
     top = max(st, key=lambda k: st[k])
     stage, loop = top
@@ -484,6 +508,7 @@ def run_ours(args, ws, rank, local):
                          "scans (neighbour densities included), %.1f s"
                          % (args.cpu_sample, args.n_side, t)}
     cfg_vals = {"tasks": base.info["ntasks"], "bundles": base.info["nbundles"],
+                "bbundles": base.binfo["nbundles"],
                 "store_gb": off.nbytes / 1e9, "buf_gb": base.buf_in.numel() / 1e9}
     staged = None
     if args.host_steps > 0:
@@ -503,7 +528,8 @@ def run_ours(args, ws, rank, local):
             "workload": "gresho256: Gresho-vortex shaped jittered 256^3 lattice, "
                         "64^3 cells of 55..73 particles, all loops",
             "particles": n, "layout": args.headline, "pipeline": args.head_pipeline,
-            "batch_threads": args.batch_threads, "tasks": cfg_vals["tasks"],
+            "batch_threads": args.batch_threads,
+            "batch_bundles": cfg_vals["bbundles"], "tasks": cfg_vals["tasks"],
             "bundles": cfg_vals["bundles"], "bundle_max_slots": args.bundle_slots,
             "slots_per_loop": slots, "candidates_per_loop": ncand,
             "pairs": dict(zip(LOOP_NAMES, pairs)),
@@ -520,6 +546,8 @@ def run_ours(args, ws, rank, local):
         "cpu_baseline": cpu,
         "clocks": cl,
         "layouts": per_layout,
+        "cuda_graph": graph,
+        "autotune": tuning,
         "host_staged": staged,
     }
     if rank == 0:
@@ -545,6 +573,7 @@ def main(argv=None):
     ap.add_argument("--pipelines", default="plain,batched")
     ap.add_argument("--head-pipeline", default="batched")
     ap.add_argument("--batch-threads", type=int, default=128)
+    ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--host-steps", type=int, default=2)
     ap.add_argument("--host-layouts", default="aos,pack_force_type,soa")
     ap.add_argument("--host-bundle-slots", type=int, default=1 << 24)

@@ -80,3 +80,30 @@ def test_batched_steps_are_reproducible():
     b = off.export()
     for k in a:
         np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_graph_replay_matches_the_eager_step():
+    from paper_2606_23891_b300.autotune import GraphStep
+    f = ragged(24, 8)
+    off = Offload(f, layout="pack_shared_type")
+    off.batch(max_target_cells=60, threads=128)
+    off.batch_step()
+    want = off.export()
+    g = GraphStep(off)
+    for _ in range(2):
+        g.replay()
+        got = off.export()
+        for k in want:
+            np.testing.assert_array_equal(got[k], want[k], err_msg=k)
+
+
+def test_autotuner_leaves_the_fastest_valid_plan():
+    from paper_2606_23891_b300.autotune import tune
+    f = ragged(24, 8)
+    off = Offload(f, layout="pack_force_type")
+    res = tune(off, reps=1)
+    assert len(res["table"]) >= 3
+    assert res["ms"] == min(r["ms"] for r in res["table"])
+    assert off.binfo["threads"] == res["threads"]
+    off.batch_step()
+    check_physics(f, off.export())
