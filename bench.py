@@ -149,7 +149,42 @@ def oracle_sample(f, nsample: int, seed: int):
     out = oracle.chain(f, oracle.params(), sel)
     dt = time.perf_counter() - t
     pairs = sum(out["pairs"].values())
+    oracle_sample.last = (sel, out)
     return pairs, dt
+
+
+def precision_study(off, f, sel, ref, steps):
+    """Per-loop error of the mixed-precision and the all-FP64 batched paths
+    against the oracle on the sampled particles, and the FP64 step time."""
+    import torch
+    import oracle
+    from oracle import compare
+    H = oracle.KERNEL_GAMMA * np.asarray(f["h"][sel], np.float64)
+    res = {"sample": int(len(sel))}
+    off.batch_step()
+    got = off.export()
+    e = compare.errors({k: v[sel] for k, v in got.items()}, ref, H)
+    res["mixed"] = {"per_loop": compare.per_loop(e), "fields": e}
+    off.fp64_step()                                   # warm-up (allocates buffers)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        off.fp64_step()
+    e1.record()
+    torch.cuda.synchronize()
+    res["fp64_ms_per_step"] = e0.elapsed_time(e1) / steps
+    got = off.export()
+    e = compare.errors({k: v[sel] for k, v in got.items()}, ref, H)
+    res["fp64"] = {"per_loop": compare.per_loop(e), "fields": e}
+    res["metrics"] = ("relative error for rho, wcount, f_gradh, pressure, soundspeed, "
+                      "v_sig; err / (3 rho / H) and err / max(|x|, 3 wcount / H) for the "
+                      "h-derivatives; max err / rms for div v, curl v, laplace u, a, "
+                      "du/dt, dh/dt; absolute error for the Balsara switch")
+    off.f64_in = off.f64_out = None
+    torch.cuda.empty_cache()
+    return res
 
 
 def cpu_cores() -> int:
@@ -507,6 +542,11 @@ def run_ours(args, ws, rank, local):
                          "density->ghost->gradient->force chain by brute-force O(N) "
                          "scans (neighbour densities included), %.1f s"
                          % (args.cpu_sample, args.n_side, t)}
+    precision = None
+    if cpu is not None and args.precision_steps > 0 and args.head_pipeline == "batched":
+        sel, ref = oracle_sample.last
+        precision = precision_study(off, f, sel, ref, args.precision_steps)
+        precision["mixed_ms_per_step"] = ms_step
     cfg_vals = {"tasks": base.info["ntasks"], "bundles": base.info["nbundles"],
                 "bbundles": base.binfo["nbundles"],
                 "store_gb": off.nbytes / 1e9, "buf_gb": base.buf_in.numel() / 1e9}
@@ -549,6 +589,7 @@ def run_ours(args, ws, rank, local):
         "cuda_graph": graph,
         "autotune": tuning,
         "host_staged": staged,
+        "precision": precision,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -570,6 +611,8 @@ def main(argv=None):
     ap.add_argument("--n-side", type=int, default=N_SIDE)
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--ref-sample", type=int, default=2)
+    ap.add_argument("--precision-steps", type=int, default=2,
+                    help="timed steps of the all-FP64 path (0: skip the precision study)")
     ap.add_argument("--pipelines", default="plain,batched")
     ap.add_argument("--head-pipeline", default="batched")
     ap.add_argument("--batch-threads", type=int, default=128)

@@ -358,6 +358,14 @@ int sph_batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const void 
 int sph_batch_offload_loop(sph_store s, sph_batch b, int loop, void *dev_buf_in,
                            void *dev_buf_out, const sph_params *p, void *stream);
 int sph_batch_destroy(sph_batch b);
+
+/* All-FP64 variant of the batched cycle (precision study): the same cells and
+ * results, every arithmetic step in FP64 (positions, separations, kernel
+ * values, sums, ghost), results rounded to the FP32 store once.  Buffers of
+ * sph_batch_buffer_bytes_fp64(b, 0 / 1) bytes. */
+size_t sph_batch_buffer_bytes_fp64(sph_batch b, int in_or_out);
+int sph_batch_offload_loop_fp64(sph_store s, sph_batch b, int loop, void *dev_buf_in,
+                                void *dev_buf_out, const sph_params *p, void *stream);
 int sph_offload_loop_noalloc(sph_store s, sph_tasks t, int loop, const sph_params *p,
                              void *stream);
 

@@ -1,0 +1,56 @@
+"""Error metrics of GPU outputs against the oracle's (test infrastructure).
+
+One number per output field, each on the scale the parity bars use:
+relative error for the positive sums (rho, wcount, f_gradh, pressure,
+soundspeed, the two signal velocities), the natural scales 3 rho / H and
+max(|wcount_dh|, 3 wcount / H) for the cancelling h-derivatives, max error
+over the field's rms for the signed vector-like sums (div v, curl v,
+Laplacian of u, a, du/dt, dh/dt), and the absolute error of the Balsara
+switch (a number in [0, 1]).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+RELATIVE = ("rho", "wcount", "f_gradh", "pressure", "soundspeed", "v_sig_grad", "v_sig")
+RMS = ("laplace_u", "div_v", "rot_v", "a", "u_dt", "h_dt")
+LOOP_OF = {"rho": "density", "rho_dh": "density", "wcount": "density",
+           "wcount_dh": "density", "div_v": "density", "rot_v": "density",
+           "f_gradh": "density", "pressure": "density", "soundspeed": "density",
+           "balsara": "density", "v_sig_grad": "gradient", "laplace_u": "gradient",
+           "a": "force", "u_dt": "force", "h_dt": "force", "v_sig": "force"}
+
+
+def _rel(a, b):
+    d = np.abs(a - b)
+    return np.where(d == 0.0, 0.0, d / np.maximum(np.abs(b), 1e-300))
+
+
+def errors(got: dict, ref: dict, H) -> dict:
+    """Per-field error of ``got`` (arrays indexed like ``ref``) against the
+    oracle's ``ref``; ``H`` is the kernel support of the same particles."""
+    g = {k: np.asarray(got[k], np.float64) for k in LOOP_OF}
+    r = {k: np.asarray(ref[k], np.float64) for k in LOOP_OF}
+    H = np.asarray(H, np.float64)
+    out = {}
+    for k in RELATIVE:
+        out[k] = float(np.max(_rel(g[k], r[k]), initial=0.0))
+    out["rho_dh"] = float(np.max(np.abs(g["rho_dh"] - r["rho_dh"]) / (3 * r["rho"] / H),
+                                 initial=0.0))
+    sc = np.maximum(np.abs(r["wcount_dh"]), 3 * r["wcount"] / H)
+    out["wcount_dh"] = float(np.max(np.abs(g["wcount_dh"] - r["wcount_dh"]) / sc, initial=0.0))
+    for k in RMS:
+        s = np.sqrt(np.mean(r[k] * r[k])) if r[k].size else 0.0
+        e = float(np.max(np.abs(g[k] - r[k]), initial=0.0))
+        out[k] = e / s if s > 0 else e
+    out["balsara"] = float(np.max(np.abs(g["balsara"] - r["balsara"]), initial=0.0))
+    return out
+
+
+def per_loop(err: dict) -> dict:
+    """Worst field error of each loop."""
+    res = {}
+    for k, v in err.items():
+        loop = LOOP_OF[k]
+        res[loop] = max(res.get(loop, 0.0), v)
+    return res

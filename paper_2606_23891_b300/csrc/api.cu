@@ -15,6 +15,7 @@
 #include "physics_kernels.cuh"
 #include "store_kernels.cuh"
 #include "batch_kernels.cuh"
+#include "fp64_kernels.cuh"
 
 namespace sph {
 
@@ -944,5 +945,86 @@ int sph_batch_destroy(sph_batch b) {
     batch_free(b);
     delete b;
     return SPH_OK;
+}
+
+size_t sph_batch_buffer_bytes_fp64(sph_batch b, int in_or_out) {
+    if (!b || (in_or_out != 0 && in_or_out != 1)) return 0;
+    if (in_or_out == 0) return (size_t)D64Layout::bytes(b->max_slots);
+    return (size_t)D64Layout::out_bytes(SPH_DENSITY, b->max_slots);
+}
+
+int sph_batch_offload_loop_fp64(sph_store s, sph_batch b, int loop, void *dev_buf_in,
+                                void *dev_buf_out, const sph_params *p, void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (!b) return fail(SPH_EINVAL, "NULL batch handle");
+    if (int rc = check_loop(loop)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (s->n != b->n) return fail(SPH_EINVAL, "store and batch disagree on particle count");
+    if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_buf_out || !aligned256(dev_buf_out))
+        return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
+    if (int rc = sph_init(s, loop, p, stream)) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int roles[R_NUM][2] = {{F_X, 0}, {F_X, 1}, {F_X, 2}, {F_V, 0}, {F_V, 1},
+                                 {F_V, 2}, {F_MASS, 0}, {F_H, 0}, {F_U, 0}, {F_RHO, 0},
+                                 {F_FGRADH, 0}, {F_BALS, 0}, {F_AVISC, 0}, {F_ADIFF, 0},
+                                 {F_TBIN, 0}};
+    for (int k = 0; k < (int)b->bundles.size(); ++k) {
+        const BatchBundle &bb = b->bundles[k];
+        if (bb.ncells == 0 || bb.ntargets == 0) continue;
+        D64PackArgs pa{};
+        pa.cells = b->d_cells + bb.cell0;
+        pa.buf = (char *)dev_buf_in;
+        pa.S = bb.slots;
+        for (int r = 0; r < R_NUM; ++r) pa.src[r] = at(s, roles[r][0], roles[r][1]);
+        pa.kernel_gamma = p->kernel_gamma;
+        k_pack64<<<(unsigned)bb.ncells, 128, 0, st>>>(pa);
+        if (int rc = launch_check("fp64 pack")) return rc;
+        D64Args ia{};
+        ia.cells = b->d_cells + bb.cell0;
+        ia.targets = b->d_targets + bb.target0;
+        ia.in = (const char *)dev_buf_in;
+        ia.out = (char *)dev_buf_out;
+        ia.S = bb.slots;
+        ia.gamma = p->gamma;
+        ia.beta = p->beta_visc;
+        for (int d = 0; d < 3; ++d) ia.box[d] = b->box[d];
+        ia.active_bin = p->active_bin;
+        const unsigned g = (unsigned)bb.ntargets;
+        if (loop == SPH_DENSITY) k_interact64<SPH_DENSITY><<<g, 128, 0, st>>>(ia);
+        else if (loop == SPH_GRADIENT) k_interact64<SPH_GRADIENT><<<g, 128, 0, st>>>(ia);
+        else k_interact64<SPH_FORCE><<<g, 128, 0, st>>>(ia);
+        if (int rc = launch_check("fp64 interaction kernel")) return rc;
+        D64UnpackArgs ua{};
+        ua.cells = b->d_cells + bb.cell0;
+        ua.targets = b->d_targets + bb.target0;
+        ua.out = (const double *)dev_buf_out;
+        ua.perm = reinterpret_cast<const int32_t *>((const char *)dev_buf_in +
+                                                    D64Layout::perm(bb.slots));
+        int q = 0;
+        if (loop == SPH_DENSITY) {
+            for (int f : {F_RHO, F_RHODH, F_WCOUNT, F_WCOUNTDH, F_DIVV}) ua.dst[q++] = at(s, f, 0);
+            for (int c = 0; c < 3; ++c) ua.dst[q++] = at(s, F_ROTV, c);
+        } else if (loop == SPH_GRADIENT) {
+            ua.dst[q++] = at(s, F_VSIGG, 0);
+            ua.dst[q++] = at(s, F_LAPU, 0);
+        } else {
+            for (int c = 0; c < 3; ++c) ua.dst[q++] = at(s, F_A, c);
+            for (int f : {F_UDT, F_HDT, F_VSIG}) ua.dst[q++] = at(s, f, 0);
+        }
+        if (loop == SPH_DENSITY) k_unpack64<SPH_DENSITY><<<g, 128, 0, st>>>(ua);
+        else if (loop == SPH_GRADIENT) k_unpack64<SPH_GRADIENT><<<g, 128, 0, st>>>(ua);
+        else k_unpack64<SPH_FORCE><<<g, 128, 0, st>>>(ua);
+        if (int rc = launch_check("fp64 unpack")) return rc;
+    }
+    if (loop != SPH_DENSITY || s->n == 0) return SPH_OK;
+    GhostArgs ga{};
+    const int groles[14][2] = {{F_MASS, 0}, {F_H, 0}, {F_U, 0}, {F_RHO, 0}, {F_RHODH, 0},
+                               {F_WCOUNT, 0}, {F_DIVV, 0}, {F_ROTV, 0}, {F_ROTV, 1},
+                               {F_ROTV, 2}, {F_FGRADH, 0}, {F_PRES, 0}, {F_CS, 0},
+                               {F_BALS, 0}};
+    for (int r = 0; r < 14; ++r) ga.f[r] = at(s, groles[r][0], groles[r][1]);
+    k_ghost64<<<grid_for(s->n, 256), 256, 0, st>>>(ga, s->n, p->kernel_gamma, p->gamma,
+                                                    p->balsara_eps);
+    return launch_check("fp64 ghost");
 }
 }  // extern "C"

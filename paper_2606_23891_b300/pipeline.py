@@ -199,7 +199,19 @@ class Offload:
         for loop in (sph.SPH_DENSITY, sph.SPH_GRADIENT, sph.SPH_FORCE):
             self.batch_loop(loop)
 
+    def fp64_step(self) -> None:
+        """The batched step with every arithmetic step in FP64."""
+        if getattr(self, "f64_in", None) is None:
+            nin = sph.sph_batch_buffer_bytes_fp64(self.bplan, 0)
+            nout = sph.sph_batch_buffer_bytes_fp64(self.bplan, 1)
+            self.f64_in = torch.empty(max(nin, 256), dtype=torch.uint8, device=self.device)
+            self.f64_out = torch.empty(max(nout, 256), dtype=torch.uint8, device=self.device)
+        for loop in (sph.SPH_DENSITY, sph.SPH_GRADIENT, sph.SPH_FORCE):
+            sph.sph_batch_offload_loop_fp64(self.store, self.bplan, loop, self.f64_in.data_ptr(),
+                                            self.f64_out.data_ptr(), self.params, self.stream)
+
     def close_batch(self) -> None:
+        self.f64_in = self.f64_out = None
         if getattr(self, "bplan", None) is not None:
             if not getattr(self, "bshared", False):
                 sph.sph_batch_destroy(self.bplan)

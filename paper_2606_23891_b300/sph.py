@@ -120,6 +120,8 @@ def lib() -> C.CDLL:
         "sph_batch_unpack": (i, [p, p, i, i, p, p, p]),
         "sph_batch_offload_loop": (i, [p, p, i, p, p, p, p]),
         "sph_batch_destroy": (i, [p]),
+        "sph_batch_buffer_bytes_fp64": (sz, [p, i]),
+        "sph_batch_offload_loop_fp64": (i, [p, p, i, p, p, p, p]),
         "sph_store_create_host": (i, [i64, i, u64, p, sz, p]),
         "sph_store_import_host": (i, [p, p, p, i]),
         "sph_store_export_host": (i, [p, p, p, i]),
@@ -335,6 +337,15 @@ def sph_batch_unpack(s, b, loop: int, bundle: int, dev_out: int, dev_in: int, st
 def sph_batch_offload_loop(s, b, loop: int, dev_in: int, dev_out: int, p: Params,
                            stream: int = 0):
     _ok(lib().sph_batch_offload_loop(s, b, loop, dev_in, dev_out, C.byref(p), stream))
+
+
+def sph_batch_buffer_bytes_fp64(b, in_or_out: int) -> int:
+    return lib().sph_batch_buffer_bytes_fp64(b, in_or_out)
+
+
+def sph_batch_offload_loop_fp64(s, b, loop: int, dev_in: int, dev_out: int, p: Params,
+                                stream: int = 0):
+    _ok(lib().sph_batch_offload_loop_fp64(s, b, loop, dev_in, dev_out, C.byref(p), stream))
 
 
 def sph_batch_destroy(b) -> None:
