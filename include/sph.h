@@ -359,6 +359,50 @@ int sph_batch_offload_loop(sph_store s, sph_batch b, int loop, void *dev_buf_in,
                            void *dev_buf_out, const sph_params *p, void *stream);
 int sph_batch_destroy(sph_batch b);
 
+/* ---- adaptive plan for clustered particle sets -------------------------
+ * A uniform grid needs cell edges >= the largest support, so when h spans
+ * decades (clustered sets) its cells hold up to millions of particles.  The
+ * tree plan replaces the grid's cells by the leaves of an octree over the
+ * particles' Morton keys (21 bits per dimension; positions are clamped into
+ * the box the way the grid builder clamps them): a node is split while it
+ * holds more than leaf_max particles.  Each leaf's neighbour entries are all
+ * (leaf, periodic shift) pairs whose particle bounding boxes are closer than
+ * max(H_max of either leaf) + 4e-6 * (largest box edge), found by a pruned
+ * walk of the tree; the batched kernels then run unchanged over those lists.
+ * host_perm_out[k] receives the original index of the k-th particle in leaf
+ * (Morton) order, to be passed to sph_store_import.  Requires every support
+ * to be below half the smallest box edge (one periodic image per pair);
+ * SPH_EUNSUPPORTED otherwise.  Host inputs, uploads the plan to the current
+ * device. */
+typedef struct {
+    double box[3];
+    double kernel_gamma;
+    int32_t leaf_max;    /* 8 .. 2048 */
+    int32_t reserved;    /* must be 0 */
+} sph_tree_params;
+int sph_batch_build_tree(int64_t n, const double *host_x, const float *host_h,
+                         const sph_tree_params *tp, const sph_batch_params *bp,
+                         int64_t *host_perm_out, sph_batch *out);
+/* The tree plan's leaves and neighbour entries, on the host only (no device
+ * call): leaf l holds Morton-ordered particles [leaf_start[l], leaf_start[l+1])
+ * (arrays of n + 1 entries suffice), its entries are nb[nb_start[l] ..
+ * nb_start[l+1]), each (leaf << 6) | shift code.  *nleaf_out and *nnb_out
+ * receive the counts; SPH_EINVAL if nb_cap < *nnb_out (nb may then be NULL:
+ * call once to size nb). */
+int sph_tree_plan(int64_t n, const double *host_x, const float *host_h,
+                  const sph_tree_params *tp, int64_t *host_perm_out,
+                  int64_t *host_leaf_start, int64_t *nleaf_out, int64_t *host_nb_start,
+                  int32_t *host_nb, int64_t nb_cap, int64_t *nnb_out);
+/* info[0] plan kind (0 grid, 1 tree), [1] cells or leaves with particles,
+ * [2] largest cell / leaf population, [3] neighbour entries (all cells). */
+int sph_batch_plan_info(sph_batch b, int64_t info[4]);
+/* Pair interactions of `loop` over the plan, decided in FP64 as the loops
+ * define them (density and gradient: r < H_i; force: r < max(H_i, H_j),
+ * active i only), added to *dev_count (device uint64).  Uses dev_buf_in of
+ * sph_batch_buffer_bytes_fp64(b, 0) bytes as scratch. */
+int sph_batch_count_pairs(sph_store s, sph_batch b, int loop, void *dev_buf_in,
+                          const sph_params *p, unsigned long long *dev_count, void *stream);
+
 /* All-FP64 variant of the batched cycle (precision study): the same cells and
  * results, every arithmetic step in FP64 (positions, separations, kernel
  * values, sums, ghost), results rounded to the FP32 store once.  Buffers of

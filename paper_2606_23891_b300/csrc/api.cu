@@ -740,11 +740,45 @@ static void batch_free(sph_batch b) {
     if (b->d_cells) cudaFree(b->d_cells);
     if (b->d_targets) cudaFree(b->d_targets);
     if (b->d_items) cudaFree(b->d_items);
+    if (b->d_nbrs) cudaFree(b->d_nbrs);
     if (b->d_counter) cudaFree(b->d_counter);
+    b->d_nbrs = nullptr;
     b->d_cells = nullptr;
     b->d_targets = nullptr;
     b->d_items = nullptr;
     b->d_counter = nullptr;
+}
+
+// Copy a built plan to the current device; frees and deletes it on failure.
+static int batch_upload(sph_batch b, int rc, sph_batch *out) {
+    auto up = [&](void **dst, const void *src, size_t bytes, const char *what) -> int {
+        if (bytes == 0) return SPH_OK;
+        if (cudaMalloc(dst, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SPH_ENOMEM, "device allocation of %s (%zu bytes)", what, bytes);
+        }
+        if (!src) return cuda_check(cudaMemset(*dst, 0, bytes), what);
+        return cuda_check(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), what);
+    };
+    if (rc == SPH_OK &&
+        ((rc = up((void **)&b->d_cells, b->cells.data(), b->cells.size() * sizeof(BCellDev),
+                  "batch cells")) ||
+         (rc = up((void **)&b->d_targets, b->targets.data(),
+                  b->targets.size() * sizeof(BTargetDev), "batch targets")) ||
+         (rc = up((void **)&b->d_nbrs, b->nbrs.data(), b->nbrs.size() * sizeof(BNbrDev),
+                  "batch neighbour entries")) ||
+         (rc = up((void **)&b->d_items, b->items.data(), b->items.size() * sizeof(BItemDev),
+                  "batch items")) ||
+         (rc = up((void **)&b->d_counter, nullptr,
+                  (b->bundles.size() + 1) * sizeof(unsigned int), "batch counters")))) {
+    }
+    if (rc) {
+        batch_free(b);
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return SPH_OK;
 }
 
 int sph_batch_build(sph_tasks t, const sph_batch_params *bp, sph_batch *out) {
@@ -760,31 +794,45 @@ int sph_batch_build(sph_tasks t, const sph_batch_params *bp, sph_batch *out) {
     } catch (const std::bad_alloc &) {
         rc = fail(SPH_ENOMEM, "batch_build: host allocation failed");
     }
-    auto up = [&](void **dst, const void *src, size_t bytes, const char *what) -> int {
-        if (bytes == 0) return SPH_OK;
-        if (cudaMalloc(dst, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(SPH_ENOMEM, "device allocation of %s (%zu bytes)", what, bytes);
-        }
-        if (!src) return cuda_check(cudaMemset(*dst, 0, bytes), what);
-        return cuda_check(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), what);
-    };
-    if (rc == SPH_OK &&
-        ((rc = up((void **)&b->d_cells, b->cells.data(), b->cells.size() * sizeof(BCellDev),
-                  "batch cells")) ||
-         (rc = up((void **)&b->d_targets, b->targets.data(),
-                  b->targets.size() * sizeof(BTargetDev), "batch targets")) ||
-         (rc = up((void **)&b->d_items, b->items.data(), b->items.size() * sizeof(BItemDev),
-                  "batch items")) ||
-         (rc = up((void **)&b->d_counter, nullptr,
-                  (b->bundles.size() + 1) * sizeof(unsigned int), "batch counters")))) {
+    return batch_upload(b, rc, out);
+}
+
+int sph_batch_build_tree(int64_t n, const double *host_x, const float *host_h,
+                         const sph_tree_params *tp, const sph_batch_params *bp,
+                         int64_t *host_perm_out, sph_batch *out) {
+    if (!out) return fail(SPH_EINVAL, "NULL out");
+    *out = nullptr;
+    if (!tp || !bp) return fail(SPH_EINVAL, "NULL tree or batch params");
+    if (bp->reserved != 0) return fail(SPH_EINVAL, "batch params: reserved must be 0");
+    sph_batch b = new (std::nothrow) sph_batch_s;
+    if (!b) return fail(SPH_ENOMEM, "batch handle");
+    int rc;
+    try {
+        rc = build_batch_tree(n, host_x, host_h, tp, bp, host_perm_out, b);
+    } catch (const std::bad_alloc &) {
+        rc = fail(SPH_ENOMEM, "batch_build_tree: host allocation failed");
     }
-    if (rc) {
-        batch_free(b);
-        delete b;
-        return rc;
+    return batch_upload(b, rc, out);
+}
+
+int sph_tree_plan(int64_t n, const double *host_x, const float *host_h,
+                  const sph_tree_params *tp, int64_t *host_perm_out,
+                  int64_t *host_leaf_start, int64_t *nleaf_out, int64_t *host_nb_start,
+                  int32_t *host_nb, int64_t nb_cap, int64_t *nnb_out) {
+    try {
+        return tree_plan_host(n, host_x, host_h, tp, host_perm_out, host_leaf_start, nleaf_out,
+                              host_nb_start, host_nb, nb_cap, nnb_out);
+    } catch (const std::bad_alloc &) {
+        return fail(SPH_ENOMEM, "tree_plan: host allocation failed");
     }
-    *out = b;
+}
+
+int sph_batch_plan_info(sph_batch b, int64_t info[4]) {
+    if (!b || !info) return fail(SPH_EINVAL, "NULL argument");
+    info[0] = b->kind;
+    info[1] = b->plan_cells;
+    info[2] = b->plan_max_cell;
+    info[3] = b->plan_nbrs;
     return SPH_OK;
 }
 
@@ -859,6 +907,7 @@ int sph_batch_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in
     BInteractArgs a{};
     a.cells = b->d_cells + bb.cell0;
     a.targets = b->d_targets + bb.target0;
+    a.nbrs = b->d_nbrs;
     a.items = b->d_items + bb.item0;
     a.counter = b->d_counter + bundle;
     a.nitems = (int)bb.nitems;
@@ -982,6 +1031,7 @@ int sph_batch_offload_loop_fp64(sph_store s, sph_batch b, int loop, void *dev_bu
         D64Args ia{};
         ia.cells = b->d_cells + bb.cell0;
         ia.targets = b->d_targets + bb.target0;
+        ia.nbrs = b->d_nbrs;
         ia.in = (const char *)dev_buf_in;
         ia.out = (char *)dev_buf_out;
         ia.S = bb.slots;
@@ -1026,5 +1076,47 @@ int sph_batch_offload_loop_fp64(sph_store s, sph_batch b, int loop, void *dev_bu
     k_ghost64<<<grid_for(s->n, 256), 256, 0, st>>>(ga, s->n, p->kernel_gamma, p->gamma,
                                                     p->balsara_eps);
     return launch_check("fp64 ghost");
+}
+
+int sph_batch_count_pairs(sph_store s, sph_batch b, int loop, void *dev_buf_in,
+                          const sph_params *p, unsigned long long *dev_count, void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (!b) return fail(SPH_EINVAL, "NULL batch handle");
+    if (int rc = check_loop(loop)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (s->n != b->n) return fail(SPH_EINVAL, "store and batch disagree on particle count");
+    if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_count)
+        return fail(SPH_EINVAL, "buffer must be a 256-byte aligned device pointer; count non-NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int roles[R_NUM][2] = {{F_X, 0}, {F_X, 1}, {F_X, 2}, {F_V, 0}, {F_V, 1},
+                                 {F_V, 2}, {F_MASS, 0}, {F_H, 0}, {F_U, 0}, {F_RHO, 0},
+                                 {F_FGRADH, 0}, {F_BALS, 0}, {F_AVISC, 0}, {F_ADIFF, 0},
+                                 {F_TBIN, 0}};
+    for (int k = 0; k < (int)b->bundles.size(); ++k) {
+        const BatchBundle &bb = b->bundles[k];
+        if (bb.ncells == 0 || bb.ntargets == 0) continue;
+        D64PackArgs pa{};
+        pa.cells = b->d_cells + bb.cell0;
+        pa.buf = (char *)dev_buf_in;
+        pa.S = bb.slots;
+        for (int r = 0; r < R_NUM; ++r) pa.src[r] = at(s, roles[r][0], roles[r][1]);
+        pa.kernel_gamma = p->kernel_gamma;
+        k_pack64<<<(unsigned)bb.ncells, 128, 0, st>>>(pa);
+        if (int rc = launch_check("fp64 pack")) return rc;
+        D64Args ia{};
+        ia.cells = b->d_cells + bb.cell0;
+        ia.targets = b->d_targets + bb.target0;
+        ia.nbrs = b->d_nbrs;
+        ia.in = (const char *)dev_buf_in;
+        ia.S = bb.slots;
+        for (int d = 0; d < 3; ++d) ia.box[d] = b->box[d];
+        ia.active_bin = p->active_bin;
+        const unsigned g = (unsigned)bb.ntargets;
+        if (loop == SPH_DENSITY) k_count64<SPH_DENSITY><<<g, 128, 0, st>>>(ia, dev_count);
+        else if (loop == SPH_GRADIENT) k_count64<SPH_GRADIENT><<<g, 128, 0, st>>>(ia, dev_count);
+        else k_count64<SPH_FORCE><<<g, 128, 0, st>>>(ia, dev_count);
+        if (int rc = launch_check("fp64 pair count")) return rc;
+    }
+    return SPH_OK;
 }
 }  // extern "C"

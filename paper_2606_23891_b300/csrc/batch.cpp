@@ -1,113 +1,110 @@
-// Host builder of the batched (cell-dedup) offload pipeline.
+// Host builders of the batched (cell-dedup) offload pipeline.
 //
 // The batched pipeline runs the same cell-pair interactions as the per-task
 // cycle (Sec. 2.3: ready tasks fused into bundles), but a bundle is a range
-// of *target cells*: every cell the range needs (targets plus their 26
-// periodic neighbours) is packed once into the bundle buffer, and one
+// of *target cells*: every cell the range needs (targets plus their
+// neighbour entries) is packed once into the bundle buffer, and one
 // persistent launch computes, for every target particle, its sums over all
-// 27 neighbour cells.  Work items are (target cell, 32-particle chunk) pairs,
-// one per warp, in decreasing classes of estimated cost (a coarse
+// its neighbour entries.  Work items are (target cell, 32-particle chunk)
+// pairs, one per warp, in decreasing classes of estimated cost (a coarse
 // longest-first order, so uneven cells balance over the persistent warps)
 // and in cell order inside a class.
+//
+// Two plans produce the cells and their neighbour entries:
+//  - grid: the uniform cell grid of the task builder, 27 periodic
+//    neighbours per cell (empty ones dropped);
+//  - tree: leaves of an octree over Morton keys, split while a node holds
+//    more than leaf_max particles, with neighbour entries from a pruned walk
+//    over bounding boxes and support maxima (clustered particle sets, whose
+//    supports span decades, would put millions of particles in a grid cell).
+#include <parallel/algorithm>
+
 #include <algorithm>
+#include <cmath>
 #include <numeric>
+
+#include <omp.h>
 
 #include "internal.h"
 
 namespace sph {
 
-int build_batch(const sph_tasks_s *T, const sph_batch_params *bp, sph_batch_s *B) {
-    if (!T || !bp) return fail(SPH_EINVAL, "batch_build: bad arguments");
-    const int threads = bp->threads;
-    if (threads != 64 && threads != 128 && threads != 256)
-        return fail(SPH_EINVAL, "batch_build: threads must be 64, 128 or 256");
-    const int64_t ichunk = 32;  // one work item per warp
-    const int32_t *nc = T->ncell;
-    const int64_t ncells = (int64_t)nc[0] * nc[1] * nc[2];
-    auto count = [&](int64_t c) { return T->cell_start[c + 1] - T->cell_start[c]; };
-    B->threads = threads;
-    B->n = T->n;
-    for (int d = 0; d < 3; ++d) B->box[d] = T->box[d];
+namespace {
 
-    // targets: non-empty cells in index order, split into bundles
-    std::vector<int64_t> targets;
-    for (int64_t c = 0; c < ncells; ++c)
-        if (count(c) > 0) targets.push_back(c);
-    const int64_t per = bp->max_target_cells > 0 ? bp->max_target_cells
-                                                 : (int64_t)targets.size();
+// Cells (or leaves) with particles and their neighbour entries, with
+// global cell indices.
+struct GlobalPlan {
+    std::vector<int64_t> p0, cnt;      // store range of each cell
+    std::vector<int64_t> nb_start;     // CSR over cells
+    std::vector<int32_t> nb_cell;
+    std::vector<uint8_t> nb_code;
+};
+
+// Bundles of target cells, bundle-local cell tables, neighbour entries and
+// work items from a global plan.
+int assemble(const GlobalPlan &G, const sph_batch_params *bp, sph_batch_s *B) {
+    const int64_t ichunk = 32;  // one work item per warp
+    const int64_t ncells = (int64_t)G.cnt.size();
+    const int64_t per = bp->max_target_cells > 0 ? bp->max_target_cells : ncells;
     B->bundles.clear();
+    B->cells.clear();
+    B->targets.clear();
+    B->items.clear();
+    B->nbrs.clear();
     std::vector<int32_t> local((size_t)ncells, -1);
-    for (size_t t0 = 0; t0 < targets.size(); t0 += (size_t)per) {
-        const size_t t1 = std::min(targets.size(), t0 + (size_t)per);
+    for (int64_t t0 = 0; t0 < ncells; t0 += per) {
+        const int64_t t1 = std::min(ncells, t0 + per);
         BatchBundle bb;
-        // cells needed: targets and their 26 periodic neighbours
+        // cells needed: the targets and their neighbour entries, in index order
         std::vector<int64_t> need;
-        std::vector<std::array<int32_t, 27>> nbr_cell(t1 - t0);
-        std::vector<std::array<int32_t, 27>> nbr_shift(t1 - t0);
-        for (size_t k = t0; k < t1; ++k) {
-            const int64_t c = targets[k];
-            const int64_t ix = c % nc[0], iy = (c / nc[0]) % nc[1],
-                          iz = c / ((int64_t)nc[0] * nc[1]);
-            int e = 0;
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx, ++e) {
-                        int64_t q[3] = {ix + dx, iy + dy, iz + dz};
-                        int code = 0;
-                        for (int d = 0; d < 3; ++d) {
-                            int s = 0;
-                            if (q[d] < 0) { q[d] += nc[d]; s = -1; }
-                            if (q[d] >= nc[d]) { q[d] -= nc[d]; s = 1; }
-                            code |= (s + 1) << (2 * d);
-                        }
-                        const int64_t c2 = q[0] + nc[0] * (q[1] + nc[1] * q[2]);
-                        nbr_cell[k - t0][e] = (int32_t)c2;
-                        nbr_shift[k - t0][e] = code;
-                        if (count(c2) > 0) need.push_back(c2);
-                    }
+        for (int64_t t = t0; t < t1; ++t) {
+            if (local[t] < 0) { local[t] = 0; need.push_back(t); }
+            for (int64_t e = G.nb_start[t]; e < G.nb_start[t + 1]; ++e) {
+                const int64_t c = G.nb_cell[e];
+                if (local[c] < 0) { local[c] = 0; need.push_back(c); }
+            }
         }
         std::sort(need.begin(), need.end());
-        need.erase(std::unique(need.begin(), need.end()), need.end());
         bb.cell0 = (int64_t)B->cells.size();
         int64_t slot = 0;
         for (int64_t c : need) {
             local[c] = (int32_t)(B->cells.size() - bb.cell0);
             BCellDev cd;
-            cd.p0 = (int32_t)T->cell_start[c];
-            cd.n = (int32_t)count(c);
+            cd.p0 = (int32_t)G.p0[c];
+            cd.n = (int32_t)G.cnt[c];
             cd.slot = (int32_t)slot;
             cd.pad = 0;
             B->cells.push_back(cd);
-            slot += count(c);
+            slot += G.cnt[c];
         }
         if (slot > INT32_MAX) return fail(SPH_EUNSUPPORTED, "batch bundle exceeds 2^31-1 slots");
         bb.ncells = (int64_t)need.size();
         bb.slots = slot;
-        // targets of the bundle with their neighbour tables (local indices)
         bb.target0 = (int64_t)B->targets.size();
-        for (size_t k = t0; k < t1; ++k) {
+        for (int64_t t = t0; t < t1; ++t) {
             BTargetDev td;
-            td.cell = local[targets[k]];
-            for (int e = 0; e < 27; ++e) {
-                const int32_t c2 = nbr_cell[k - t0][e];
-                td.nbr[e] = count(c2) > 0 ? local[c2] : -1;
-                td.shift[e] = (uint8_t)nbr_shift[k - t0][e];
-            }
+            td.cell = local[t];
+            td.nb0 = (int32_t)B->nbrs.size();
+            td.nnb = (int32_t)(G.nb_start[t + 1] - G.nb_start[t]);
+            td.pad = 0;
+            if ((int64_t)B->nbrs.size() + td.nnb > INT32_MAX)
+                return fail(SPH_EUNSUPPORTED, "batch plan exceeds 2^31-1 neighbour entries");
+            for (int64_t e = G.nb_start[t]; e < G.nb_start[t + 1]; ++e)
+                B->nbrs.push_back(BNbrDev{local[G.nb_cell[e]], (int32_t)G.nb_code[e]});
             B->targets.push_back(td);
         }
-        bb.ntargets = (int64_t)(t1 - t0);
+        bb.ntargets = t1 - t0;
         // work items: larger cost classes (log2 of the estimated candidate
         // count) first, cell order inside a class (keeps neighbour cells of
         // concurrently processed items close in L2)
         std::vector<std::pair<int64_t, BItemDev>> items;
-        for (size_t k = t0; k < t1; ++k) {
-            const int64_t c = targets[k];
+        for (int64_t t = t0; t < t1; ++t) {
             int64_t around = 0;
-            for (int e = 0; e < 27; ++e) around += count(nbr_cell[k - t0][e]);
-            for (int64_t i0 = 0; i0 < count(c); i0 += ichunk) {
-                const int64_t len = std::min<int64_t>(ichunk, count(c) - i0);
+            for (int64_t e = G.nb_start[t]; e < G.nb_start[t + 1]; ++e) around += G.cnt[G.nb_cell[e]];
+            for (int64_t i0 = 0; i0 < G.cnt[t]; i0 += ichunk) {
+                const int64_t len = std::min<int64_t>(ichunk, G.cnt[t] - i0);
                 BItemDev it;
-                it.target = (int32_t)(k - t0);
+                it.target = (int32_t)(t - t0);
                 it.i0 = (int32_t)i0;
                 int64_t cost = len * around, cls = 0;
                 while (cost > 1) { cost >>= 1; ++cls; }
@@ -117,6 +114,8 @@ int build_batch(const sph_tasks_s *T, const sph_batch_params *bp, sph_batch_s *B
         std::stable_sort(items.begin(), items.end(),
                          [](const std::pair<int64_t, BItemDev> &a,
                             const std::pair<int64_t, BItemDev> &b2) { return a.first > b2.first; });
+        if ((int64_t)items.size() > INT32_MAX)
+            return fail(SPH_EUNSUPPORTED, "batch bundle exceeds 2^31-1 work items");
         bb.item0 = (int64_t)B->items.size();
         for (auto &it : items) B->items.push_back(it.second);
         bb.nitems = (int64_t)items.size();
@@ -132,6 +131,326 @@ int build_batch(const sph_tasks_s *T, const sph_batch_params *bp, sph_batch_s *B
             tslots += B->cells[bb.cell0 + B->targets[bb.target0 + k].cell].n;
         B->max_targets = std::max(B->max_targets, tslots);
     }
+    B->plan_cells = ncells;
+    B->plan_max_cell = 0;
+    for (int64_t c = 0; c < ncells; ++c) B->plan_max_cell = std::max(B->plan_max_cell, G.cnt[c]);
+    B->plan_nbrs = (int64_t)G.nb_cell.size();
+    return SPH_OK;
+}
+
+int check_batch_params(const sph_batch_params *bp) {
+    const int threads = bp->threads;
+    if (threads != 64 && threads != 128 && threads != 256)
+        return fail(SPH_EINVAL, "batch_build: threads must be 64, 128 or 256");
+    return SPH_OK;
+}
+
+}  // namespace
+
+int build_batch(const sph_tasks_s *T, const sph_batch_params *bp, sph_batch_s *B) {
+    if (!T || !bp) return fail(SPH_EINVAL, "batch_build: bad arguments");
+    if (int rc = check_batch_params(bp)) return rc;
+    const int32_t *nc = T->ncell;
+    const int64_t ngrid = (int64_t)nc[0] * nc[1] * nc[2];
+    auto count = [&](int64_t c) { return T->cell_start[c + 1] - T->cell_start[c]; };
+    B->threads = bp->threads;
+    B->n = T->n;
+    B->kind = 0;
+    for (int d = 0; d < 3; ++d) B->box[d] = T->box[d];
+
+    // cells with particles, in grid index order
+    GlobalPlan G;
+    std::vector<int32_t> id((size_t)ngrid, -1);
+    for (int64_t c = 0; c < ngrid; ++c)
+        if (count(c) > 0) {
+            id[c] = (int32_t)G.cnt.size();
+            G.p0.push_back(T->cell_start[c]);
+            G.cnt.push_back(count(c));
+        }
+    // 27 periodic neighbours in (dz, dy, dx) order, empty cells dropped
+    G.nb_start.push_back(0);
+    for (int64_t c = 0; c < ngrid; ++c) {
+        if (id[c] < 0) continue;
+        const int64_t ix = c % nc[0], iy = (c / nc[0]) % nc[1], iz = c / ((int64_t)nc[0] * nc[1]);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int64_t q[3] = {ix + dx, iy + dy, iz + dz};
+                    int code = 0;
+                    for (int d = 0; d < 3; ++d) {
+                        int s = 0;
+                        if (q[d] < 0) { q[d] += nc[d]; s = -1; }
+                        if (q[d] >= nc[d]) { q[d] -= nc[d]; s = 1; }
+                        code |= (s + 1) << (2 * d);
+                    }
+                    const int64_t c2 = q[0] + nc[0] * (q[1] + nc[1] * q[2]);
+                    if (id[c2] < 0) continue;
+                    G.nb_cell.push_back(id[c2]);
+                    G.nb_code.push_back((uint8_t)code);
+                }
+        G.nb_start.push_back((int64_t)G.nb_cell.size());
+    }
+    return assemble(G, bp, B);
+}
+
+// ---------------------------------------------------------------- tree plan
+namespace {
+
+constexpr int kMortonBits = 21;
+
+inline uint64_t spread3(uint64_t v) {  // 21 bits -> every third bit
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+struct Node {
+    int64_t b, e;          // particle range (Morton order)
+    int32_t level;         // 0 = root (the whole box)
+    int32_t child0, nchild;
+    double lo[3], hi[3];   // bounding box of the particles' positions
+    float hmax;            // largest support H of the particles
+};
+
+}  // namespace
+
+namespace {
+
+int tree_plan(int64_t n, const double *x, const float *h, const sph_tree_params *tp,
+              int64_t *perm_out, GlobalPlan &G) {
+    if (n < 0 || (n > 0 && (!x || !h)) || !tp || !perm_out)
+        return fail(SPH_EINVAL, "batch_build_tree: bad arguments");
+    if (n > INT32_MAX) return fail(SPH_EUNSUPPORTED, "batch_build_tree: more than 2^31-1 particles");
+    if (tp->reserved != 0) return fail(SPH_EINVAL, "batch_build_tree: reserved must be 0");
+    if (tp->leaf_max < 8 || tp->leaf_max > 2048)
+        return fail(SPH_EINVAL, "batch_build_tree: leaf_max must be in [8, 2048]");
+    if (!(tp->kernel_gamma > 0.0)) return fail(SPH_EINVAL, "batch_build_tree: kernel_gamma");
+    for (int d = 0; d < 3; ++d)
+        if (!(tp->box[d] > 0.0)) return fail(SPH_EINVAL, "batch_build_tree: box edge %d", d);
+    const double *L = tp->box;
+    const double lmax = std::max(L[0], std::max(L[1], L[2]));
+    const double lmin = std::min(L[0], std::min(L[1], L[2]));
+    const double delta = (double)(float)(4e-6 * lmax);  // the kernels' prefilter margin
+    const float kg = (float)tp->kernel_gamma;
+
+    // supports (as the kernels compute them) and the one-image condition
+    int bad = -1;
+    float Hmax = 0.f;
+#pragma omp parallel for reduction(max : Hmax) reduction(max : bad)
+    for (int64_t i = 0; i < n; ++i) {
+        const float hi = h[i];
+        if (!(hi > 0.f) || !std::isfinite(hi)) bad = 1;
+        else Hmax = std::max(Hmax, kg * hi);
+    }
+    if (bad > 0) return fail(SPH_EINVAL, "batch_build_tree: h must be positive and finite");
+    if (!((double)Hmax + delta < 0.5 * lmin))
+        return fail(SPH_EUNSUPPORTED,
+                    "batch_build_tree: a support (%g) reaches half the box; more than one "
+                    "periodic image per pair", (double)Hmax);
+
+    // Morton keys of the clamped positions, sorted with the index as tie-break
+    std::vector<std::pair<uint64_t, int64_t>> key((size_t)n);
+    const double scale = (double)(1 << kMortonBits);
+#pragma omp parallel for
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t k = 0;
+        for (int d = 0; d < 3; ++d) {
+            int64_t q = (int64_t)std::floor(x[3 * i + d] / L[d] * scale);
+            q = q < 0 ? 0 : (q >= (1 << kMortonBits) ? (1 << kMortonBits) - 1 : q);
+            k |= spread3((uint64_t)q) << d;
+        }
+        key[(size_t)i] = {k, i};
+    }
+    __gnu_parallel::sort(key.begin(), key.end());
+    std::vector<uint64_t> ks((size_t)n);
+    std::vector<double> xs((size_t)n * 3);
+    std::vector<float> Hs((size_t)n);
+#pragma omp parallel for
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t i = key[(size_t)k].second;
+        perm_out[k] = i;
+        ks[(size_t)k] = key[(size_t)k].first;
+        for (int d = 0; d < 3; ++d) xs[(size_t)(3 * k + d)] = x[3 * i + d];
+        Hs[(size_t)k] = kg * h[i];
+    }
+    std::vector<std::pair<uint64_t, int64_t>>().swap(key);
+
+    // octree, breadth first (children of a node are contiguous)
+    std::vector<Node> nodes;
+    nodes.reserve((size_t)(2 * n / tp->leaf_max + 64));
+    nodes.push_back(Node{0, n, 0, -1, 0, {0, 0, 0}, {0, 0, 0}, 0.f});
+    for (size_t q = 0; q < nodes.size(); ++q) {
+        Node nd = nodes[q];
+        if (nd.e - nd.b <= tp->leaf_max || nd.level == kMortonBits) continue;
+        const int shift = 3 * (kMortonBits - 1 - nd.level);
+        const int32_t first = (int32_t)nodes.size();
+        int32_t nch = 0;
+        int64_t b = nd.b;
+        const uint64_t pre = ks[(size_t)nd.b] >> (shift + 3);
+        for (uint64_t c = 0; c < 8 && b < nd.e; ++c) {
+            const uint64_t lim = ((pre << 3) | c) + 1;  // first prefix past child c
+            const int64_t e = std::lower_bound(ks.begin() + b, ks.begin() + nd.e, lim << shift,
+                                               [](uint64_t a, uint64_t v) { return a < v; }) -
+                              ks.begin();
+            if (e > b) {
+                nodes.push_back(Node{b, e, nd.level + 1, -1, 0, {0, 0, 0}, {0, 0, 0}, 0.f});
+                ++nch;
+            }
+            b = e;
+        }
+        nodes[q].child0 = first;
+        nodes[q].nchild = nch;
+    }
+    // leaves in Morton order; their boxes and supports
+    std::vector<int32_t> leaves;
+    for (size_t q = 0; q < nodes.size(); ++q)
+        if (nodes[q].nchild == 0 && nodes[q].e > nodes[q].b) leaves.push_back((int32_t)q);
+    std::sort(leaves.begin(), leaves.end(),
+              [&](int32_t a, int32_t b2) { return nodes[a].b < nodes[b2].b; });
+    const int64_t nleaf = (int64_t)leaves.size();
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t l = 0; l < nleaf; ++l) {
+        Node &nd = nodes[leaves[l]];
+        for (int d = 0; d < 3; ++d) { nd.lo[d] = INFINITY; nd.hi[d] = -INFINITY; }
+        float hm = 0.f;
+        for (int64_t k = nd.b; k < nd.e; ++k) {
+            for (int d = 0; d < 3; ++d) {
+                nd.lo[d] = std::min(nd.lo[d], xs[(size_t)(3 * k + d)]);
+                nd.hi[d] = std::max(nd.hi[d], xs[(size_t)(3 * k + d)]);
+            }
+            hm = std::max(hm, Hs[(size_t)k]);
+        }
+        nd.hmax = hm;
+    }
+    for (size_t q = nodes.size(); q-- > 0;) {  // children come after parents
+        Node &nd = nodes[q];
+        if (nd.nchild == 0) continue;
+        for (int d = 0; d < 3; ++d) { nd.lo[d] = INFINITY; nd.hi[d] = -INFINITY; }
+        nd.hmax = 0.f;
+        for (int32_t c = nd.child0; c < nd.child0 + nd.nchild; ++c) {
+            for (int d = 0; d < 3; ++d) {
+                nd.lo[d] = std::min(nd.lo[d], nodes[c].lo[d]);
+                nd.hi[d] = std::max(nd.hi[d], nodes[c].hi[d]);
+            }
+            nd.hmax = std::max(nd.hmax, nodes[c].hmax);
+        }
+    }
+    std::vector<int32_t> leaf_id(nodes.size(), -1);
+    for (int64_t l = 0; l < nleaf; ++l) leaf_id[leaves[l]] = (int32_t)l;
+
+    // neighbour entries: all (leaf, shift) within max(H_T, H_J) + delta of
+    // the target's box, by a walk pruned with each subtree's box and H_max
+    G.p0.resize((size_t)nleaf);
+    G.cnt.resize((size_t)nleaf);
+    for (int64_t l = 0; l < nleaf; ++l) {
+        G.p0[(size_t)l] = nodes[leaves[l]].b;
+        G.cnt[(size_t)l] = nodes[leaves[l]].e - nodes[leaves[l]].b;
+    }
+    const int nth = omp_get_max_threads();
+    std::vector<std::vector<int32_t>> tcell((size_t)nth);
+    std::vector<std::vector<uint8_t>> tcode((size_t)nth);
+    std::vector<int64_t> nnb((size_t)nleaf, 0);
+    std::vector<int> owner((size_t)nleaf, 0);
+    std::vector<int64_t> off((size_t)nleaf, 0);
+#pragma omp parallel
+    {
+        const int tid = omp_get_thread_num();
+        std::vector<int32_t> stack;
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t l = 0; l < nleaf; ++l) {
+            const Node &T = nodes[leaves[l]];
+            owner[(size_t)l] = tid;
+            off[(size_t)l] = (int64_t)tcell[(size_t)tid].size();
+            stack.clear();
+            stack.push_back(0);
+            while (!stack.empty()) {
+                const int32_t q = stack.back();
+                stack.pop_back();
+                const Node &N = nodes[q];
+                const double R = (double)std::max(T.hmax, N.hmax) + delta;
+                // per dimension, the interval distance under each shift
+                double dd[3][3];
+                double dmin2 = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                    double m = INFINITY;
+                    for (int s = -1; s <= 1; ++s) {
+                        const double a0 = N.lo[d] + s * L[d], a1 = N.hi[d] + s * L[d];
+                        const double g = std::max(0.0, std::max(a0 - T.hi[d], T.lo[d] - a1));
+                        dd[d][s + 1] = g;
+                        m = std::min(m, g);
+                    }
+                    dmin2 += m * m;
+                }
+                if (!(dmin2 < R * R)) continue;
+                if (N.nchild > 0) {
+                    for (int32_t c = N.child0 + N.nchild - 1; c >= N.child0; --c) stack.push_back(c);
+                    continue;
+                }
+                for (int s2 = 0; s2 < 3; ++s2)
+                    for (int s1 = 0; s1 < 3; ++s1)
+                        for (int s0 = 0; s0 < 3; ++s0) {
+                            const double g2 = dd[0][s0] * dd[0][s0] + dd[1][s1] * dd[1][s1] +
+                                              dd[2][s2] * dd[2][s2];
+                            if (!(g2 < R * R)) continue;
+                            tcell[(size_t)tid].push_back(leaf_id[q]);
+                            tcode[(size_t)tid].push_back((uint8_t)(s0 | (s1 << 2) | (s2 << 4)));
+                        }
+            }
+            nnb[(size_t)l] = (int64_t)tcell[(size_t)tid].size() - off[(size_t)l];
+        }
+    }
+    G.nb_start.assign((size_t)nleaf + 1, 0);
+    for (int64_t l = 0; l < nleaf; ++l) G.nb_start[(size_t)l + 1] = G.nb_start[(size_t)l] + nnb[(size_t)l];
+    G.nb_cell.resize((size_t)G.nb_start[(size_t)nleaf]);
+    G.nb_code.resize((size_t)G.nb_start[(size_t)nleaf]);
+#pragma omp parallel for schedule(static, 1024)
+    for (int64_t l = 0; l < nleaf; ++l) {
+        const auto &vc = tcell[(size_t)owner[(size_t)l]];
+        const auto &vk = tcode[(size_t)owner[(size_t)l]];
+        std::copy(vc.begin() + off[(size_t)l], vc.begin() + off[(size_t)l] + nnb[(size_t)l],
+                  G.nb_cell.begin() + G.nb_start[(size_t)l]);
+        std::copy(vk.begin() + off[(size_t)l], vk.begin() + off[(size_t)l] + nnb[(size_t)l],
+                  G.nb_code.begin() + G.nb_start[(size_t)l]);
+    }
+    return SPH_OK;
+}
+
+}  // namespace
+
+int build_batch_tree(int64_t n, const double *x, const float *h, const sph_tree_params *tp,
+                     const sph_batch_params *bp, int64_t *perm_out, sph_batch_s *B) {
+    if (!bp) return fail(SPH_EINVAL, "batch_build_tree: bad arguments");
+    if (int rc = check_batch_params(bp)) return rc;
+    GlobalPlan G;
+    if (int rc = tree_plan(n, x, h, tp, perm_out, G)) return rc;
+    B->threads = bp->threads;
+    B->n = n;
+    B->kind = 1;
+    for (int d = 0; d < 3; ++d) B->box[d] = tp->box[d];
+    return assemble(G, bp, B);
+}
+
+int tree_plan_host(int64_t n, const double *x, const float *h, const sph_tree_params *tp,
+                   int64_t *perm_out, int64_t *leaf_start, int64_t *nleaf_out,
+                   int64_t *nb_start, int32_t *nb, int64_t nb_cap, int64_t *nnb_out) {
+    if (!leaf_start || !nleaf_out || !nb_start || !nnb_out)
+        return fail(SPH_EINVAL, "tree_plan: NULL output");
+    GlobalPlan G;
+    if (int rc = tree_plan(n, x, h, tp, perm_out, G)) return rc;
+    const int64_t nleaf = (int64_t)G.cnt.size(), nnb = (int64_t)G.nb_cell.size();
+    *nleaf_out = nleaf;
+    *nnb_out = nnb;
+    if (nnb > nb_cap || (nnb > 0 && !nb))
+        return fail(SPH_EINVAL, "tree_plan: %lld neighbour entries, capacity %lld",
+                    (long long)nnb, (long long)nb_cap);
+    leaf_start[0] = 0;
+    for (int64_t l = 0; l < nleaf; ++l) leaf_start[l + 1] = G.p0[(size_t)l] + G.cnt[(size_t)l];
+    for (int64_t l = 0; l <= nleaf; ++l) nb_start[l] = G.nb_start[(size_t)l];
+    for (int64_t e = 0; e < nnb; ++e) nb[e] = (G.nb_cell[(size_t)e] << 6) | G.nb_code[(size_t)e];
     return SPH_OK;
 }
 

@@ -8,7 +8,7 @@
 //           are spatially compact.
 // k_binteract persistent CTAs pull (target cell, particle chunk) items from
 //           an atomic queue (items are sorted longest first).  For each of
-//           the 27 neighbour cells, tiles of j records are staged in shared
+//           the target's neighbour entries, tiles of j records are staged in shared
 //           memory (the periodic shift added as an exact two-float sum); each
 //           warp keeps only the j inside its particles' bounding box widened
 //           by the support, tests those per lane, and runs the pair body on
@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(128) k_bpack(BPackArgs a) {
 struct BInteractArgs {
     const BCellDev *cells;
     const BTargetDev *targets;
+    const BNbrDev *nbrs;
     const BItemDev *items;
     unsigned int *counter;
     int nitems;
@@ -320,11 +321,11 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? SPH_BMINB_FORCE : 1024
         const bool warp_live = __any_sync(0xffffffffu, live);
         const BTargetDev &Tg = a.targets[W.target];
 #pragma unroll 1
-        for (int e = 0; e < 27 && warp_live; ++e) {
-            const int nb = Tg.nbr[e];
-            if (nb < 0) continue;
+        for (int e = Tg.nb0; e < Tg.nb0 + Tg.nnb && warp_live; ++e) {
+            const BNbrDev E = a.nbrs[e];
+            const int nb = E.cell;
             const BCellDev Cn = a.cells[nb];
-            const int code = Tg.shift[e];
+            const int code = E.code;
             float sh[3], sl[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) {

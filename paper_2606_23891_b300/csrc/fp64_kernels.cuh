@@ -67,12 +67,15 @@ __device__ __forceinline__ double dw64(double q) {
 struct D64Args {
     const BCellDev *cells;
     const BTargetDev *targets;
+    const BNbrDev *nbrs;
     const char *in;
     char *out;
     long long S;
     double gamma, beta, box[3];
     int active_bin;
 };
+
+constexpr int kSelfCode = 1 | (1 << 2) | (1 << 4);  // no shift in any dimension
 
 // One CTA per target cell, one thread per target particle.
 template <int LOOP>
@@ -98,11 +101,9 @@ __global__ void __launch_bounds__(128) k_interact64(D64Args a) {
         const double Pi_ = (a.gamma - 1.0) * rhoi * ui;
         const double ci = sqrt(gg * ui);
         const double Ai = qi.z * Pi_ / (rhoi * rhoi);
-        for (int e = 0; e < 27 && active; ++e) {
-            const int nb = Tg.nbr[e];
-            if (nb < 0) continue;
-            const BCellDev Cn = a.cells[nb];
-            const int code = Tg.shift[e];
+        for (int e = Tg.nb0; e < Tg.nb0 + Tg.nnb && active; ++e) {
+            const BCellDev Cn = a.cells[a.nbrs[e].cell];
+            const int code = a.nbrs[e].code;
             double s[3];
             for (int d = 0; d < 3; ++d) {
                 const int c = ((code >> (2 * d)) & 3) - 1;
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(128) k_interact64(D64Args a) {
             }
             for (int q = 0; q < Cn.n; ++q) {
                 const long long sj = (long long)Cn.slot + q;
-                if (sj == si) continue;
+                if (sj == si && code == kSelfCode) continue;
                 const double4_32a xj = R0[sj];
                 const double dx = xi.x - (xj.x + s[0]), dy = xi.y - (xj.y + s[1]),
                              dz = xi.z - (xj.z + s[2]);
@@ -181,6 +182,42 @@ __global__ void __launch_bounds__(128) k_interact64(D64Args a) {
             out[6 * si + 5] = active ? vsig : 0.0;
         }
     }
+}
+
+// Pair interactions of a loop, decided in FP64 as the loops define them
+// (density, gradient: r < H_i; force: r < max(H_i, H_j) for active i).
+template <int LOOP>
+__global__ void __launch_bounds__(128) k_count64(D64Args a, unsigned long long *count) {
+    const BTargetDev &Tg = a.targets[blockIdx.x];
+    const BCellDev C = a.cells[Tg.cell];
+    const double4_32a *R0 = reinterpret_cast<const double4_32a *>(a.in + D64Layout::rec(0, a.S));
+    const double4_32a *R3 = reinterpret_cast<const double4_32a *>(a.in + D64Layout::rec(3, a.S));
+    unsigned long long mine = 0;
+    for (int k = threadIdx.x; k < C.n; k += blockDim.x) {
+        const long long si = (long long)C.slot + k;
+        const double4_32a xi = R0[si];
+        if (LOOP == SPH_FORCE && (int)R3[si].z > a.active_bin) continue;
+        for (int e = Tg.nb0; e < Tg.nb0 + Tg.nnb; ++e) {
+            const BCellDev Cn = a.cells[a.nbrs[e].cell];
+            const int code = a.nbrs[e].code;
+            double s[3];
+            for (int d = 0; d < 3; ++d) {
+                const int c = ((code >> (2 * d)) & 3) - 1;
+                s[d] = c == 0 ? 0.0 : (c > 0 ? a.box[d] : -a.box[d]);
+            }
+            for (int q = 0; q < Cn.n; ++q) {
+                const long long sj = (long long)Cn.slot + q;
+                if (sj == si && code == kSelfCode) continue;
+                const double4_32a xj = R0[sj];
+                const double dx = xi.x - (xj.x + s[0]), dy = xi.y - (xj.y + s[1]),
+                             dz = xi.z - (xj.z + s[2]);
+                const double Hm = LOOP == SPH_FORCE ? fmax(xi.w, xj.w) : xi.w;
+                mine += (dx * dx + dy * dy + dz * dz < Hm * Hm) ? 1 : 0;
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(count, mine);
 }
 
 struct D64UnpackArgs {

@@ -114,14 +114,16 @@ struct sph_tasks_s {
 struct BCellDev {
     int32_t p0, n, slot, pad;
 };
-// A target cell: its local cell index and its 27 neighbours (local index or
-// -1 for an empty cell) in (dz, dy, dx) order, each with the periodic shift
-// of the neighbour's particles (code + 1 per dimension in 2-bit fields).
+// A target cell: its local cell index and its neighbour entries
+// [nb0, nb0 + nnb) of the plan's neighbour list.
 struct BTargetDev {
-    int32_t cell;
-    int32_t nbr[27];
-    uint8_t shift[27];
-    uint8_t pad[5];
+    int32_t cell, nb0, nnb, pad;
+};
+// A neighbour entry: a local cell whose particles may interact with the
+// target's, and the periodic shift of those particles (code + 1 per
+// dimension in 2-bit fields).  A cell may appear with several shifts.
+struct BNbrDev {
+    int32_t cell, code;
 };
 // A work item (one warp): particles [i0, i0 + 32) of target `target`.
 struct BItemDev {
@@ -141,15 +143,24 @@ struct sph_batch_s {
     std::vector<BCellDev> cells;
     std::vector<BTargetDev> targets;
     std::vector<BItemDev> items;
+    std::vector<BNbrDev> nbrs;
     int64_t max_slots = 0, max_targets = 0;
+    int kind = 0;                 // 0: uniform cell grid, 1: adaptive octree leaves
+    int64_t plan_cells = 0, plan_max_cell = 0, plan_nbrs = 0;
     BCellDev *d_cells = nullptr;
     BTargetDev *d_targets = nullptr;
+    BNbrDev *d_nbrs = nullptr;
     BItemDev *d_items = nullptr;
     unsigned int *d_counter = nullptr;  // work-queue head, one per bundle
 };
 
 namespace sph {
 int build_batch(const sph_tasks_s *T, const sph_batch_params *bp, sph_batch_s *B);
+int build_batch_tree(int64_t n, const double *x, const float *h, const sph_tree_params *tp,
+                     const sph_batch_params *bp, int64_t *perm_out, sph_batch_s *B);
+int tree_plan_host(int64_t n, const double *x, const float *h, const sph_tree_params *tp,
+                   int64_t *perm_out, int64_t *leaf_start, int64_t *nleaf_out,
+                   int64_t *nb_start, int32_t *nb, int64_t nb_cap, int64_t *nnb_out);
 
 int build_tasks(int64_t n, const double *x, const float *h,
                 const sph_grid_params *gp, int64_t *perm_out, sph_tasks_s *T);

@@ -15,6 +15,10 @@ available):
   Sec. 3.4) on a jittered 256^3 lattice.  A jitter of +-0.52 spacing on cells
   of four lattice spacings reproduces the paper's 55/73/64/64 min/max/mean/
   median particles per cell.
+* ``lognormal``: a cosmology-clustering shaped set (the "Eagle25" trace of
+  Sec. 3.4 stands behind it): particles drawn from a lognormal density field
+  with sigma(ln rho) = 2, so that densities span about nine decades and
+  smoothing lengths about three.
 
 Smoothing lengths follow the usual SPH relation h = eta (m / rho)^(1/3) with
 rho the *prescribed* density of the recipe (not a measured one).
@@ -135,6 +139,102 @@ def gresho(n_side: int = 256, jitter: float = 0.52, seed: int = 3,
     f["u"][:] = (gresho_pressure(r) / ((GAMMA - 1.0) * 1.0)).astype(np.float32)
     f["alpha_visc"][:] = alpha_visc
     f["alpha_diff"][:] = alpha_diff
+    return f
+
+
+def _field_k(g: int):
+    """Integer wavenumbers of a g^3 real FFT grid (rfftn layout) and |k|."""
+    k1 = np.fft.fftfreq(g, 1.0 / g)
+    kz = np.fft.rfftfreq(g, 1.0 / g)
+    kx, ky, kz = np.meshgrid(k1, k1, kz, indexing="ij")
+    return kx, ky, kz, np.sqrt(kx * kx + ky * ky + kz * kz)
+
+
+def lognormal(n_side: int = 376, sigma_ln: float = 2.0, grid: int = 0,
+              slope: float = -2.0, smooth: float = 2.5, seed: int = 11,
+              v_amp: float = 0.3, box: float = 1.0, h_iters: int = 4) -> dict:
+    """Clustered set of n_side^3 equal-mass particles in the unit periodic box.
+
+    A Gaussian random field with power spectrum k^slope exp(-(2 pi k s / g)^2 / 2)
+    (s = ``smooth`` field cells) on a grid^3 mesh (default: the power of two
+    nearest n_side / 3, about 27 particles per mesh cell) is scaled to unit variance;
+    the density is rho = exp(sigma_ln delta - sigma_ln^2 / 2) normalised to a
+    mean of 1.  Particle counts per mesh cell are multinomial in rho, and
+    positions uniform inside each cell.  Velocities follow the field's
+    gradient flow (the linear-theory displacement direction, scaled to an rms
+    of ``v_amp`` per component); u rises with density as rho^(2/3);
+    alpha_visc, alpha_diff are drawn uniformly.  Smoothing lengths use
+    h = eta (m / rho_bar)^(1/3) with rho_bar the particles' number density
+    counted on the mesh and averaged over a sphere of radius ~ the support
+    (damped fixed-point iterations on mesh averages at radii 2^j cells), so
+    that particles in thin regions see the density around them rather than
+    their own cell's and the neighbour counts stay near the target."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = n_side ** 3
+    g = grid or 2 ** max(2, int(round(math.log2(n_side / 3.0))))
+    kx, ky, kz, kk = _field_k(g)
+    with np.errstate(divide="ignore"):
+        amp = np.where(kk > 0, kk ** (0.5 * slope), 0.0)
+    amp *= np.exp(-0.25 * (2.0 * np.pi * kk * smooth / g) ** 2)
+    dk = np.fft.rfftn(rng.standard_normal((g, g, g))) * amp
+    delta = np.fft.irfftn(dk, s=(g, g, g), axes=(0, 1, 2))
+    delta /= delta.std()
+    rho = np.exp(sigma_ln * delta - 0.5 * sigma_ln ** 2)
+    rho /= rho.mean()
+    counts = rng.multinomial(n, (rho / rho.sum()).ravel())
+    cell = np.repeat(np.arange(g ** 3, dtype=np.int64), counts)
+    del counts
+    iz, rem = np.divmod(cell, g * g)
+    iy, ix = np.divmod(rem, g)
+    del rem
+    x = np.empty((n, 3), np.float64)
+    for d, idx in enumerate((ix, iy, iz)):
+        x[:, d] = (idx + rng.random(n)) * (box / g)
+    del ix, iy, iz
+    m = box ** 3 / n
+    f = empty_fields(n)
+    f["x"][:] = x
+    f["mass"][:] = m
+    f["id"][:] = np.arange(n, dtype=np.int64)
+    # mesh averages of the particles' number density over spheres of radius
+    # 2^j cells (top-hat filter), interpolated in log radius at the support
+    nd = np.bincount(cell, minlength=g ** 3).reshape(g, g, g) * (g ** 3 / n)
+    rk = np.fft.rfftn(nd)
+    levels = [nd.ravel()]
+    radii = [0.5]                       # a particle's own cell
+    for j in range(0, int(math.log2(g // 4)) + 1):
+        r = 2.0 ** j
+        xk = 2.0 * np.pi * kk * r / g
+        with np.errstate(invalid="ignore", divide="ignore"):
+            w = np.where(xk > 1e-8, 3.0 * (np.sin(xk) - xk * np.cos(xk)) / xk ** 3, 1.0)
+        levels.append(np.maximum(np.fft.irfftn(rk * w, s=(g, g, g), axes=(0, 1, 2)), 1e-6).ravel())
+        radii.append(r)
+    lr = np.log2(np.array(radii) * (box / g))
+    kernel_gamma = 1.825742
+    H = kernel_gamma * ETA * (m / np.maximum(levels[0][cell], 1e-6)) ** (1.0 / 3.0)
+    for _ in range(h_iters):
+        t = np.clip(np.log2(H), lr[0], lr[-1])
+        j = np.minimum(np.searchsorted(lr, t, side="right") - 1, len(lr) - 2)
+        wgt = (t - lr[j]) / (lr[j + 1] - lr[j])
+        lo = np.empty(n)
+        hi = np.empty(n)
+        for L in range(len(lr) - 1):
+            sel = j == L
+            lo[sel] = levels[L][cell[sel]]
+            hi[sel] = levels[L + 1][cell[sel]]
+        rho_bar = np.exp((1.0 - wgt) * np.log(lo) + wgt * np.log(hi))
+        H = np.sqrt(H * kernel_gamma * ETA * (m / rho_bar) ** (1.0 / 3.0))   # damped
+    f["h"][:] = (H / kernel_gamma).astype(np.float32)
+    # velocities: gradient flow of the field, sampled at the particle's cell
+    with np.errstate(invalid="ignore", divide="ignore"):
+        phi = np.where(kk > 0, dk / (kk * kk), 0.0)
+    for d, kd in enumerate((kx, ky, kz)):
+        vd = np.fft.irfftn(1j * kd * phi, s=(g, g, g), axes=(0, 1, 2)).ravel()
+        vd *= v_amp / max(vd.std(), 1e-30)
+        f["v"][:, d] = vd[cell].astype(np.float32)
+    f["u"][:] = (rho.ravel()[cell] ** (2.0 / 3.0)).astype(np.float32)
+    f["alpha_visc"][:] = rng.uniform(0.1, 1.0, n).astype(np.float32)
+    f["alpha_diff"][:] = rng.uniform(0.0, 0.2, n).astype(np.float32)
     return f
 
 

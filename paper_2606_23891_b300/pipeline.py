@@ -45,9 +45,17 @@ class Offload:
     def __init__(self, fields: dict, layout="aos", seed: int = 0,
                  box=(1.0, 1.0, 1.0), bundle_max_slots: int = 0,
                  ncell=(0, 0, 0), params: sph.Params | None = None,
-                 device: str = "cuda", share: "Offload | None" = None):
+                 device: str = "cuda", share: "Offload | None" = None,
+                 plan: str = "grid", leaf_max: int = 64):
         """``share``: reuse another Offload's task list, permutation and
-        buffers (same particles, different store layout)."""
+        buffers (same particles, different store layout).  ``plan="tree"``:
+        no uniform grid or per-task list; the particles are ordered by the
+        octree-leaf plan of the batched pipeline (clustered sets), and only
+        the batched calls are available."""
+        if plan not in ("grid", "tree"):
+            raise ValueError("plan must be 'grid' or 'tree'")
+        self.plan = plan if share is None else share.plan
+        self.leaf_max = leaf_max if share is None else share.leaf_max
         self.device = torch.device(device)
         self.layout = sph.LAYOUTS[layout] if isinstance(layout, str) else int(layout)
         self.seed = seed
@@ -56,7 +64,20 @@ class Offload:
         self.n = n = x.shape[0]
         self.box = tuple(float(b) for b in box)
         self.owner = share is None
-        if share is None:
+        if share is None and self.plan == "tree":
+            self._x = x
+            self._h = np.ascontiguousarray(fields["h"], np.float32)
+            self.perm = np.empty(n, np.int64)
+            self.tasks = None
+            self.bplan = sph.sph_batch_build_tree(
+                n, x.ctypes.data, self._h.ctypes.data, self.box, self.params.kernel_gamma,
+                leaf_max, 0, 128, self.perm.ctypes.data)
+            self._batch_buffers()
+            self.info = dict(sph.sph_batch_plan_info(self.bplan))
+            self.info.update(slots=None, nbundles=None)
+            self.d_perm = torch.from_numpy(self.perm).to(self.device)
+            self.buf_in = self.buf_out = None
+        elif share is None:
             h = np.ascontiguousarray(fields["h"], np.float32)
             gp = sph.grid_params(box, self.params.kernel_gamma, ncell, bundle_max_slots)
             self.perm = np.empty(n, np.int64)
@@ -72,6 +93,9 @@ class Offload:
         else:
             self.perm, self.tasks, self.info = share.perm, share.tasks, share.info
             self.d_perm, self.buf_in, self.buf_out = share.d_perm, share.buf_in, share.buf_out
+            if self.plan == "tree":
+                self._x, self._h = share._x, share._h
+                self.use_batch_of(share)
         self.nbytes = sph.sph_store_bytes(n, self.layout, seed)
         self.mem = torch.empty(max(self.nbytes, 256), dtype=torch.uint8, device=self.device)
         self.store = sph.sph_store_create(n, self.layout, seed, self.mem.data_ptr(),
@@ -142,6 +166,8 @@ class Offload:
 
     def count_pairs(self, loop: int) -> int:
         """Pair interactions of `loop` (packs each bundle into buf_in)."""
+        if self.plan == "tree":
+            return self.count_pairs_fp64(loop)
         cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
         for b in range(self.nbundles()):
             self.pack(loop, b)
@@ -178,8 +204,22 @@ class Offload:
     def batch(self, max_target_cells: int = 0, threads: int = 128) -> None:
         """Build the batched plan for this particle set and its buffers."""
         self.close_batch()
-        self.bplan = sph.sph_batch_build(self.tasks, max_target_cells, threads)
+        if self.plan == "tree":
+            perm = np.empty(self.n, np.int64)
+            self.bplan = sph.sph_batch_build_tree(
+                self.n, self._x.ctypes.data, self._h.ctypes.data, self.box,
+                self.params.kernel_gamma, self.leaf_max, max_target_cells, threads,
+                perm.ctypes.data)
+            if not np.array_equal(perm, self.perm):
+                raise RuntimeError("tree plan order changed for the same particles")
+        else:
+            self.bplan = sph.sph_batch_build(self.tasks, max_target_cells, threads)
+        self.bshared = False
+        self._batch_buffers()
+
+    def _batch_buffers(self) -> None:
         self.binfo = sph.sph_batch_info(self.bplan)
+        self.binfo.update(sph.sph_batch_plan_info(self.bplan))
         nin = max(sph.sph_batch_buffer_bytes(self.bplan, l, 0) for l in range(3))
         nout = max(sph.sph_batch_buffer_bytes(self.bplan, l, 1) for l in range(3))
         self.bbuf_in = torch.empty(max(nin, 256), dtype=torch.uint8, device=self.device)
@@ -199,13 +239,24 @@ class Offload:
         for loop in (sph.SPH_DENSITY, sph.SPH_GRADIENT, sph.SPH_FORCE):
             self.batch_loop(loop)
 
-    def fp64_step(self) -> None:
-        """The batched step with every arithmetic step in FP64."""
+    def count_pairs_fp64(self, loop: int) -> int:
+        """Pair interactions of `loop` over the batched plan, decided in FP64."""
+        self._fp64_buffers()
+        cnt = torch.zeros(1, dtype=torch.int64, device=self.device)
+        sph.sph_batch_count_pairs(self.store, self.bplan, loop, self.f64_in.data_ptr(),
+                                  self.params, cnt.data_ptr(), self.stream)
+        return int(cnt.item())
+
+    def _fp64_buffers(self) -> None:
         if getattr(self, "f64_in", None) is None:
             nin = sph.sph_batch_buffer_bytes_fp64(self.bplan, 0)
             nout = sph.sph_batch_buffer_bytes_fp64(self.bplan, 1)
             self.f64_in = torch.empty(max(nin, 256), dtype=torch.uint8, device=self.device)
             self.f64_out = torch.empty(max(nout, 256), dtype=torch.uint8, device=self.device)
+
+    def fp64_step(self) -> None:
+        """The batched step with every arithmetic step in FP64."""
+        self._fp64_buffers()
         for loop in (sph.SPH_DENSITY, sph.SPH_GRADIENT, sph.SPH_FORCE):
             sph.sph_batch_offload_loop_fp64(self.store, self.bplan, loop, self.f64_in.data_ptr(),
                                             self.f64_out.data_ptr(), self.params, self.stream)

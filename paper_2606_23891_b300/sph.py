@@ -58,6 +58,11 @@ class BatchParams(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class TreeParams(C.Structure):
+    _fields_ = [("box", C.c_double * 3), ("kernel_gamma", C.c_double),
+                ("leaf_max", C.c_int32), ("reserved", C.c_int32)]
+
+
 def params(gamma=5.0 / 3.0, kernel_gamma=1.825742, beta_visc=3.0,
            balsara_eps=1e-4, active_bin=0) -> Params:
     return Params(gamma, kernel_gamma, beta_visc, balsara_eps, active_bin, 0)
@@ -121,6 +126,10 @@ def lib() -> C.CDLL:
         "sph_batch_offload_loop": (i, [p, p, i, p, p, p, p]),
         "sph_batch_destroy": (i, [p]),
         "sph_batch_buffer_bytes_fp64": (sz, [p, i]),
+        "sph_batch_build_tree": (i, [i64, p, p, p, p, p, p]),
+        "sph_batch_plan_info": (i, [p, p]),
+        "sph_tree_plan": (i, [i64, p, p, p, p, p, p, p, p, i64, p]),
+        "sph_batch_count_pairs": (i, [p, p, i, p, p, p, p]),
         "sph_batch_offload_loop_fp64": (i, [p, p, i, p, p, p, p]),
         "sph_store_create_host": (i, [i64, i, u64, p, sz, p]),
         "sph_store_import_host": (i, [p, p, p, i]),
@@ -308,6 +317,58 @@ def sph_batch_build(t, max_target_cells: int = 0, threads: int = 128):
     bp = BatchParams(max_target_cells, threads, 0)
     _ok(lib().sph_batch_build(t, C.byref(bp), C.byref(h)))
     return h
+
+
+def sph_batch_build_tree(n: int, x_ptr: int, h_ptr: int, box=(1.0, 1.0, 1.0),
+                         kernel_gamma=1.825742, leaf_max: int = 64,
+                         max_target_cells: int = 0, threads: int = 128, perm_ptr: int = 0):
+    h = C.c_void_p()
+    tp = TreeParams()
+    tp.box[:] = list(box)
+    tp.kernel_gamma = kernel_gamma
+    tp.leaf_max = leaf_max
+    tp.reserved = 0
+    bp = BatchParams(max_target_cells, threads, 0)
+    _ok(lib().sph_batch_build_tree(n, x_ptr, h_ptr, C.byref(tp), C.byref(bp), perm_ptr,
+                                   C.byref(h)))
+    return h
+
+
+def sph_tree_plan(x, h, box=(1.0, 1.0, 1.0), kernel_gamma=1.825742, leaf_max: int = 64):
+    """Host-only tree plan: (perm, leaf_start, nb_start, nb) as numpy arrays."""
+    import numpy as np
+    x = np.ascontiguousarray(x, np.float64)
+    h = np.ascontiguousarray(h, np.float32)
+    n = x.shape[0]
+    tp = TreeParams()
+    tp.box[:] = list(box)
+    tp.kernel_gamma = kernel_gamma
+    tp.leaf_max = leaf_max
+    tp.reserved = 0
+    perm = np.empty(n, np.int64)
+    ls = np.empty(n + 1, np.int64)
+    nbs = np.empty(n + 1, np.int64)
+    nleaf, nnb = C.c_int64(), C.c_int64()
+    args = (n, x.ctypes.data, h.ctypes.data, C.byref(tp), perm.ctypes.data, ls.ctypes.data,
+            C.byref(nleaf), nbs.ctypes.data)
+    rc = lib().sph_tree_plan(*args, None, 0, C.byref(nnb))
+    if rc != 0 and nnb.value == 0:
+        _ok(rc)
+    nb = np.empty(max(nnb.value, 1), np.int32)
+    _ok(lib().sph_tree_plan(*args, nb.ctypes.data, nb.size, C.byref(nnb)))
+    L = nleaf.value
+    return perm, ls[:L + 1].copy(), nbs[:L + 1].copy(), nb[:nnb.value].copy()
+
+
+def sph_batch_plan_info(b) -> dict:
+    info = (C.c_int64 * 4)()
+    _ok(lib().sph_batch_plan_info(b, info))
+    return dict(zip(("kind", "cells", "max_cell", "nbrs"), list(info)))
+
+
+def sph_batch_count_pairs(s, b, loop: int, dev_in: int, p: Params, dev_count: int,
+                          stream: int = 0):
+    _ok(lib().sph_batch_count_pairs(s, b, loop, dev_in, C.byref(p), dev_count, stream))
 
 
 def sph_batch_info(b) -> dict:

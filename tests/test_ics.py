@@ -41,3 +41,24 @@ def test_generators_are_seeded():
     c = ics.jittered_lattice(8, 0.3, 6)
     assert np.array_equal(a, b) and not np.array_equal(a, c)
     assert a.min() >= 0.0 and a.max() < 1.0
+
+
+def test_lognormal_recipe():
+    """Clustered set: equal masses, positions in the box, a wide spread of
+    smoothing lengths with neighbour counts near the target (scipy KD-tree
+    count), and reproducible draws."""
+    from scipy.spatial import cKDTree
+    f = ics.lognormal(n_side=32, seed=21)
+    n = 32 ** 3
+    assert f["x"].shape == (n, 3)
+    assert np.all((f["x"] >= 0) & (f["x"] < 1))
+    assert np.all(f["mass"] == np.float32(1.0 / n))
+    H = 1.825742 * f["h"].astype(np.float64)
+    assert H.max() / H.min() > 5
+    assert H.max() < 0.5
+    cnt = cKDTree(f["x"], boxsize=1.0).query_ball_point(f["x"], H, return_length=True) - 1
+    assert 40 < np.median(cnt) < 56
+    assert cnt.min() >= 4
+    g = ics.lognormal(n_side=32, seed=21)
+    for k in ("x", "v", "h", "u", "alpha_visc"):
+        np.testing.assert_array_equal(f[k], g[k])
