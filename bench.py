@@ -42,6 +42,7 @@ VIEW_OUT = (32, 8, 24)
 # FP32 operations (FMA = 2) of the implemented formula: per candidate test
 # and per accepted pair of each loop
 FLOPS_CANDIDATE = 8
+FLOPS_EXACT = 14      # two-float separation, r^2 and both loop criteria
 FLOPS_PAIR = (73, 52, 113)
 # FP32 CUDA-core peak: 148 SMs x 128 lanes x 2 flop x 2.032 GHz
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
@@ -153,7 +154,7 @@ def oracle_sample(f, nsample: int, seed: int):
     return pairs, dt
 
 
-def precision_study(off, f, sel, ref, steps):
+def precision_study(off, f, sel, ref, steps, mixed_step):
     """Per-loop error of the mixed-precision and the all-FP64 batched paths
     against the oracle on the sampled particles, and the FP64 step time."""
     import torch
@@ -161,7 +162,7 @@ def precision_study(off, f, sel, ref, steps):
     from oracle import compare
     H = oracle.KERNEL_GAMMA * np.asarray(f["h"][sel], np.float64)
     res = {"sample": int(len(sel))}
-    off.batch_step()
+    mixed_step()
     got = off.export()
     e = compare.errors({k: v[sel] for k, v in got.items()}, ref, H)
     res["mixed"] = {"per_loop": compare.per_loop(e), "fields": e}
@@ -252,9 +253,17 @@ class StepTimer:
     def step(self, record: bool):
         from paper_2606_23891_b300 import sph
         off = self.off
-        batched = self.pipeline == "batched"
+        lists = self.pipeline == "list"
+        batched = self.pipeline in ("batched", "list")
         nb = off.binfo["nbundles"] if batched else off.nbundles()
         st = off.stream
+        if lists:
+            e0 = self.ev() if record else None
+            off.list_build()
+            e1 = self.ev() if record else None
+            self.launches += 2 * nb
+            if record:
+                self.recs.append((-1, e0, e1, e1, e1))
         for loop in range(3):
             sph.sph_init(off.store, loop, off.params, st)
             self.launches += 1
@@ -266,7 +275,11 @@ class StepTimer:
                 else:
                     off.pack(loop, b)
                 e1 = self.ev() if record else None
-                if batched:
+                if lists:
+                    sph.sph_batch_list_interact(off.bplan, loop, b, off.bbuf_in.data_ptr(),
+                                                off.bbuf_out.data_ptr(), off.blist.data_ptr(),
+                                                off.blist_bytes, off.params, st)
+                elif batched:
                     sph.sph_batch_interact(off.bplan, loop, b, off.bbuf_in.data_ptr(),
                                            off.bbuf_out.data_ptr(), off.params, st)
                 else:
@@ -289,6 +302,9 @@ class StepTimer:
         out = {(s, l): 0.0 for s in ("pack", "kernel", "unpack") for l in range(3)}
         cnt = {l: 0 for l in range(3)}
         for loop, e0, e1, e2, e3 in self.recs:
+            if loop < 0:        # neighbour-list build (once per step, all bundles)
+                out[("list", 0)] = out.get(("list", 0), 0.0) + e0.elapsed_time(e1)
+                continue
             out[("pack", loop)] += e0.elapsed_time(e1)
             out[("kernel", loop)] += e1.elapsed_time(e2)
             out[("unpack", loop)] += e2.elapsed_time(e3)
@@ -405,6 +421,134 @@ def run_host_staged(f, layouts, steps, bundle_slots):
             "h2d_link": "pinned host memory, cudaMemcpyAsync on 2 streams", "layouts": out}
 
 
+def plan_candidates(f, leaf_max: int = 128) -> dict:
+    """Candidate pairs per loop under the uniform grid of the per-task cycle
+    (cell pairs: 2 n_i n_j, self n_i (n_i - 1)) and under the octree-leaf
+    plan (each leaf's particles x those of its neighbour entries); host-only
+    plan builds, nothing runs on the GPU."""
+    from paper_2606_23891_b300 import sph
+    x = np.ascontiguousarray(f["x"], np.float64)
+    h = np.ascontiguousarray(f["h"], np.float32)
+    n = x.shape[0]
+    out = {}
+    try:
+        perm = np.empty(n, np.int64)
+        t = sph.sph_tasks_build(n, x.ctypes.data, h.ctypes.data, sph.grid_params(),
+                                perm.ctypes.data)
+        info = sph.sph_tasks_info(t)
+        ncell = info["ncell_x"] * info["ncell_y"] * info["ncell_z"]
+        ci = np.empty(info["ntasks"], np.int32)
+        cj = np.empty(info["ntasks"], np.int32)
+        cs = np.empty(ncell + 1, np.int64)
+        sph.sph_tasks_get(t, ci.ctypes.data, cj.ctypes.data, 0, cs.ctypes.data, 0)
+        sph.sph_tasks_destroy(t)
+        cnt = np.diff(cs).astype(np.float64)
+        ni, nj = cnt[ci], np.where(cj >= 0, cnt[np.maximum(cj, 0)], 0.0)
+        out["grid"] = {"ncell": [info["ncell_" + a] for a in "xyz"],
+                       "max_cell": info["max_cell"],
+                       "candidates": float(np.where(cj >= 0, 2 * ni * nj, ni * (ni - 1)).sum())}
+    except sph.SphError as e:
+        out["grid"] = {"unsupported": str(e)}
+    perm, ls, nbs, nb = sph.sph_tree_plan(x, h, leaf_max=leaf_max)
+    cnt = np.diff(ls).astype(np.float64)
+    owner = np.repeat(np.arange(cnt.size), np.diff(nbs))
+    out["tree"] = {"leaf_max": leaf_max, "leaves": int(cnt.size),
+                   "candidates": float((cnt[owner] * cnt[nb >> 6]).sum())}
+    return out
+
+
+def run_cosmology(args, ws, peaks):
+    """Clustered set (lognormal, sigma(ln rho) = 2): the batched pipeline on the
+    octree-leaf plan, autotuned, per layout, with CUDA-graph replay."""
+    import torch
+    from paper_2606_23891_b300 import ics, sph
+    from paper_2606_23891_b300.autotune import GraphStep, tune_tree
+    from paper_2606_23891_b300.pipeline import Offload
+    t = time.perf_counter()
+    f = ics.lognormal(n_side=args.cosmo_n_side)
+    t_gen = time.perf_counter() - t
+    n = f["x"].shape[0]
+    H = 1.825742 * f["h"].astype(np.float64)
+    t = time.perf_counter()
+    off = Offload(f, layout=args.cosmo_layouts[0], plan="tree", leaf_max=128)
+    t_build = time.perf_counter() - t
+    pairs = [off.count_pairs(l) for l in range(3)]
+    tuning = tune_tree(off, reps=1, step="list") if args.autotune else None
+    grid = plan_candidates(f, off.leaf_max)
+    res = {"workload": "lognormal%d: %d^3 particles from a lognormal density field, "
+                       "sigma(ln rho) = 2, octree-leaf plan" % (args.cosmo_n_side, args.cosmo_n_side),
+           "particles": n, "support_range": [float(H.min()), float(H.max())],
+           "generate_s": t_gen, "plan_build_s": t_build, "candidates_per_loop": grid,
+           "pairs": dict(zip(LOOP_NAMES, pairs)),
+           "pairs_per_particle": [p / n for p in pairs], "autotune": tuning,
+           "plan": {k: off.binfo[k] for k in ("cells", "max_cell", "nbrs", "threads",
+                                              "nbundles", "max_slots")},
+           "layouts": {}}
+    res["plan"]["leaf_max"] = off.leaf_max
+    head = None
+    for lname in args.cosmo_layouts:
+        o = off if lname == args.cosmo_layouts[0] else Offload(f, layout=lname, share=off)
+        res["layouts"][lname] = {}
+        for pipeline in (["list", "batched"] if o is off else ["list"]):
+            total_ms, timer, _ = run_layout(o, args.steps, args.warmup, ws, None, pipeline)
+            total_ms = barrier_max(total_ms, ws)
+            st, cnt = timer.stage_ms()
+            ms = total_ms / args.steps
+            loops = {}
+            for l in range(3):
+                pk, kr, up = (st[(s_, l)] / args.steps for s_ in ("pack", "kernel", "unpack"))
+                loops[LOOP_NAMES[l]] = {"pack_ms": pk, "kernel_ms": kr, "unpack_ms": up,
+                                        "kernel_useful_fp32_TFLOPs":
+                                            pairs[l] * FLOPS_PAIR[l] / (kr * 1e-3) / 1e12}
+            r = {"ms_per_step": ms, "pair_interactions_per_s": sum(pairs) * ws / (ms * 1e-3),
+                 "loops": loops}
+            if ("list", 0) in st:
+                r["list_build_ms"] = st[("list", 0)] / args.steps
+            res["layouts"][lname][pipeline] = r
+            if head is None:
+                head = (st, cnt, ms, timer.launches)
+        if o is not off:
+            o.close()
+            del o
+            torch.cuda.empty_cache()
+    gs = GraphStep(off, step=off.list_step)
+    for _ in range(args.warmup):
+        gs.replay()
+    torch.cuda.synchronize()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record()
+    for _ in range(args.steps):
+        gs.replay()
+    g1.record()
+    torch.cuda.synchronize()
+    gms = barrier_max(g0.elapsed_time(g1), ws) / args.steps
+    res["cuda_graph"] = {"ms_per_step": gms,
+                         "pair_interactions_per_s": sum(pairs) * ws / (gms * 1e-3)}
+    del gs
+    st, cnt, ms, launches = head
+    top = max(st, key=lambda k: st[k])
+    stage, loop = top
+    ncand = grid["tree"]["candidates"]
+    if stage == "list":
+        nbl = off.binfo["nbundles"]
+        dur = st[top] / (args.steps * nbl)
+        ach = (ncand * FLOPS_CANDIDATE + pairs[2] * FLOPS_EXACT) / nbl / (dur * 1e-3) / 1e12
+        name = "neighbour-list build (tree plan)"
+    else:
+        dur = st[top] / cnt[loop]
+        ach = pairs[loop] * FLOPS_PAIR[loop] / cnt[loop] * args.steps / (dur * 1e-3) / 1e12
+        name = "list interaction/%s (tree plan)" % LOOP_NAMES[loop]
+    res["roofline"] = {"kernel": name, "bound": "alu", "achieved": ach,
+                       "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": ach / FP32_PEAK_TFLOPS}
+    res["gpu_launches_per_step"] = launches / args.steps
+    off.close()
+    del off
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_2606_23891_b300 import ics, sph
@@ -425,9 +569,9 @@ def run_ours(args, ws, rank, local):
     per_layout = {}
     head = None
     tuning = None
-    if "batched" in args.pipelines and args.autotune:
+    if ("batched" in args.pipelines or "list" in args.pipelines) and args.autotune:
         from paper_2606_23891_b300.autotune import tune
-        tuning = tune(base, reps=1)
+        tuning = tune(base, reps=1, step="list" if args.head_pipeline == "list" else "batched")
         args.batch_threads = tuning["threads"]
     else:
         base.batch(threads=args.batch_threads)
@@ -451,8 +595,11 @@ def run_ours(args, ws, rank, local):
                 "pair_interactions_per_s": pairs[l] / ((pk + kr + up) * 1e-3),
                 "kernel_useful_fp32_TFLOPs": pairs[l] * FLOPS_PAIR[l] / (kr * 1e-3) / 1e12,
             }
-        return {"ms_per_step": ms_step,
-                "pair_interactions_per_s": sum(pairs) * ws / (ms_step * 1e-3), "loops": loops}
+        res = {"ms_per_step": ms_step,
+               "pair_interactions_per_s": sum(pairs) * ws / (ms_step * 1e-3), "loops": loops}
+        if ("list", 0) in st:
+            res["list_build_ms"] = st[("list", 0)] / args.steps
+        return res
 
     for lname in args.layouts:
         off = base if lname == args.layouts[0] else Offload(
@@ -478,10 +625,10 @@ def run_ours(args, ws, rank, local):
     ms_step = total_ms / args.steps
     value = sum(pairs) * ws / (ms_step * 1e-3)
     graph = None
-    if args.head_pipeline == "batched":
+    if args.head_pipeline in ("batched", "list"):
         # the same step recorded once into a CUDA graph and replayed
         from paper_2606_23891_b300.autotune import GraphStep
-        gs = GraphStep(off)
+        gs = GraphStep(off, step=off.list_step if args.head_pipeline == "list" else None)
         for _ in range(args.warmup):
             gs.replay()
         torch.cuda.synchronize()
@@ -501,7 +648,18 @@ def run_ours(args, ws, rank, local):
     per_step = cnt[loop] / args.steps             # launches per step (bundles)
     dur = st[top] / cnt[loop]                     # ms per launch
     peaks = measured_peaks()
-    if stage == "kernel":
+    if stage == "list":
+        # the neighbour-list build: the candidate tests of the cell pairs (hi-only
+        # r^2 against the support) and the exact two-float decision on each pair
+        per_step = off.binfo["nbundles"]
+        dur = st[top] / (args.steps * per_step)
+        flops = (ncand * FLOPS_CANDIDATE + pairs[2] * FLOPS_EXACT) / per_step
+        achieved = flops / (dur * 1e-3) / 1e12
+        roof = {"kernel": "neighbour-list build", "bound": "alu",
+                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"}
+    elif stage == "kernel":
         # useful FP32 work only: accepted pairs x the pair body; the candidate
         # tests of the cell pairs (most skipped by the projection windows) are
         # reported beside it, not counted as achieved work
@@ -543,9 +701,11 @@ def run_ours(args, ws, rank, local):
                          "scans (neighbour densities included), %.1f s"
                          % (args.cpu_sample, args.n_side, t)}
     precision = None
-    if cpu is not None and args.precision_steps > 0 and args.head_pipeline == "batched":
+    if cpu is not None and args.precision_steps > 0 and args.head_pipeline in ("batched", "list"):
         sel, ref = oracle_sample.last
-        precision = precision_study(off, f, sel, ref, args.precision_steps)
+        precision = precision_study(off, f, sel, ref, args.precision_steps,
+                                    off.list_step if args.head_pipeline == "list"
+                                    else off.batch_step)
         precision["mixed_ms_per_step"] = ms_step
     cfg_vals = {"tasks": base.info["ntasks"], "bundles": base.info["nbundles"],
                 "bbundles": base.binfo["nbundles"],
@@ -559,6 +719,15 @@ def run_ours(args, ws, rank, local):
         staged = run_host_staged(f, args.host_layouts, args.host_steps, args.host_bundle_slots)
         for lname, v in staged["layouts"].items():
             v["pair_interactions_per_s"] = sum(pairs) / (v["ms_per_step"] * 1e-3)
+    cosmo = None
+    if args.cosmo_n_side > 0:
+        if staged is None:
+            off.close()
+            base.close()
+            del off, base
+            torch.cuda.empty_cache()
+        del f
+        cosmo = run_cosmology(args, ws, peaks)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -590,6 +759,7 @@ def run_ours(args, ws, rank, local):
         "autotune": tuning,
         "host_staged": staged,
         "precision": precision,
+        "cosmology": cosmo,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -611,10 +781,14 @@ def main(argv=None):
     ap.add_argument("--n-side", type=int, default=N_SIDE)
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--ref-sample", type=int, default=2)
+    ap.add_argument("--cosmo-n-side", type=int, default=376,
+                    help="clustered (lognormal) set on the tree plan; 0: skip")
+    ap.add_argument("--cosmo-layouts", type=lambda s: s.split(","),
+                    default=["pack_force_type", "aos"])
     ap.add_argument("--precision-steps", type=int, default=2,
                     help="timed steps of the all-FP64 path (0: skip the precision study)")
-    ap.add_argument("--pipelines", default="plain,batched")
-    ap.add_argument("--head-pipeline", default="batched")
+    ap.add_argument("--pipelines", default="plain,batched,list")
+    ap.add_argument("--head-pipeline", default="list")
     ap.add_argument("--batch-threads", type=int, default=128)
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--host-steps", type=int, default=2)

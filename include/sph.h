@@ -256,7 +256,9 @@ int sph_count_pairs(sph_tasks t, int loop, int bundle, const void *dev_buf_in,
                     const sph_params *p, unsigned long long *dev_count,
                     void *stream);
 
-/* Wait for `stream` and report errors latched by kernels (SPH_EBOUNDS). */
+/* Wait for `stream` and report errors latched by kernels: SPH_EBOUNDS (an
+ * index outside its buffers), SPH_ETIMEOUT (a bounded wait ran out),
+ * SPH_ENOMEM (a neighbour-list pool ran out). */
 int sph_sync(void *stream);
 
 /* ---- host-staged offload (Sec. 2.3, the paper's own setting) ------------
@@ -402,6 +404,35 @@ int sph_batch_plan_info(sph_batch b, int64_t info[4]);
  * sph_batch_buffer_bytes_fp64(b, 0) bytes as scratch. */
 int sph_batch_count_pairs(sph_store s, sph_batch b, int loop, void *dev_buf_in,
                           const sph_params *p, unsigned long long *dev_count, void *stream);
+
+/* ---- neighbour-list variant of the batched cycle --------------------------
+ * The batched interaction kernels test all candidates of a target's
+ * neighbour entries again in each loop.  The list variant tests them once per
+ * step: sph_batch_list_build packs the density view of each bundle and
+ * stores, for every target particle, the bundle slots of the j with
+ * r < max(H_i, H_j) (flagged when r < H_i), decided exactly as the loops
+ * decide; sph_batch_offload_loop_list then runs each loop over the lists
+ * (pack -> list loop -> unpack per bundle, ghost after density).  Results
+ * equal the batched cycle's up to the rounding order of r^2.
+ * The list buffer (caller memory, 256-byte aligned) holds a header, per-item
+ * tables and a pool of chunks of 2048 entries; sph_batch_list_bytes(b, c)
+ * is the size with room for c chunks.  If the pool runs out, the build marks
+ * the buffer, the loops skip their pairs, and sph_sync returns SPH_ENOMEM;
+ * sph_batch_list_status (synchronous) then gives the chunks needed.  Lists
+ * depend on positions and h only: build once per step, before the density
+ * loop, with the same plan. */
+size_t sph_batch_list_bytes(sph_batch b, int64_t chunks);
+int sph_batch_list_build(sph_store s, sph_batch b, void *dev_buf_in, void *dev_list,
+                         size_t list_bytes, const sph_params *p, void *stream);
+int sph_batch_list_status(const void *dev_list, int64_t *chunks_needed, int *overflow);
+/* One bundle's list loop (after sph_batch_pack of the same loop and bundle);
+ * results land in dev_buf_out for sph_batch_unpack. */
+int sph_batch_list_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in,
+                            void *dev_buf_out, const void *dev_list, size_t list_bytes,
+                            const sph_params *p, void *stream);
+int sph_batch_offload_loop_list(sph_store s, sph_batch b, int loop, void *dev_buf_in,
+                                void *dev_buf_out, const void *dev_list, size_t list_bytes,
+                                const sph_params *p, void *stream);
 
 /* All-FP64 variant of the batched cycle (precision study): the same cells and
  * results, every arithmetic step in FP64 (positions, separations, kernel

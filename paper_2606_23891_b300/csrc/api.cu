@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -16,6 +18,7 @@
 #include "store_kernels.cuh"
 #include "batch_kernels.cuh"
 #include "fp64_kernels.cuh"
+#include "list_kernels.cuh"
 
 namespace sph {
 
@@ -124,6 +127,59 @@ int launch_binteract(const BInteractArgs &a, cudaStream_t st) {
     if (g <= 0) return SPH_OK;
     k_binteract<LOOP, T><<<g, T, 0, st>>>(a);
     return launch_check("batch interaction kernel");
+}
+
+// Persistent launch: as many CTAs as fit on the device at once (occupancy
+// looked up once per kernel and device), at most one per work item.
+template <typename Kernel, typename... Args>
+int launch_persistent(Kernel kernel, int threads, int nitems, cudaStream_t st, const char *what,
+                      Args... args) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> grid_of;
+    int dev = 0;
+    if (int rc = cuda_check(cudaGetDevice(&dev), "get device")) return rc;
+    int grid_max = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto key = std::make_pair((const void *)kernel, dev);
+        auto itg = grid_of.find(key);
+        if (itg == grid_of.end()) {
+            int per_sm = 0, sms = 0;
+            if (int rc = cuda_check(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel,
+                                                                                  threads, 0),
+                                    "occupancy"))
+                return rc;
+            if (int rc = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount,
+                                                           dev),
+                                    "SM count"))
+                return rc;
+            itg = grid_of.emplace(key, (per_sm > 0 ? per_sm : 1) * sms).first;
+        }
+        grid_max = itg->second;
+    }
+    const int g = nitems < grid_max ? nitems : grid_max;
+    if (g <= 0) return SPH_OK;
+    kernel<<<g, threads, 0, st>>>(args...);
+    return launch_check(what);
+}
+
+template <int LOOP>
+int dispatch_bloop(int threads, const BInteractArgs &a, const ListView &L, long long item0,
+                   cudaStream_t st) {
+    if (threads == 64)
+        return launch_persistent(k_bloop<LOOP, 64>, 64, a.nitems, st, "list loop", a, L, item0);
+    if (threads == 256)
+        return launch_persistent(k_bloop<LOOP, 256>, 256, a.nitems, st, "list loop", a, L, item0);
+    return launch_persistent(k_bloop<LOOP, 128>, 128, a.nitems, st, "list loop", a, L, item0);
+}
+
+inline int dispatch_blist(int threads, const BInteractArgs &a, const ListView &L, long long item0,
+                          cudaStream_t st) {
+    if (threads == 64)
+        return launch_persistent(k_blist<64>, 64, a.nitems, st, "list build", a, L, item0);
+    if (threads == 256)
+        return launch_persistent(k_blist<256>, 256, a.nitems, st, "list build", a, L, item0);
+    return launch_persistent(k_blist<128>, 128, a.nitems, st, "list build", a, L, item0);
 }
 
 template <int LOOP>
@@ -583,6 +639,9 @@ int sph_sync(void *stream) {
     if (w) {
         unsigned int z = 0;
         cudaMemcpyToSymbol(g_error_word, &z, sizeof(z));
+        if (w & 4u)
+            return fail(SPH_ENOMEM, "neighbour list buffer too small: read "
+                                    "sph_batch_list_status and grow it (word 0x%x)", w);
         if (w & 2u)
             return fail(SPH_ETIMEOUT, "a kernel's bounded wait for its copies ran out (word 0x%x)",
                         w);
@@ -896,13 +955,8 @@ int sph_batch_pack(sph_store s, sph_batch b, int loop, int bundle, void *dev_buf
     return launch_check("batch pack");
 }
 
-int sph_batch_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in,
-                       void *dev_buf_out, const sph_params *p, void *stream) {
-    if (int rc = check_batch(b, bundle)) return rc;
-    if (int rc = check_loop(loop)) return rc;
-    if (int rc = check_params(p)) return rc;
-    if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_buf_out || !aligned256(dev_buf_out))
-        return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
+static BInteractArgs interact_args(sph_batch b, int bundle, const void *dev_buf_in,
+                                   void *dev_buf_out, const sph_params *p) {
     const BatchBundle &bb = b->bundles[bundle];
     BInteractArgs a{};
     a.cells = b->d_cells + bb.cell0;
@@ -923,6 +977,7 @@ int sph_batch_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in
     for (int d = 0; d < 3; ++d) {
         a.shift_hi[d] = (float)b->box[d];
         a.shift_lo[d] = (float)(b->box[d] - (double)a.shift_hi[d]);
+        a.half[d] = (float)(0.5 * b->box[d]);
     }
     a.active_bin = p->active_bin;
     a.pa.beta = a.beta;
@@ -930,6 +985,18 @@ int sph_batch_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in
     a.pa.gamma = a.gamma;
     a.pa.delta = a.delta;
     a.pa.active_bin = a.active_bin;
+    return a;
+}
+
+int sph_batch_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in,
+                       void *dev_buf_out, const sph_params *p, void *stream) {
+    if (int rc = check_batch(b, bundle)) return rc;
+    if (int rc = check_loop(loop)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_buf_out || !aligned256(dev_buf_out))
+        return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
+    const BatchBundle &bb = b->bundles[bundle];
+    BInteractArgs a = interact_args(b, bundle, dev_buf_in, dev_buf_out, p);
     cudaStream_t st = (cudaStream_t)stream;
     if (bb.nitems == 0) return SPH_OK;
     if (int rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st),
@@ -1119,4 +1186,92 @@ int sph_batch_count_pairs(sph_store s, sph_batch b, int loop, void *dev_buf_in,
     }
     return SPH_OK;
 }
+
+// ---- neighbour-list variant of the batched cycle ---------------------------
+size_t sph_batch_list_bytes(sph_batch b, int64_t chunks) {
+    if (!b || chunks < 0) return 0;
+    return (size_t)ListLayout::bytes((int64_t)b->items.size(), chunks);
+}
+
+int sph_batch_list_build(sph_store s, sph_batch b, void *dev_buf_in, void *dev_list,
+                         size_t list_bytes, const sph_params *p, void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (!b) return fail(SPH_EINVAL, "NULL batch handle");
+    if (int rc = check_params(p)) return rc;
+    if (s->n != b->n) return fail(SPH_EINVAL, "store and batch disagree on particle count");
+    if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_list || !aligned256(dev_list))
+        return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
+    const int64_t NI = (int64_t)b->items.size();
+    if ((int64_t)list_bytes < ListLayout::fixed(NI) + 512)
+        return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
+    cudaStream_t st = (cudaStream_t)stream;
+    ListView L = ListLayout::view(dev_list, NI, (int64_t)list_bytes);
+    if (int rc = cuda_check(cudaMemsetAsync(L.hdr, 0, sizeof(ListHdr), st), "reset list header"))
+        return rc;
+    for (int k = 0; k < (int)b->bundles.size(); ++k) {
+        const BatchBundle &bb = b->bundles[k];
+        if (bb.nitems == 0) continue;
+        if (int rc = sph_batch_pack(s, b, SPH_DENSITY, k, dev_buf_in, p, stream)) return rc;
+        BInteractArgs a = interact_args(b, k, dev_buf_in, nullptr, p);
+        if (int rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st),
+                                "reset work queue"))
+            return rc;
+        if (int rc = dispatch_blist(b->threads, a, L, bb.item0, st)) return rc;
+    }
+    return SPH_OK;
+}
+
+int sph_batch_list_status(const void *dev_list, int64_t *chunks_needed, int *overflow) {
+    if (!dev_list || !chunks_needed || !overflow) return fail(SPH_EINVAL, "NULL argument");
+    ListHdr h{};
+    if (int rc = cuda_check(cudaMemcpy(&h, dev_list, sizeof(h), cudaMemcpyDeviceToHost),
+                            "read list header"))
+        return rc;
+    *chunks_needed = (int64_t)h.chunks_used;
+    *overflow = (int)h.overflow;
+    return SPH_OK;
+}
+
+int sph_batch_list_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in,
+                            void *dev_buf_out, const void *dev_list, size_t list_bytes,
+                            const sph_params *p, void *stream) {
+    if (int rc = check_batch(b, bundle)) return rc;
+    if (int rc = check_loop(loop)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_buf_out || !aligned256(dev_buf_out) ||
+        !dev_list || !aligned256(dev_list))
+        return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
+    const int64_t NI = (int64_t)b->items.size();
+    if ((int64_t)list_bytes < ListLayout::fixed(NI) + 512)
+        return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
+    const BatchBundle &bb = b->bundles[bundle];
+    if (bb.nitems == 0) return SPH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    ListView L = ListLayout::view(const_cast<void *>(dev_list), NI, (int64_t)list_bytes);
+    BInteractArgs a = interact_args(b, bundle, dev_buf_in, dev_buf_out, p);
+    if (int rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st),
+                            "reset work queue"))
+        return rc;
+    if (loop == SPH_DENSITY) return dispatch_bloop<SPH_DENSITY>(b->threads, a, L, bb.item0, st);
+    if (loop == SPH_GRADIENT) return dispatch_bloop<SPH_GRADIENT>(b->threads, a, L, bb.item0, st);
+    return dispatch_bloop<SPH_FORCE>(b->threads, a, L, bb.item0, st);
+}
+
+int sph_batch_offload_loop_list(sph_store s, sph_batch b, int loop, void *dev_buf_in,
+                                void *dev_buf_out, const void *dev_list, size_t list_bytes,
+                                const sph_params *p, void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (!b) return fail(SPH_EINVAL, "NULL batch handle");
+    if (int rc = check_loop(loop)) return rc;
+    if (int rc = sph_init(s, loop, p, stream)) return rc;
+    for (int k = 0; k < (int)b->bundles.size(); ++k) {
+        if (int rc = sph_batch_pack(s, b, loop, k, dev_buf_in, p, stream)) return rc;
+        if (int rc = sph_batch_list_interact(b, loop, k, dev_buf_in, dev_buf_out, dev_list,
+                                             list_bytes, p, stream))
+            return rc;
+        if (int rc = sph_batch_unpack(s, b, loop, k, dev_buf_out, dev_buf_in, stream)) return rc;
+    }
+    return sph_ghost(s, loop, p, stream);
+}
+
 }  // extern "C"

@@ -239,6 +239,7 @@ struct BInteractArgs {
     long long S;
     float kernel_gamma, gamma, beta, delta;
     float shift_hi[3], shift_lo[3];   // box edge as a two-float value
+    float half[3];                    // half the box edge (image choice of the list loops)
     int active_bin;
     PhysArgs pa;  // parameters the pair bodies read (beta)
 };

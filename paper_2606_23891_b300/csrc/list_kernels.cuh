@@ -1,0 +1,337 @@
+// Neighbour-list variant of the batched interaction kernels.
+//
+// The tile kernels (k_binteract) test every candidate of the 27 neighbour
+// cells (or leaf entries) again in each of the three loops, and run the pair
+// body per lane over that lane's own hits, so lanes with fewer hits idle.
+// Here the candidate tests run once per step:
+//
+// k_blist   persistent warps over the same work items: stage neighbour tiles,
+//           cull by the warp box, prefilter on hi-only separations, take the
+//           exact two-float decision of both loop criteria (r < H_i for
+//           density and gradient, r < max(H_i, H_j) for force) and append
+//           each accepted j's bundle slot to the lane's list, bit 31 set when
+//           r < H_i.  Lists are stored in chunks of 64 entries per lane for
+//           the 32 lanes of an item (lane-interleaved, so the loops read them
+//           coalesced); chunks come from a pool through an atomic counter
+//           and are chained per item.  The content and order of each list
+//           are fixed (neighbour entry, tile, slot order), only the chunks'
+//           places in the pool vary, so results are reproducible.
+// k_bloop   persistent warps over the items again: each lane walks its list,
+//           gathers the j records of the loop's view from the bundle buffer
+//           (read-only path), applies the periodic image shift (decided from
+//           the hi-part separation: supports are below half the box, so the
+//           image is unique) as an exact two-float add, and runs the pair body.
+//           Lanes' lists differ in length by the neighbour-count scatter only.
+//
+// When the pool runs out, the build marks the list header and the error word
+// (bit 2); the loops then skip all pairs and sph_sync reports it.
+#pragma once
+#include "batch_kernels.cuh"
+
+namespace sph {
+
+constexpr int kLPer = 64;                  // entries per lane per chunk
+constexpr int kLChunk = 32 * kLPer;        // entries per chunk (8 KB)
+constexpr int kLMaxChain = 256;            // chunks per item (16384 entries per lane)
+constexpr uint32_t kLNone = 0xffffffffu;
+
+struct ListHdr {
+    unsigned long long chunks_used;  // chunks requested (counts past the pool too)
+    unsigned int overflow;           // 1: the pool ran out, 2: an item's chain did
+    unsigned int pad;
+};
+
+struct ListView {
+    ListHdr *hdr;
+    uint32_t *first;    // per plan item: first chunk (kLNone: empty)
+    uint32_t *lcount;   // per plan item and lane: list length
+    uint32_t *next;     // per chunk: next chunk of the same item
+    uint32_t *entries;  // pool of chunks
+    unsigned long long pool;
+};
+
+// Byte layout of a list buffer: header, first[NI], lcount[32 NI], next[pool],
+// entries[pool * kLChunk], each starting on a 256-byte boundary.
+struct ListLayout {
+    static int64_t r256(int64_t b) { return (b + 255) / 256 * 256; }
+    static int64_t fixed(int64_t nitems) { return 256 + r256(4 * nitems) + r256(128 * nitems); }
+    static int64_t bytes(int64_t nitems, int64_t pool) {
+        return fixed(nitems) + r256(4 * pool) + r256(4 * pool * kLChunk);
+    }
+    static int64_t pool_for(int64_t nitems, int64_t bytes) {
+        int64_t p = (bytes - fixed(nitems)) / (4 + 4 * (int64_t)kLChunk);
+        while (p > 0 && ListLayout::bytes(nitems, p) > bytes) --p;
+        return p < 0 ? 0 : p;
+    }
+    static ListView view(void *base, int64_t nitems, int64_t bytes) {
+        ListView v{};
+        char *b = (char *)base;
+        v.pool = (unsigned long long)pool_for(nitems, bytes);
+        v.hdr = (ListHdr *)b;
+        v.first = (uint32_t *)(b + 256);
+        v.lcount = (uint32_t *)(b + 256 + r256(4 * nitems));
+        v.next = (uint32_t *)(b + fixed(nitems));
+        v.entries = (uint32_t *)(b + fixed(nitems) + r256(4 * (int64_t)v.pool));
+        return v;
+    }
+};
+
+// ---------------------------------------------------------------- build --
+template <int T>
+__global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView L, long long item0) {
+    using BL = BLayout<SPH_DENSITY>;
+    constexpr int kWarps = T / 32;
+    __shared__ float4 smw[kWarps][2][kWTile];
+    __shared__ uint32_t chainw[kWarps][kLMaxChain];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4(*sm)[kWTile] = smw[warp];
+    uint32_t *chain = chainw[warp];
+    const float4 *rec0 = reinterpret_cast<const float4 *>(a.in + BL::rec(0, a.S));
+    const float4 *rec1 = reinterpret_cast<const float4 *>(a.in + BL::rec(1, a.S));
+    const float *cellh = reinterpret_cast<const float *>(a.in + BL::cellh(a.S));
+    constexpr int kSelf = 1 | (1 << 2) | (1 << 4);
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(a.counter, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= a.nitems) break;
+        const long long gitem = item0 + it;
+        const BItemDev W = a.items[it];
+        const int tcell = a.targets[W.target].cell;
+        const BCellDev C = a.cells[tcell];
+        const int i = W.i0 + lane;
+        const bool valid = i < C.n;
+        const long long slot = (long long)C.slot + i;
+        float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0;
+        if (valid) {
+            o0 = rec0[slot];
+            o1 = rec1[slot];
+        }
+        const float Hi = o0.w;
+        const float H2i = Hi * Hi;
+        const float Hpre = Hi + a.delta;
+        const float Hpre2 = Hpre * Hpre;
+        float bmn[3], bmx[3], hw;
+        bmn[0] = valid ? o0.x : INFINITY; bmx[0] = valid ? o0.x : -INFINITY;
+        bmn[1] = valid ? o0.y : INFINITY; bmx[1] = valid ? o0.y : -INFINITY;
+        bmn[2] = valid ? o0.z : INFINITY; bmx[2] = valid ? o0.z : -INFINITY;
+        hw = valid ? Hpre : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                bmn[d] = fminf(bmn[d], __shfl_xor_sync(0xffffffffu, bmn[d], o));
+                bmx[d] = fmaxf(bmx[d], __shfl_xor_sync(0xffffffffu, bmx[d], o));
+            }
+            hw = fmaxf(hw, __shfl_xor_sync(0xffffffffu, hw, o));
+        }
+        int count = 0;      // this lane's entries
+        int nch = 0;        // chunks of the item (warp-uniform)
+        bool lost = false;  // the pool or the chain ran out (warp-uniform)
+        const BTargetDev &Tg = a.targets[W.target];
+#pragma unroll 1
+        for (int e = Tg.nb0; e < Tg.nb0 + Tg.nnb; ++e) {
+            const BNbrDev E = a.nbrs[e];
+            const int nb = E.cell;
+            const BCellDev Cn = a.cells[nb];
+            const int code = E.code;
+            float sh[3], sl[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int c = ((code >> (2 * d)) & 3) - 1;
+                sh[d] = c == 0 ? 0.f : (c > 0 ? a.shift_hi[d] : -a.shift_hi[d]);
+                sl[d] = c == 0 ? 0.f : (c > 0 ? a.shift_lo[d] : -a.shift_lo[d]);
+            }
+            const float R = fmaxf(hw, cellh[nb] + a.delta);
+            const float R2 = R * R;
+            const bool self = nb == tcell && code == kSelf;
+#pragma unroll 1
+            for (int j0 = 0; j0 < Cn.n; j0 += kWTile) {
+                const int jn = min(kWTile, Cn.n - j0);
+                __syncwarp();
+                // stage: positions with the shift added, (H_j + delta)^2 for the
+                // prefilter in .w of the hi record and H_j^2 in .w of the lo one
+                unsigned int cw[kWTile / 32];
+#pragma unroll
+                for (int w = 0; w < kWTile / 32; ++w) {
+                    const int k = 32 * w + lane;
+                    bool in = false;
+                    if (k < jn) {
+                        const long long js = (long long)Cn.slot + j0 + k;
+                        float4 r0 = rec0[js], r1 = rec1[js];
+                        if (code != kSelf) {
+                            add2(r0.x, r1.x, sh[0], sl[0]);
+                            add2(r0.y, r1.y, sh[1], sl[1]);
+                            add2(r0.z, r1.z, sh[2], sl[2]);
+                        }
+                        const float Hj = r0.w, Hjp = Hj + a.delta;
+                        r1.w = Hj * Hj;
+                        r0.w = Hjp * Hjp;
+                        sm[0][k] = r0;
+                        sm[1][k] = r1;
+                        const float ex = fmaxf(fmaxf(bmn[0] - r0.x, r0.x - bmx[0]), 0.f);
+                        const float ey = fmaxf(fmaxf(bmn[1] - r0.y, r0.y - bmx[1]), 0.f);
+                        const float ez = fmaxf(fmaxf(bmn[2] - r0.z, r0.z - bmx[2]), 0.f);
+                        in = ex * ex + ey * ey + ez * ez < R2;
+                    }
+                    cw[w] = __ballot_sync(0xffffffffu, in);
+                }
+                __syncwarp();
+                // pass 1: hi-only prefilter under the wider (force) criterion
+                unsigned int hm[kWTile / 32];
+                int nh = 0;
+#pragma unroll
+                for (int w = 0; w < kWTile / 32; ++w) {
+                    unsigned int m = cw[w], h = 0;
+                    while (m) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1;
+                        const float4 pj = sm[0][32 * w + b];
+                        const float dx = o0.x - pj.x, dy = o0.y - pj.y, dz = o0.z - pj.z;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        h |= r2 < fmaxf(Hpre2, pj.w) ? (1u << b) : 0u;
+                    }
+                    if (self && (i - j0) >= 32 * w && (i - j0) < 32 * w + 32)
+                        h &= ~(1u << (i - j0 - 32 * w));
+                    hm[w] = valid ? h : 0u;
+                    nh += __popc(hm[w]);
+                }
+                // room for up to nh more entries in every lane's chain; once
+                // an item is lost its further chunks are still counted, so the
+                // header ends with the pool size a complete build needs
+                const int need = __reduce_max_sync(0xffffffffu, count + nh);
+                while (need > nch * kLPer) {
+                    uint32_t c = kLNone;
+                    if (lane == 0) {
+                        const unsigned long long u = atomicAdd(&L.hdr->chunks_used, 1ull);
+                        if (!lost && u < L.pool && nch < kLMaxChain) {
+                            c = (uint32_t)u;
+                            chain[nch] = c;
+                            L.next[c] = kLNone;
+                            if (nch > 0) L.next[chain[nch - 1]] = c;
+                        } else if (!lost) {
+                            atomicMax(&L.hdr->overflow, nch < kLMaxChain ? 1u : 2u);
+                            atomicOr(&g_error_word, 4u);
+                        }
+                    }
+                    c = __shfl_sync(0xffffffffu, c, 0);
+                    __syncwarp();
+                    if (c == kLNone) lost = true;
+                    ++nch;
+                }
+                // exact decisions on the hits, appended in slot order
+#pragma unroll 1
+                for (int w = 0; w < kWTile / 32; ++w) {
+                    unsigned int m = hm[w];
+                    while (m) {
+                        const int j = 32 * w + (__ffs(m) - 1);
+                        m &= m - 1;
+                        const float4 p0 = sm[0][j], p1 = sm[1][j];
+                        const float dx = (o0.x - p0.x) + (o1.x - p1.x);
+                        const float dy = (o0.y - p0.y) + (o1.y - p1.y);
+                        const float dz = (o0.z - p0.z) + (o1.z - p1.z);
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const bool dens = r2 < H2i;
+                        if (!(dens || r2 < fmaxf(H2i, p1.w))) continue;
+                        if (!lost) {
+                            const uint32_t js = (uint32_t)(Cn.slot + j0 + j);
+                            L.entries[(long long)chain[count / kLPer] * kLChunk +
+                                      (count % kLPer) * 32 + lane] = js | (dens ? 0x80000000u : 0u);
+                        }
+                        ++count;
+                    }
+                }
+            }
+        }
+        L.lcount[gitem * 32 + lane] = valid && !lost ? (uint32_t)count : 0u;
+        if (lane == 0) L.first[gitem] = nch > 0 && !lost ? chain[0] : kLNone;
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- loops --
+template <int LOOP, int T>
+__global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? SPH_BMINB_FORCE : 1024) / T)
+    k_bloop(BInteractArgs a, ListView L, long long item0) {
+    using BL = BLayout<LOOP>;
+    constexpr int nf = NF<LOOP>::value;
+    const int lane = threadIdx.x & 31;
+    const float4 *rec[nf];
+#pragma unroll
+    for (int f = 0; f < nf; ++f) rec[f] = reinterpret_cast<const float4 *>(a.in + BL::rec(f, a.S));
+    const bool broken = L.hdr->overflow != 0u;
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(a.counter, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= a.nitems) break;
+        const long long gitem = item0 + it;
+        const BItemDev W = a.items[it];
+        const BCellDev C = a.cells[a.targets[W.target].cell];
+        const int i = W.i0 + lane;
+        const bool valid = i < C.n;
+        const long long slot = (long long)C.slot + i;
+        float4 own[nf];
+        Acc<LOOP> acc;
+        bool active = false;
+        if (valid) {
+#pragma unroll
+            for (int f = 0; f < nf; ++f) own[f] = rec[f][slot];
+            acc.init(own, a.delta);
+            active = LOOP != SPH_FORCE ||
+                     (int)reinterpret_cast<const int8_t *>(a.in + BL::tb(a.S))[slot] <= a.active_bin;
+        } else {
+#pragma unroll
+            for (int f = 0; f < nf; ++f) own[f] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const int cnt = valid && active && !broken ? (int)L.lcount[gitem * 32 + lane] : 0;
+        const int maxc = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
+        uint32_t chunk = L.first[gitem];
+#pragma unroll 1
+        for (int k = 0; k < maxc; ++k) {
+            if (k > 0 && k % kLPer == 0) chunk = L.next[chunk];
+            if (k >= cnt) continue;
+            const uint32_t ent = __ldg(&L.entries[(long long)chunk * kLChunk + (k % kLPer) * 32 + lane]);
+            if (LOOP != SPH_FORCE && !(ent & 0x80000000u)) continue;
+            const long long js = (long long)(ent & 0x7fffffffu);
+            float4 oth[nf];
+#pragma unroll
+            for (int f = 0; f < nf; ++f) oth[f] = __ldg(&rec[f][js]);
+            // periodic image: the hi-part separation exceeds half the box
+            {
+                const float ax = own[0].x - oth[0].x, ay = own[0].y - oth[0].y,
+                            az = own[0].z - oth[0].z;
+                if (ax > a.half[0]) add2(oth[0].x, oth[1].x, a.shift_hi[0], a.shift_lo[0]);
+                else if (ax < -a.half[0]) add2(oth[0].x, oth[1].x, -a.shift_hi[0], -a.shift_lo[0]);
+                if (ay > a.half[1]) add2(oth[0].y, oth[1].y, a.shift_hi[1], a.shift_lo[1]);
+                else if (ay < -a.half[1]) add2(oth[0].y, oth[1].y, -a.shift_hi[1], -a.shift_lo[1]);
+                if (az > a.half[2]) add2(oth[0].z, oth[1].z, a.shift_hi[2], a.shift_lo[2]);
+                else if (az < -a.half[2]) add2(oth[0].z, oth[1].z, -a.shift_hi[2], -a.shift_lo[2]);
+            }
+            const float dx = (own[0].x - oth[0].x) + (own[1].x - oth[1].x);
+            const float dy = (own[0].y - oth[0].y) + (own[1].y - oth[1].y);
+            const float dz = (own[0].z - oth[0].z) + (own[1].z - oth[1].z);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            acc.body(own, oth, dx, dy, dz, r2, a.pa);
+        }
+        if (valid) {
+            if constexpr (LOOP == SPH_DENSITY) {
+                acc.write(PhysArgs{nullptr, {}, {a.out, a.out + BL::r256(a.S * 16)}}, slot, own);
+            } else if constexpr (LOOP == SPH_GRADIENT) {
+                acc.write(PhysArgs{nullptr, {}, {a.out, nullptr}}, slot, own);
+            } else {
+                float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f);
+                float2 o1 = make_float2(0.f, 0.f);
+                if (active) {
+                    const float hf = reinterpret_cast<const float *>(a.in + BL::hf(a.S))[slot];
+                    o0 = make_float4(acc.ax, acc.ay, acc.az, acc.udt);
+                    o1 = make_float2(-(1.f / 3.f) * hf * acc.hsum, acc.vsig);
+                }
+                reinterpret_cast<float4 *>(a.out)[slot] = o0;
+                reinterpret_cast<float2 *>(a.out + BL::r256(a.S * 16))[slot] = o1;
+            }
+        }
+    }
+}
+
+}  // namespace sph

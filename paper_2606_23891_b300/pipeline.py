@@ -201,9 +201,16 @@ class Offload:
         return cnt[ci] + np.where(cj >= 0, cnt[np.maximum(cj, 0)], 0)
 
     # -- batched (cell-dedup) cycle --------------------------------------
-    def batch(self, max_target_cells: int = 0, threads: int = 128) -> None:
-        """Build the batched plan for this particle set and its buffers."""
+    def batch(self, max_target_cells: int = 0, threads: int = 128,
+              leaf_max: int | None = None) -> None:
+        """Build the batched plan for this particle set and its buffers
+        (``leaf_max``: tree plan only; the leaves' Morton order, and so the
+        store order, does not depend on it)."""
         self.close_batch()
+        if leaf_max is not None:
+            if self.plan != "tree":
+                raise ValueError("leaf_max applies to the tree plan only")
+            self.leaf_max = leaf_max
         if self.plan == "tree":
             perm = np.empty(self.n, np.int64)
             self.bplan = sph.sph_batch_build_tree(
@@ -229,6 +236,8 @@ class Offload:
         """Share another Offload's batched plan and buffers."""
         self.bplan, self.binfo = other.bplan, other.binfo
         self.bbuf_in, self.bbuf_out = other.bbuf_in, other.bbuf_out
+        self.blist = getattr(other, "blist", None)
+        self.blist_bytes = getattr(other, "blist_bytes", 0)
         self.bshared = True
 
     def batch_loop(self, loop: int) -> None:
@@ -261,8 +270,52 @@ class Offload:
             sph.sph_batch_offload_loop_fp64(self.store, self.bplan, loop, self.f64_in.data_ptr(),
                                             self.f64_out.data_ptr(), self.params, self.stream)
 
+    # -- neighbour-list variant ---------------------------------------------
+    def _alloc_list(self, chunks: int) -> None:
+        self.blist = None
+        torch.cuda.empty_cache()
+        self.blist_bytes = sph.sph_batch_list_bytes(self.bplan, chunks)
+        self.blist = torch.empty(self.blist_bytes, dtype=torch.uint8, device=self.device)
+
+    def list_build(self) -> None:
+        """Build the per-step neighbour lists (sized on first use: one
+        synchronous status read, the pool grown if it ran out)."""
+        if getattr(self, "blist", None) is None:
+            self._alloc_list(int(1.25 * self.binfo["items"]) + 16)
+            for _ in range(3):
+                sph.sph_batch_list_build(self.store, self.bplan, self.bbuf_in.data_ptr(),
+                                         self.blist.data_ptr(), self.blist_bytes, self.params,
+                                         self.stream)
+                need, overflow = sph.sph_batch_list_status(self.blist.data_ptr())
+                if not overflow:
+                    break
+                try:
+                    sph.sph_sync(self.stream)      # clears the latched pool error
+                except sph.SphError:
+                    pass
+                if overflow == 2:
+                    raise sph.SphError(6, "a particle has more neighbours than one list chain "
+                                       "holds (16384)")
+                self._alloc_list(int(1.05 * need) + 16)
+            return
+        sph.sph_batch_list_build(self.store, self.bplan, self.bbuf_in.data_ptr(),
+                                 self.blist.data_ptr(), self.blist_bytes, self.params,
+                                 self.stream)
+
+    def list_loop(self, loop: int) -> None:
+        sph.sph_batch_offload_loop_list(self.store, self.bplan, loop, self.bbuf_in.data_ptr(),
+                                        self.bbuf_out.data_ptr(), self.blist.data_ptr(),
+                                        self.blist_bytes, self.params, self.stream)
+
+    def list_step(self) -> None:
+        """Lists, then density -> ghost -> gradient -> force over them."""
+        self.list_build()
+        for loop in (sph.SPH_DENSITY, sph.SPH_GRADIENT, sph.SPH_FORCE):
+            self.list_loop(loop)
+
     def close_batch(self) -> None:
         self.f64_in = self.f64_out = None
+        self.blist = None
         if getattr(self, "bplan", None) is not None:
             if not getattr(self, "bshared", False):
                 sph.sph_batch_destroy(self.bplan)

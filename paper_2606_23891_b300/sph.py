@@ -128,6 +128,11 @@ def lib() -> C.CDLL:
         "sph_batch_buffer_bytes_fp64": (sz, [p, i]),
         "sph_batch_build_tree": (i, [i64, p, p, p, p, p, p]),
         "sph_batch_plan_info": (i, [p, p]),
+        "sph_batch_list_bytes": (sz, [p, i64]),
+        "sph_batch_list_build": (i, [p, p, p, p, sz, p, p]),
+        "sph_batch_list_status": (i, [p, p, p]),
+        "sph_batch_offload_loop_list": (i, [p, p, i, p, p, p, sz, p, p]),
+        "sph_batch_list_interact": (i, [p, i, i, p, p, p, sz, p, p]),
         "sph_tree_plan": (i, [i64, p, p, p, p, p, p, p, p, i64, p]),
         "sph_batch_count_pairs": (i, [p, p, i, p, p, p, p]),
         "sph_batch_offload_loop_fp64": (i, [p, p, i, p, p, p, p]),
@@ -369,6 +374,33 @@ def sph_batch_plan_info(b) -> dict:
 def sph_batch_count_pairs(s, b, loop: int, dev_in: int, p: Params, dev_count: int,
                           stream: int = 0):
     _ok(lib().sph_batch_count_pairs(s, b, loop, dev_in, C.byref(p), dev_count, stream))
+
+
+def sph_batch_list_bytes(b, chunks: int) -> int:
+    return lib().sph_batch_list_bytes(b, chunks)
+
+
+def sph_batch_list_build(s, b, dev_in: int, dev_list: int, list_bytes: int, p: Params,
+                         stream: int = 0):
+    _ok(lib().sph_batch_list_build(s, b, dev_in, dev_list, list_bytes, C.byref(p), stream))
+
+
+def sph_batch_list_status(dev_list: int):
+    need, ovf = C.c_int64(), C.c_int()
+    _ok(lib().sph_batch_list_status(dev_list, C.byref(need), C.byref(ovf)))
+    return need.value, ovf.value
+
+
+def sph_batch_list_interact(b, loop: int, bundle: int, dev_in: int, dev_out: int, dev_list: int,
+                            list_bytes: int, p: Params, stream: int = 0):
+    _ok(lib().sph_batch_list_interact(b, loop, bundle, dev_in, dev_out, dev_list, list_bytes,
+                                      C.byref(p), stream))
+
+
+def sph_batch_offload_loop_list(s, b, loop: int, dev_in: int, dev_out: int, dev_list: int,
+                                list_bytes: int, p: Params, stream: int = 0):
+    _ok(lib().sph_batch_offload_loop_list(s, b, loop, dev_in, dev_out, dev_list, list_bytes,
+                                          C.byref(p), stream))
 
 
 def sph_batch_info(b) -> dict:

@@ -1,0 +1,94 @@
+"""Neighbour-list variant of the batched cycle: the same results as the tile
+kernels (to the rounding order of r^2) and as the oracle, on the grid and
+the tree plans; pool sizing and its overflow report."""
+import numpy as np
+import pytest
+
+from paper_2606_23891_b300 import ics, sph
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2606_23891_b300.pipeline import Offload  # noqa: E402
+from test_parity_gpu import CONFIGS, check_physics, ragged, rms_err  # noqa: E402
+
+
+@pytest.mark.parametrize("threads", [64, 128, 256])
+@pytest.mark.parametrize("case", sorted(CONFIGS))
+def test_list_pass_matches_the_oracle(case, threads):
+    f = CONFIGS[case]()
+    off = Offload(f, layout="pack_force_type")
+    off.batch(threads=threads)
+    off.list_step()
+    check_physics(f, off.export())
+
+
+@pytest.mark.parametrize("mtc", [0, 37])
+def test_list_agrees_with_the_tile_kernels(mtc):
+    f = ragged(24, 8)
+    off = Offload(f, layout=6)
+    off.batch(max_target_cells=mtc)
+    off.batch_step()
+    a = off.export()
+    off.list_step()
+    b = off.export()
+    for k in a:
+        assert rms_err(b[k], a[k]) <= 1e-6, k
+
+
+def test_list_on_the_tree_plan_and_inactive_particles():
+    f = ics.lognormal(n_side=24, seed=31)
+    f["time_bin"][::4] = 5
+    off = Offload(f, layout=5, plan="tree", params=sph.params(active_bin=2))
+    off.batch(max_target_cells=101)
+    pre = {"a": np.full((f["x"].shape[0], 3), 7.0, np.float32)}
+    off.import_fields(pre, ("a",))
+    off.list_step()
+    got = off.export()
+    inactive = f["time_bin"] > 2
+    assert np.all(got["a"][inactive] == 7.0)
+    sel = np.nonzero(~inactive)[0]
+    check_physics(f, got, sel=sel, active_bin=2)
+
+
+def test_list_steps_are_reproducible_and_graph_replay_matches():
+    from paper_2606_23891_b300.autotune import GraphStep
+    f = ragged(12, 41)
+    off = Offload(f, layout=8)
+    off.batch(threads=64)
+    off.list_step()
+    a = off.export()
+    off.list_step()
+    b = off.export()
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    gs = GraphStep(off, step=off.list_step)
+    gs.replay()
+    torch.cuda.synchronize()
+    c = off.export()
+    for k in a:
+        np.testing.assert_array_equal(a[k], c[k], err_msg=k)
+
+
+def test_list_pool_overflow_is_reported_and_recovered():
+    f = ragged(12, 5)
+    off = Offload(f, layout=0)
+    off.batch()
+    small = sph.sph_batch_list_bytes(off.bplan, 2)
+    buf = torch.zeros(small, dtype=torch.uint8, device=off.device)
+    sph.sph_batch_list_build(off.store, off.bplan, off.bbuf_in.data_ptr(), buf.data_ptr(),
+                             small, off.params, off.stream)
+    need, overflow = sph.sph_batch_list_status(buf.data_ptr())
+    assert overflow and need > 2
+    with pytest.raises(sph.SphError):
+        sph.sph_sync(off.stream)
+    sph.sph_sync(off.stream)                      # the error was cleared
+    big = sph.sph_batch_list_bytes(off.bplan, need)
+    buf = torch.zeros(big, dtype=torch.uint8, device=off.device)
+    sph.sph_batch_list_build(off.store, off.bplan, off.bbuf_in.data_ptr(), buf.data_ptr(),
+                             big, off.params, off.stream)
+    need2, overflow2 = sph.sph_batch_list_status(buf.data_ptr())
+    assert not overflow2 and need2 == need
+    with pytest.raises(sph.SphError):             # buffer below the fixed tables
+        sph.sph_batch_list_build(off.store, off.bplan, off.bbuf_in.data_ptr(), buf.data_ptr(),
+                                 256, off.params, off.stream)
