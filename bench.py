@@ -449,11 +449,22 @@ def plan_candidates(f, leaf_max: int = 128) -> dict:
                        "candidates": float(np.where(cj >= 0, 2 * ni * nj, ni * (ni - 1)).sum())}
     except sph.SphError as e:
         out["grid"] = {"unsupported": str(e)}
+    def occupancy(c):
+        return {"min": int(c.min()), "max": int(c.max()), "mean": float(c.mean()),
+                "median": float(np.median(c))}
+
     perm, ls, nbs, nb = sph.sph_tree_plan(x, h, leaf_max=leaf_max)
     cnt = np.diff(ls).astype(np.float64)
     owner = np.repeat(np.arange(cnt.size), np.diff(nbs))
-    out["tree"] = {"leaf_max": leaf_max, "leaves": int(cnt.size),
+    out["tree"] = {"leaf_max": leaf_max, "leaves": int(cnt.size), "occupancy": occupancy(cnt),
                    "candidates": float((cnt[owner] * cnt[nb >> 6]).sum())}
+    # the cell tree's own rule (split while half the edge covers the largest
+    # support inside): occupancy to set beside the paper's cosmological trace
+    perm, ls, nbs, nb = sph.sph_tree_plan(x, h, leaf_max=8, rule=1)
+    cnt = np.diff(ls).astype(np.float64)
+    owner = np.repeat(np.arange(cnt.size), np.diff(nbs))
+    out["octree_rule"] = {"leaves": int(cnt.size), "occupancy": occupancy(cnt),
+                          "candidates": float((cnt[owner] * cnt[nb >> 6]).sum())}
     return out
 
 

@@ -380,7 +380,11 @@ typedef struct {
     double box[3];
     double kernel_gamma;
     int32_t leaf_max;    /* 8 .. 2048 */
-    int32_t reserved;    /* must be 0 */
+    int32_t rule;        /* 0: split while a node holds > leaf_max particles;
+                            1: the octree rule of the cell tree (Sec. 2.2) as well:
+                            split only while half the node's edge is >= the
+                            largest support of its particles, so leaves can
+                            hold far more than leaf_max */
 } sph_tree_params;
 int sph_batch_build_tree(int64_t n, const double *host_x, const float *host_h,
                          const sph_tree_params *tp, const sph_batch_params *bp,

@@ -225,7 +225,7 @@ int tree_plan(int64_t n, const double *x, const float *h, const sph_tree_params 
     if (n < 0 || (n > 0 && (!x || !h)) || !tp || !perm_out)
         return fail(SPH_EINVAL, "batch_build_tree: bad arguments");
     if (n > INT32_MAX) return fail(SPH_EUNSUPPORTED, "batch_build_tree: more than 2^31-1 particles");
-    if (tp->reserved != 0) return fail(SPH_EINVAL, "batch_build_tree: reserved must be 0");
+    if (tp->rule != 0 && tp->rule != 1) return fail(SPH_EINVAL, "batch_build_tree: rule must be 0 or 1");
     if (tp->leaf_max < 8 || tp->leaf_max > 2048)
         return fail(SPH_EINVAL, "batch_build_tree: leaf_max must be in [8, 2048]");
     if (!(tp->kernel_gamma > 0.0)) return fail(SPH_EINVAL, "batch_build_tree: kernel_gamma");
@@ -286,6 +286,14 @@ int tree_plan(int64_t n, const double *x, const float *h, const sph_tree_params 
     for (size_t q = 0; q < nodes.size(); ++q) {
         Node nd = nodes[q];
         if (nd.e - nd.b <= tp->leaf_max || nd.level == kMortonBits) continue;
+        if (tp->rule == 1) {
+            // half the node's edge must still cover the largest support inside
+            float hm = 0.f;
+            for (int64_t k = nd.b; k < nd.e; ++k) hm = std::max(hm, Hs[(size_t)k]);
+            double half = INFINITY;
+            for (int d = 0; d < 3; ++d) half = std::min(half, L[d] / (double)(2ll << nd.level));
+            if (half < (double)hm) continue;
+        }
         const int shift = 3 * (kMortonBits - 1 - nd.level);
         const int32_t first = (int32_t)nodes.size();
         int32_t nch = 0;

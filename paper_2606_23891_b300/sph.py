@@ -60,7 +60,7 @@ class BatchParams(C.Structure):
 
 class TreeParams(C.Structure):
     _fields_ = [("box", C.c_double * 3), ("kernel_gamma", C.c_double),
-                ("leaf_max", C.c_int32), ("reserved", C.c_int32)]
+                ("leaf_max", C.c_int32), ("rule", C.c_int32)]
 
 
 def params(gamma=5.0 / 3.0, kernel_gamma=1.825742, beta_visc=3.0,
@@ -332,14 +332,15 @@ def sph_batch_build_tree(n: int, x_ptr: int, h_ptr: int, box=(1.0, 1.0, 1.0),
     tp.box[:] = list(box)
     tp.kernel_gamma = kernel_gamma
     tp.leaf_max = leaf_max
-    tp.reserved = 0
+    tp.rule = 0
     bp = BatchParams(max_target_cells, threads, 0)
     _ok(lib().sph_batch_build_tree(n, x_ptr, h_ptr, C.byref(tp), C.byref(bp), perm_ptr,
                                    C.byref(h)))
     return h
 
 
-def sph_tree_plan(x, h, box=(1.0, 1.0, 1.0), kernel_gamma=1.825742, leaf_max: int = 64):
+def sph_tree_plan(x, h, box=(1.0, 1.0, 1.0), kernel_gamma=1.825742, leaf_max: int = 64,
+                  rule: int = 0):
     """Host-only tree plan: (perm, leaf_start, nb_start, nb) as numpy arrays."""
     import numpy as np
     x = np.ascontiguousarray(x, np.float64)
@@ -349,7 +350,7 @@ def sph_tree_plan(x, h, box=(1.0, 1.0, 1.0), kernel_gamma=1.825742, leaf_max: in
     tp.box[:] = list(box)
     tp.kernel_gamma = kernel_gamma
     tp.leaf_max = leaf_max
-    tp.reserved = 0
+    tp.rule = rule
     perm = np.empty(n, np.int64)
     ls = np.empty(n + 1, np.int64)
     nbs = np.empty(n + 1, np.int64)

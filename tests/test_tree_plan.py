@@ -19,8 +19,8 @@ def morton(x, box=1.0, bits=21):
     return key
 
 
-def plan(f, leaf_max):
-    return sph.sph_tree_plan(f["x"], f["h"], leaf_max=leaf_max)
+def plan(f, leaf_max, rule=0):
+    return sph.sph_tree_plan(f["x"], f["h"], leaf_max=leaf_max, rule=rule)
 
 
 def entries(nb):
@@ -51,9 +51,9 @@ def test_leaves_partition_the_particles_in_morton_order(case, leaf_max):
     assert nbs[0] == 0 and nbs[-1] == nb.size and np.all(np.diff(nbs) >= 1)
 
 
-@pytest.mark.parametrize("leaf_max", [8, 64])
+@pytest.mark.parametrize("leaf_max,rule", [(8, 0), (64, 0), (8, 1)])
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_neighbour_entries_cover_every_interacting_pair(case, leaf_max):
+def test_neighbour_entries_cover_every_interacting_pair(case, leaf_max, rule):
     """Every pair with r < max(H_i, H_j) (minimum image) must find j's leaf,
     with the shift that brings j's image next to i, among i's leaf entries;
     no entry repeats."""
@@ -61,7 +61,7 @@ def test_neighbour_entries_cover_every_interacting_pair(case, leaf_max):
     f = CASES[case]()
     x = np.asarray(f["x"], np.float64)
     H = (np.float32(KG) * f["h"]).astype(np.float64)
-    perm, ls, nbs, nb = plan(f, leaf_max)
+    perm, ls, nbs, nb = plan(f, leaf_max, rule)
     n = x.shape[0]
     leaf_of = np.empty(n, np.int64)                       # by original index
     leaf_of[perm] = np.repeat(np.arange(ls.size - 1), np.diff(ls))
@@ -89,6 +89,29 @@ def test_neighbour_entries_cover_every_interacting_pair(case, leaf_max):
     need = (leaf_of[i] * L + leaf_of[j]) * 64 + codes
     ok = np.isin(need, have)
     assert ok.all(), (i[~ok][:5], j[~ok][:5])
+
+
+@pytest.mark.parametrize("case", ["lognormal24", "lattice12"])
+def test_octree_rule_leaves(case):
+    """Rule 1 (the cell tree's rule): a leaf is split no further once half its
+    edge is below the largest support inside it; leaves hold up to thousands."""
+    f = CASES[case]()
+    H = np.float32(KG) * f["h"]
+    perm, ls, nbs, nb = plan(f, 8, rule=1)
+    perm0, ls0, _, _ = plan(f, 8, rule=0)
+    assert np.array_equal(perm, perm0)                   # same Morton order
+    k = morton(f["x"][perm])
+    cnt = np.diff(ls)
+    assert cnt.max() > 8 or case == "lattice12"
+    for l in range(cnt.size):
+        if cnt[l] <= 8:
+            continue
+        kk = k[ls[l]:ls[l + 1]]
+        # the leaf's level: the longest common Morton prefix of its keys
+        x = int(kk[0]) ^ int(kk[-1])
+        level = 21 - (x.bit_length() + 2) // 3
+        hmax = float(H[perm[ls[l]:ls[l + 1]]].max())
+        assert 1.0 / (2 << level) < hmax or level == 21, (l, level, hmax)
 
 
 def test_tree_plan_rejects_bad_input():
