@@ -438,6 +438,26 @@ int sph_batch_offload_loop_list(sph_store s, sph_batch b, int loop, void *dev_bu
                                 void *dev_buf_out, const void *dev_list, size_t list_bytes,
                                 const sph_params *p, void *stream);
 
+/* ---- adjoint of density -> ghost -> force (differentiation) --------------
+ * Gradient of L = sum_i |a_i|^2 + sum_i (du_i/dt)^2 (active particles) with
+ * respect to positions, masses and internal energies, for upstream adjoints
+ * dev_abar = dL/da (n x 3) and dev_ebar = dL/d(du/dt) (n), both in ORIGINAL
+ * particle order like the outputs dev_gx (n x 3, FP64), dev_gm, dev_gu (n).
+ * dev_store_perm is the permutation passed to sph_store_import (NULL for the
+ * identity).  Smoothing lengths, velocities and the switches' coefficients
+ * are held fixed.  Preconditions: a plan of one bundle, the store holding the
+ * results of the list cycle (sph_batch_list_build then the three
+ * sph_batch_offload_loop_list calls) on the current inputs, and that list
+ * buffer.  Scratch: sph_batch_adjoint_bytes(b) bytes (0 when the plan has
+ * more than one bundle).  Every particle gathers both directions of its
+ * pairs from its list: no atomics, deterministic.  FP32 arithmetic. */
+size_t sph_batch_adjoint_bytes(sph_batch b);
+int sph_batch_adjoint(sph_store s, sph_batch b, void *dev_buf_in, const void *dev_list,
+                      size_t list_bytes, void *dev_scratch, size_t scratch_bytes,
+                      const int64_t *dev_store_perm, const float *dev_abar,
+                      const float *dev_ebar, double *dev_gx, float *dev_gm, float *dev_gu,
+                      const sph_params *p, void *stream);
+
 /* All-FP64 variant of the batched cycle (precision study): the same cells and
  * results, every arithmetic step in FP64 (positions, separations, kernel
  * values, sums, ghost), results rounded to the FP32 store once.  Buffers of

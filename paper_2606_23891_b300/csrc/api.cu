@@ -19,6 +19,7 @@
 #include "batch_kernels.cuh"
 #include "fp64_kernels.cuh"
 #include "list_kernels.cuh"
+#include "adjoint_kernels.cuh"
 
 namespace sph {
 
@@ -1274,4 +1275,92 @@ int sph_batch_offload_loop_list(sph_store s, sph_batch b, int loop, void *dev_bu
     return sph_ghost(s, loop, p, stream);
 }
 
+
+// ---- adjoint of density -> ghost -> force ----------------------------------
+size_t sph_batch_adjoint_bytes(sph_batch b) {
+    if (!b || b->bundles.size() != 1) return 0;
+    const int64_t S = b->bundles[0].slots;
+    return (size_t)(((S * 16 * (kAdjRec + 4)) + 255) / 256 * 256 + 256);
+}
+
+int sph_batch_adjoint(sph_store s, sph_batch b, void *dev_buf_in, const void *dev_list,
+                      size_t list_bytes, void *dev_scratch, size_t scratch_bytes,
+                      const int64_t *dev_store_perm, const float *dev_abar,
+                      const float *dev_ebar, double *dev_gx, float *dev_gm, float *dev_gu,
+                      const sph_params *p, void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (!b) return fail(SPH_EINVAL, "NULL batch handle");
+    if (int rc = check_params(p)) return rc;
+    if (s->n != b->n) return fail(SPH_EINVAL, "store and batch disagree on particle count");
+    if (b->bundles.size() != 1)
+        return fail(SPH_EUNSUPPORTED, "the adjoint needs a plan of one bundle "
+                                      "(max_target_cells <= 0)");
+    if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_list || !aligned256(dev_list) ||
+        !dev_scratch || !aligned256(dev_scratch))
+        return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
+    if (!dev_abar || !dev_ebar || !dev_gx || !dev_gm || !dev_gu)
+        return fail(SPH_EINVAL, "NULL adjoint array");
+    if (scratch_bytes < sph_batch_adjoint_bytes(b))
+        return fail(SPH_EINVAL, "scratch smaller than sph_batch_adjoint_bytes");
+    const int64_t NI = (int64_t)b->items.size();
+    if ((int64_t)list_bytes < ListLayout::fixed(NI) + 512)
+        return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
+    const BatchBundle &bb = b->bundles[0];
+    if (bb.nitems == 0) return SPH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the slot order of the lists: the bundle's density pack
+    if (int rc = sph_batch_pack(s, b, SPH_DENSITY, 0, dev_buf_in, p, stream)) return rc;
+    AdjArgs a{};
+    a.cells = b->d_cells + bb.cell0;
+    a.targets = b->d_targets + bb.target0;
+    a.items = b->d_items + bb.item0;
+    a.counter = b->d_counter;
+    a.nitems = (int)bb.nitems;
+    a.item0 = bb.item0;
+    a.L = ListLayout::view(const_cast<void *>(dev_list), NI, (int64_t)list_bytes);
+    a.S = bb.slots;
+    a.perm = reinterpret_cast<const int32_t *>((const char *)dev_buf_in +
+                                               BLayout<SPH_DENSITY>::perm(bb.slots));
+    a.store_perm = dev_store_perm;
+    char *sc = (char *)dev_scratch;
+    a.rec = reinterpret_cast<float4 *>(sc);
+    a.g = a.rec + kAdjRec * bb.slots;
+    a.sg = a.g + 2 * bb.slots;
+    const int roles[A_NUM][2] = {{F_X, 0}, {F_X, 1}, {F_X, 2}, {F_V, 0}, {F_V, 1}, {F_V, 2},
+                                 {F_MASS, 0}, {F_H, 0}, {F_U, 0}, {F_RHO, 0}, {F_FGRADH, 0},
+                                 {F_BALS, 0}, {F_AVISC, 0}, {F_ADIFF, 0}, {F_CS, 0},
+                                 {F_PRES, 0}, {F_TBIN, 0}, {F_RHODH, 0}, {F_DIVV, 0},
+                                 {F_ROTV, 0}, {F_ROTV, 1}, {F_ROTV, 2}};
+    for (int r = 0; r < A_NUM; ++r) a.f[r] = at(s, roles[r][0], roles[r][1]);
+    a.abar = dev_abar;
+    a.ebar = dev_ebar;
+    a.gx_out = dev_gx;
+    a.gm_out = dev_gm;
+    a.gu_out = dev_gu;
+    a.kernel_gamma = (float)p->kernel_gamma;
+    a.gamma = (float)p->gamma;
+    a.beta = (float)p->beta_visc;
+    a.eps = (float)p->balsara_eps;
+    for (int d = 0; d < 3; ++d) {
+        a.shift_hi[d] = (float)b->box[d];
+        a.shift_lo[d] = (float)(b->box[d] - (double)a.shift_hi[d]);
+        a.half[d] = (float)(0.5 * b->box[d]);
+    }
+    a.active_bin = p->active_bin;
+    const unsigned g = grid_for(bb.slots, 256);
+    k_adj_pack<<<g, 256, 0, st>>>(a);
+    if (int rc = launch_check("adjoint pack")) return rc;
+    if (int rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st), "queue"))
+        return rc;
+    if (int rc = launch_persistent(k_adj_pairs<0>, 128, a.nitems, st, "force adjoint", a))
+        return rc;
+    k_adj_ghost<<<g, 256, 0, st>>>(a);
+    if (int rc = launch_check("ghost adjoint")) return rc;
+    if (int rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st), "queue"))
+        return rc;
+    if (int rc = launch_persistent(k_adj_pairs<1>, 128, a.nitems, st, "density adjoint", a))
+        return rc;
+    k_adj_scatter<<<g, 256, 0, st>>>(a);
+    return launch_check("adjoint scatter");
+}
 }  // extern "C"

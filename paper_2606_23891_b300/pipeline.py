@@ -122,6 +122,42 @@ class Offload:
                              self.stream)
         torch.cuda.synchronize(self.device)
 
+    def import_device(self, tensors: dict) -> None:
+        """Copy device tensors (original particle order, contiguous, the
+        field's dtype) into the store on the offload's stream."""
+        sph.sph_store_import(self.store, fields_struct(tensors), self.d_perm.data_ptr(),
+                             self.stream)
+
+    def export_device(self, names) -> dict:
+        """Store fields as device tensors in original particle order (enqueued
+        on the offload's stream; no host synchronisation)."""
+        dev = self.device_fields(names)
+        sph.sph_store_export(self.store, fields_struct(dev), self.d_perm.data_ptr(),
+                             self.stream)
+        return dev
+
+    def adjoint(self, abar, ebar):
+        """Gradient of sum |a|^2 + sum (du/dt)^2 through the last list step,
+        for upstream adjoints abar (n, 3) and ebar (n,) on the device; returns
+        device tensors (dL/dx (n, 3) FP64, dL/dm (n,), dL/du (n,))."""
+        need = sph.sph_batch_adjoint_bytes(self.bplan)
+        if need == 0:
+            raise sph.SphError(6, "the adjoint needs a plan of one bundle")
+        if getattr(self, "adj_scratch", None) is None or self.adj_scratch.numel() < need:
+            self.adj_scratch = torch.empty(need, dtype=torch.uint8, device=self.device)
+        abar = abar.to(self.device, torch.float32).contiguous()
+        ebar = ebar.to(self.device, torch.float32).contiguous()
+        gx = torch.empty((self.n, 3), dtype=torch.float64, device=self.device)
+        gm = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        gu = torch.empty(self.n, dtype=torch.float32, device=self.device)
+        sph.sph_batch_adjoint(self.store, self.bplan, self.bbuf_in.data_ptr(),
+                              self.blist.data_ptr(), self.blist_bytes,
+                              self.adj_scratch.data_ptr(), self.adj_scratch.numel(),
+                              self.d_perm.data_ptr(), abar.data_ptr(), ebar.data_ptr(),
+                              gx.data_ptr(), gm.data_ptr(), gu.data_ptr(), self.params,
+                              self.stream)
+        return gx, gm, gu
+
     def device_fields(self, names) -> dict:
         out = {}
         for name in names:

@@ -133,6 +133,8 @@ def lib() -> C.CDLL:
         "sph_batch_list_status": (i, [p, p, p]),
         "sph_batch_offload_loop_list": (i, [p, p, i, p, p, p, sz, p, p]),
         "sph_batch_list_interact": (i, [p, i, i, p, p, p, sz, p, p]),
+        "sph_batch_adjoint_bytes": (sz, [p]),
+        "sph_batch_adjoint": (i, [p, p, p, p, sz, p, sz, p, p, p, p, p, p, p, p]),
         "sph_tree_plan": (i, [i64, p, p, p, p, p, p, p, p, i64, p]),
         "sph_batch_count_pairs": (i, [p, p, i, p, p, p, p]),
         "sph_batch_offload_loop_fp64": (i, [p, p, i, p, p, p, p]),
@@ -396,6 +398,18 @@ def sph_batch_list_interact(b, loop: int, bundle: int, dev_in: int, dev_out: int
                             list_bytes: int, p: Params, stream: int = 0):
     _ok(lib().sph_batch_list_interact(b, loop, bundle, dev_in, dev_out, dev_list, list_bytes,
                                       C.byref(p), stream))
+
+
+def sph_batch_adjoint_bytes(b) -> int:
+    return lib().sph_batch_adjoint_bytes(b)
+
+
+def sph_batch_adjoint(s, b, dev_in: int, dev_list: int, list_bytes: int, dev_scratch: int,
+                      scratch_bytes: int, dev_store_perm: int, dev_abar: int, dev_ebar: int,
+                      dev_gx: int, dev_gm: int, dev_gu: int, p: Params, stream: int = 0):
+    _ok(lib().sph_batch_adjoint(s, b, dev_in, dev_list, list_bytes, dev_scratch, scratch_bytes,
+                                dev_store_perm or None, dev_abar, dev_ebar, dev_gx, dev_gm,
+                                dev_gu, C.byref(p), stream))
 
 
 def sph_batch_offload_loop_list(s, b, loop: int, dev_in: int, dev_out: int, dev_list: int,

@@ -1,0 +1,143 @@
+"""GPU adjoint of density -> ghost -> force against the oracle's gradient.
+
+Bars: the GPU path computes in FP32 like the forward (errors ~1e-6 relative
+on a and du/dt); the gradient is a sum of many pair terms whose signs cancel,
+so errors are measured against the norm of each gradient field over the
+compared particles: ||g - g_ref|| / ||g_ref|| <= 1e-4 for x, m and u."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import adjoint
+from paper_2606_23891_b300 import ics, sph
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2606_23891_b300.autodiff import loss  # noqa: E402
+from paper_2606_23891_b300.pipeline import Offload  # noqa: E402
+from test_adjoint_oracle import system  # noqa: E402
+
+
+def norm_err(g, ref):
+    g = np.asarray(g, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return np.linalg.norm(g - ref) / np.linalg.norm(ref)
+
+
+def gpu_grad(f, **kw):
+    off = Offload(f, layout=kw.pop("layout", "pack_force_type"), **kw)
+    off.batch()
+    dev = off.device
+    x = torch.tensor(np.asarray(f["x"], np.float64), device=dev, requires_grad=True)
+    m = torch.tensor(np.asarray(f["mass"], np.float32), device=dev, requires_grad=True)
+    u = torch.tensor(np.asarray(f["u"], np.float32), device=dev, requires_grad=True)
+    L = loss(x, m, u, off)
+    L.backward()
+    return L.item(), x.grad.cpu().numpy(), m.grad.cpu().numpy(), u.grad.cpu().numpy(), off
+
+
+@pytest.mark.parametrize("plan", ["grid", "tree"])
+@pytest.mark.parametrize("alpha_diff", [0.0, 0.3])
+def test_adjoint_matches_the_oracle_gradient(plan, alpha_diff):
+    f = system(n_side=12, seed=5, alpha_diff=alpha_diff)
+    ref_loss, rx, rm, ru = adjoint.gradient(f)
+    L, gx, gm, gu, _ = gpu_grad(f, plan=plan)
+    assert abs(L - ref_loss) <= 1e-5 * ref_loss
+    assert norm_err(gx, rx) <= 1e-4
+    assert norm_err(gm, rm) <= 1e-4
+    assert norm_err(gu, ru) <= 1e-4
+
+
+def test_adjoint_with_inactive_particles():
+    f = system(n_side=12, seed=6, alpha_diff=0.2)
+    f["time_bin"][::5] = 4
+    ref_loss, rx, rm, ru = adjoint.gradient(f, active_bin=2)
+    off = Offload(f, layout=6, params=sph.params(active_bin=2))
+    off.batch()
+    dev = off.device
+    x = torch.tensor(np.asarray(f["x"], np.float64), device=dev, requires_grad=True)
+    m = torch.tensor(np.asarray(f["mass"], np.float32), device=dev, requires_grad=True)
+    u = torch.tensor(np.asarray(f["u"], np.float32), device=dev, requires_grad=True)
+    from paper_2606_23891_b300.autodiff import chain_outputs
+    a, udt = chain_outputs(x, m, u, off)
+    act = torch.tensor(np.asarray(f["time_bin"]) <= 2, device=dev)
+    L = ((a.double() ** 2).sum(dim=1) + udt.double() ** 2)[act].sum()
+    L.backward()
+    assert abs(float(L) - ref_loss) <= 1e-5 * ref_loss
+    assert norm_err(x.grad.cpu().numpy(), rx) <= 1e-4
+    assert norm_err(m.grad.cpu().numpy(), rm) <= 1e-4
+    assert norm_err(u.grad.cpu().numpy(), ru) <= 1e-4
+
+
+def test_adjoint_is_deterministic():
+    f = system(n_side=12, seed=7)
+    _, gx1, gm1, gu1, _ = gpu_grad(f)
+    _, gx2, gm2, gu2, _ = gpu_grad(f)
+    np.testing.assert_array_equal(gx1, gx2)
+    np.testing.assert_array_equal(gm1, gm2)
+    np.testing.assert_array_equal(gu1, gu2)
+
+
+def test_adjoint_needs_one_bundle():
+    f = system(n_side=12, seed=8)
+    off = Offload(f, layout=0)
+    off.batch(max_target_cells=10)
+    off.list_step()
+    assert sph.sph_batch_adjoint_bytes(off.bplan) == 0
+    with pytest.raises(sph.SphError):
+        off.adjoint(torch.zeros((off.n, 3)), torch.zeros(off.n))
+
+
+# ------------------------------------------------- Gresho 64^3, FD on 32 --
+def local_loss(f, k, sub, box=(1.0, 1.0, 1.0)):
+    """The part of the loss that moves with particle k: |a|^2 + (du/dt)^2 of
+    the particles within 2 H_max of k, from the C oracle on the subset `sub`
+    (every particle within 4.5 H_max of k, which holds all the neighbour
+    densities those outputs need)."""
+    g = {key: np.ascontiguousarray(v[sub]) for key, v in f.items()}
+    x = g["x"]
+    H = oracle.KERNEL_GAMMA * np.asarray(g["h"], np.float64)
+    kk = int(np.nonzero(sub == k)[0][0])
+    d = x - x[kk]
+    d -= np.rint(d)
+    near = np.nonzero(np.sqrt((d * d).sum(axis=1)) < 2.05 * H.max())[0]
+    out = oracle.chain(g, oracle.params(box=box), near.astype(np.int64))
+    return float(((out["a"] ** 2).sum(axis=1) + out["u_dt"] ** 2).sum())
+
+
+def test_gresho_64_adjoint_against_central_differences():
+    f = ics.gresho(n_side=64)
+    n = f["x"].shape[0]
+    L, gx, gm, gu, _ = gpu_grad(f)
+    rng = np.random.Generator(np.random.PCG64(4))
+    picks = rng.choice(n, 32, replace=False)
+    Hmax = oracle.KERNEL_GAMMA * float(f["h"].max())
+    fdx, fdm, fdu, gpx, gpm, gpu_ = [], [], [], [], [], []
+    for k in picks:
+        d = f["x"] - f["x"][k]
+        d -= np.rint(d)
+        sub = np.nonzero(np.sqrt((d * d).sum(axis=1)) < 4.5 * Hmax)[0]
+        for c in range(3):
+            eps = 1e-6 * Hmax
+            g = {key: v.copy() for key, v in f.items()}
+            g["x"][k, c] += eps
+            lp = local_loss(g, k, sub)
+            g["x"][k, c] -= 2 * eps
+            lm = local_loss(g, k, sub)
+            fdx.append((lp - lm) / (2 * eps))
+            gpx.append(gx[k, c])
+        for name, out, gref in (("mass", fdm, gm), ("u", fdu, gu)):
+            g = {key: v.copy() for key, v in f.items()}
+            v0 = np.float32(f[name][k])
+            up = np.float32(v0 * np.float32(1 + 1e-3))
+            dn = np.float32(v0 * np.float32(1 - 1e-3))
+            g[name][k] = up
+            lp = local_loss(g, k, sub)
+            g[name][k] = dn
+            lm = local_loss(g, k, sub)
+            out.append((lp - lm) / (float(up) - float(dn)))
+            (gpm if name == "mass" else gpu_).append(gref[k])
+    assert norm_err(gpx, fdx) <= 1e-4
+    assert norm_err(gpm, fdm) <= 1e-4
+    assert norm_err(gpu_, fdu) <= 1e-4
