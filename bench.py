@@ -560,6 +560,101 @@ def run_cosmology(args, ws, peaks):
     return res
 
 
+def run_adjoint(args, ws):
+    """Differentiation workload: gradient of sum |a|^2 + sum (du/dt)^2 with
+    respect to x, m, u through density -> ghost -> force, on the Gresho
+    recipe at each requested size (forward list step and adjoint timed), with
+    a central-difference check of the gradient on a few particles of the
+    smallest size (FP64 C oracle on local subsets)."""
+    import torch
+    import oracle
+    from paper_2606_23891_b300 import ics
+    from paper_2606_23891_b300.pipeline import Offload
+    res = {"loss": "sum_i |a_i|^2 + sum_i (du_i/dt)^2", "wrt": ["x", "m", "u"], "sizes": {}}
+    for ns in args.adjoint_n_side:
+        f = ics.gresho(n_side=ns)
+        off = Offload(f, layout="pack_force_type")
+        off.batch(threads=args.batch_threads)
+        dev = off.device
+        off.list_step()
+        ab = off.export_device(("a", "u_dt"))
+        abar, ebar = 2 * ab["a"], 2 * ab["u_dt"]
+
+        def timed(fn, reps):
+            fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+        fwd = timed(off.list_step, args.steps)
+        bwd = timed(lambda: off.adjoint(abar, ebar), args.steps)
+        pairs = off.count_pairs(2)
+        r = {"particles": off.n, "forward_ms": fwd, "adjoint_ms": bwd,
+             "force_pairs": pairs,
+             "adjoint_pair_visits_per_s": 2 * pairs / (bwd * 1e-3)}
+        if ns == min(args.adjoint_n_side) and args.adjoint_fd > 0:
+            gx, gm, gu = (t.cpu().numpy() for t in off.adjoint(abar, ebar))
+            r["fd_check"] = adjoint_fd(f, gx, gm, gu, args.adjoint_fd)
+        res["sizes"]["gresho%d" % ns] = r
+        off.close()
+        del off
+        torch.cuda.empty_cache()
+    return res
+
+
+def adjoint_fd(f, gx, gm, gu, npick: int) -> dict:
+    """Central differences of the FP64 oracle loss for npick particles: each
+    on the subset within 4.5 H_max of the particle, the loss restricted to
+    the outputs within 2 H_max of it (all that move with it)."""
+    import oracle
+    n = f["x"].shape[0]
+    Hmax = oracle.KERNEL_GAMMA * float(f["h"].max())
+    rng = np.random.Generator(np.random.PCG64(4))
+
+    def local(g, k, sub):
+        s = {key: np.ascontiguousarray(v[sub]) for key, v in g.items()}
+        kk = int(np.nonzero(sub == k)[0][0])
+        d = s["x"] - s["x"][kk]
+        d -= np.rint(d)
+        near = np.nonzero(np.sqrt((d * d).sum(axis=1)) < 2.05 * Hmax)[0].astype(np.int64)
+        out = oracle.chain(s, oracle.params(), near)
+        return float(((out["a"] ** 2).sum(axis=1) + out["u_dt"] ** 2).sum())
+    got = {"x": [], "m": [], "u": []}
+    ref = {"x": [], "m": [], "u": []}
+    t = time.perf_counter()
+    for k in rng.choice(n, npick, replace=False):
+        d = f["x"] - f["x"][k]
+        d -= np.rint(d)
+        sub = np.nonzero(np.sqrt((d * d).sum(axis=1)) < 4.5 * Hmax)[0]
+        for c in range(3):
+            g = {key: v.copy() for key, v in f.items()}
+            eps = 1e-6 * Hmax
+            g["x"][k, c] += eps
+            lp = local(g, k, sub)
+            g["x"][k, c] -= 2 * eps
+            lm = local(g, k, sub)
+            ref["x"].append((lp - lm) / (2 * eps))
+            got["x"].append(gx[k, c])
+        for name, key, gv in (("mass", "m", gm), ("u", "u", gu)):
+            g = {kk: v.copy() for kk, v in f.items()}
+            v0 = np.float32(f[name][k])
+            up, dn = np.float32(v0 * np.float32(1.001)), np.float32(v0 * np.float32(0.999))
+            g[name][k] = up
+            lp = local(g, k, sub)
+            g[name][k] = dn
+            lm = local(g, k, sub)
+            ref[key].append((lp - lm) / (float(up) - float(dn)))
+            got[key].append(gv[k])
+    err = {key: float(np.linalg.norm(np.subtract(got[key], ref[key])) / np.linalg.norm(ref[key]))
+           for key in got}
+    return {"particles": npick, "rel_err_norm": err, "seconds": time.perf_counter() - t}
+
+
 def run_ours(args, ws, rank, local):
     import torch
     from paper_2606_23891_b300 import ics, sph
@@ -721,24 +816,19 @@ def run_ours(args, ws, rank, local):
     cfg_vals = {"tasks": base.info["ntasks"], "bundles": base.info["nbundles"],
                 "bbundles": base.binfo["nbundles"],
                 "store_gb": off.nbytes / 1e9, "buf_gb": base.buf_in.numel() / 1e9}
+    # the Gresho stores and buffers are not needed by the remaining sections
+    off.close()
+    base.close()
+    del off, base
+    torch.cuda.empty_cache()
     staged = None
     if args.host_steps > 0:
-        off.close()
-        base.close()
-        del off, base
-        torch.cuda.empty_cache()
         staged = run_host_staged(f, args.host_layouts, args.host_steps, args.host_bundle_slots)
         for lname, v in staged["layouts"].items():
             v["pair_interactions_per_s"] = sum(pairs) / (v["ms_per_step"] * 1e-3)
-    cosmo = None
-    if args.cosmo_n_side > 0:
-        if staged is None:
-            off.close()
-            base.close()
-            del off, base
-            torch.cuda.empty_cache()
-        del f
-        cosmo = run_cosmology(args, ws, peaks)
+    del f
+    adj = run_adjoint(args, ws) if args.adjoint_n_side else None
+    cosmo = run_cosmology(args, ws, peaks) if args.cosmo_n_side > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -771,6 +861,7 @@ def run_ours(args, ws, rank, local):
         "host_staged": staged,
         "precision": precision,
         "cosmology": cosmo,
+        "adjoint": adj,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -796,6 +887,10 @@ def main(argv=None):
                     help="clustered (lognormal) set on the tree plan; 0: skip")
     ap.add_argument("--cosmo-layouts", type=lambda s: s.split(","),
                     default=["pack_force_type", "aos"])
+    ap.add_argument("--adjoint-n-side", type=lambda s: [int(v) for v in s.split(",") if v],
+                    default=[64, 256], help="Gresho sizes of the adjoint timing ('' skips)")
+    ap.add_argument("--adjoint-fd", type=int, default=8,
+                    help="particles of the central-difference check of the adjoint")
     ap.add_argument("--precision-steps", type=int, default=2,
                     help="timed steps of the all-FP64 path (0: skip the precision study)")
     ap.add_argument("--pipelines", default="plain,batched,list")
