@@ -33,7 +33,8 @@ BENCH_LAYOUT = "pack_force_type"
 BUNDLE_SLOTS = 1 << 25
 N_SIDE = 256
 ALL_LAYOUTS = ("aos", "aos_random", "pack_grad", "pack_force", "pack_shared",
-               "pack_grad_type", "pack_force_type", "pack_shared_type", "soa")
+               "pack_grad_type", "pack_force_type", "pack_shared_type", "soa",
+               "pack_force_repl", "fused")
 LOOP_NAMES = ("density", "gradient", "force")
 # algorithmic bytes: view read + written per slot (pack), result read per slot
 # plus output fields read + written per particle (unpack)
@@ -378,7 +379,7 @@ def run_e2e(off, f, steps, warmup, pipeline="plain"):
     return start.elapsed_time(end) / steps, h2d, d2h
 
 
-def run_host_staged(f, layouts, steps, bundle_slots):
+def run_host_staged(f, layouts, steps, bundle_slots, fission_bundles=2):
     """The paper's own setting: store in pinned host memory, host pack and
     unpack (all host cores), double-buffered H2D / kernel / D2H on two
     streams.  Wall-clock per step, plus the isolated host pack and unpack
@@ -412,13 +413,63 @@ def run_host_staged(f, layouts, steps, bundle_slots):
                 tu += time.perf_counter() - t2
                 tp += t2 - t1
             loops[LOOP_NAMES[l]] = {"host_pack_ms": 1e3 * tp, "host_unpack_ms": 1e3 * tu}
-        # the isolated unpacks above folded garbage into the store: rerun a
-        # clean step is not needed, the store is not read again
-        out[lname] = {"ms_per_step": 1e3 * step_s, "loops": loops}
+        # loop-fission variants (Sec. 3.3, Fig. 4) on the first bundles of
+        # each loop; the isolated unpacks fold result buffers into the store,
+        # which is not read again
+        fission = {}
+        nbf = min(nb, fission_bundles)
+        for name, fv in sph.FISSION.items():
+            tp = tu = 0.0
+            for l in range(3):
+                for b in range(nbf):
+                    t1 = time.perf_counter()
+                    sph.sph_pack_host_fission(host.store, host.tasks, l, b,
+                                              host.host_in[0][0].ctypes.data, fv)
+                    t2 = time.perf_counter()
+                    sph.sph_unpack_host_fission(host.store, host.tasks, l, b,
+                                                host.host_out[0][0].ctypes.data, fv)
+                    tu += time.perf_counter() - t2
+                    tp += t2 - t1
+            fission[name] = {"pack_ms": 1e3 * tp, "unpack_ms": 1e3 * tu}
+        base_ms = fission["none"]["pack_ms"] + fission["none"]["unpack_ms"]
+        for v in fission.values():
+            v["relative_to_none"] = (v["pack_ms"] + v["unpack_ms"]) / base_ms
+        out[lname] = {"ms_per_step": 1e3 * step_s, "loops": loops,
+                      "loop_fission": {"bundles_per_loop": nbf, "variants": fission}}
     if host is not None:
         host.close()
     return {"bundle_max_slots": bundle_slots, "threads": cpu_cores(),
             "h2d_link": "pinned host memory, cudaMemcpyAsync on 2 streams", "layouts": out}
+
+
+def layout_phase_study(per_layout: dict, convert_ms: dict, base: str) -> dict:
+    """Kernel-dependent layouts (one layout per algorithmic phase): per
+    pipeline, the fixed layout with the least pack + unpack time over the
+    three loops against the best layout of each loop plus the conversions
+    between consecutive phases (density -> gradient -> force -> density).  A
+    conversion X -> Y is estimated from the measured X -> base and
+    base -> Y conversions (each a full store pass) as their mean."""
+    out = {"convert_ms": {k: {"to_base": v[0], "from_base": v[1]} for k, v in convert_ms.items()}}
+
+    def conv(a, b):
+        if a == b:
+            return 0.0
+        ta = 0.0 if a == base else convert_ms[a][0]
+        tb = 0.0 if b == base else convert_ms[b][1]
+        return 0.5 * (ta + tb) if a != base and b != base else ta + tb
+    pipelines = next(iter(per_layout.values())).keys()
+    for pl in pipelines:
+        pu = {l: [v[pl]["loops"][n]["pack_ms"] + v[pl]["loops"][n]["unpack_ms"]
+                  for n in LOOP_NAMES] for l, v in per_layout.items()}
+        fixed = min(pu, key=lambda l: sum(pu[l]))
+        best = [min(pu, key=lambda l: pu[l][k]) for k in range(3)]
+        phase = sum(pu[best[k]][k] for k in range(3)) + sum(
+            conv(best[k], best[(k + 1) % 3]) for k in range(3))
+        out[pl] = {"fixed_best": {"layout": fixed, "pack_unpack_ms": sum(pu[fixed])},
+                   "best_per_loop": {LOOP_NAMES[k]: {"layout": best[k], "pack_unpack_ms": pu[best[k]][k]}
+                                     for k in range(3)},
+                   "phase_dependent_ms": phase}
+    return out
 
 
 def plan_candidates(f, leaf_max: int = 128) -> dict:
@@ -707,6 +758,20 @@ def run_ours(args, ws, rank, local):
             res["list_build_ms"] = st[("list", 0)] / args.steps
         return res
 
+    convert_ms = {}
+
+    def time_convert(dst, src, reps=3):
+        sph.sph_store_convert(dst.store, src.store, dst.stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            sph.sph_store_convert(dst.store, src.store, dst.stream)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
     for lname in args.layouts:
         off = base if lname == args.layouts[0] else Offload(
             f, layout=lname, share=base)
@@ -722,6 +787,8 @@ def run_ours(args, ws, rank, local):
             per_layout[lname][pipeline] = loop_stats(st, total_ms / args.steps, pipeline)
             if is_head:
                 head = (off, total_ms, timer, cl, st, cnt)
+        if off is not base:
+            convert_ms[lname] = (time_convert(off, base), time_convert(base, off))
         if head is None or head[0] is not off:
             if off is not base:
                 off.close()
@@ -729,6 +796,7 @@ def run_ours(args, ws, rank, local):
                 torch.cuda.empty_cache()
     off, total_ms, timer, cl, st, cnt = head
     ms_step = total_ms / args.steps
+    kernel_dependent = layout_phase_study(per_layout, convert_ms, args.layouts[0])
     value = sum(pairs) * ws / (ms_step * 1e-3)
     graph = None
     if args.head_pipeline in ("batched", "list"):
@@ -860,6 +928,7 @@ def run_ours(args, ws, rank, local):
         "autotune": tuning,
         "host_staged": staged,
         "precision": precision,
+        "kernel_dependent_layout": kernel_dependent,
         "cosmology": cosmo,
         "adjoint": adj,
     }

@@ -51,7 +51,13 @@ enum sph_layout {
     SPH_SAOS_PACK_FORCE_TYPE = 6,  /* pack-force split by type */
     SPH_SAOS_PACK_SHARED_TYPE = 7, /* pack-shared split by type */
     SPH_SOA = 8,                   /* one array per field component */
-    SPH_NUM_LAYOUTS = 9
+    SPH_SAOS_PACK_FORCE_REPL = 9,  /* pack-force plus the density view
+                                      {x, v, m, h} stored again on its own
+                                      (replicated positions, Sec. 6): the
+                                      density pack reads only that copy */
+    SPH_SAOS_FUSED = 10,           /* fused views: each loop's inputs with the
+                                      outputs its unpack writes, in phase order */
+    SPH_NUM_LAYOUTS = 11
 };
 
 /* Interaction loops of Sec. 2.1. */
@@ -156,6 +162,13 @@ int sph_store_import(sph_store s, const sph_fields *dev_src,
                      const int64_t *dev_perm, void *stream);
 int sph_store_export(sph_store s, const sph_fields *dev_dst,
                      const int64_t *dev_perm, void *stream);
+
+/* Layout conversion between two device stores of the same particles (same
+ * count and order): every field of dst, every copy of a replicated one, from
+ * src; the ballast bytes too.  One kernel pass.  This is the step a
+ * kernel-dependent layout (one layout per algorithmic phase, Sec. 4) pays
+ * between phases. */
+int sph_store_convert(sph_store dst, sph_store src, void *stream);
 
 /* ---- cells, tasks, bundles (Sec. 2.2-2.3) ------------------------------
  * Host-side builder.  Cells: a uniform grid with edges >= H_max =
@@ -279,6 +292,23 @@ int sph_pack_host(sph_store s, sph_tasks t, int loop, int bundle, void *host_buf
                   int nthreads);
 int sph_unpack_host(sph_store s, sph_tasks t, int loop, int bundle,
                     const void *host_buf_out, int nthreads);
+/* Loop-fission variants of the host pack and unpack (Sec. 3.3): the same
+ * bytes as sph_pack_host / sph_unpack_host, with the innermost loop split
+ * by store substruct, by field component, by data type, or by substruct and
+ * type (SPH_FISSION_NONE: one loop over all components).  The copies use one
+ * generic body over component descriptors in every variant, so that only
+ * the loop structure differs between them. */
+enum sph_fission {
+    SPH_FISSION_NONE = 0,
+    SPH_FISSION_BY_STRUCT = 1,
+    SPH_FISSION_BY_ELEMENT = 2,
+    SPH_FISSION_BY_TYPE = 3,
+    SPH_FISSION_BY_STRUCT_AND_TYPE = 4
+};
+int sph_pack_host_fission(sph_store s, sph_tasks t, int loop, int bundle, void *host_buf_in,
+                          int fission, int nthreads);
+int sph_unpack_host_fission(sph_store s, sph_tasks t, int loop, int bundle,
+                            const void *host_buf_out, int fission, int nthreads);
 int sph_init_host(sph_store s, int loop, const sph_params *p, int nthreads);
 int sph_ghost_host(sph_store s, int after_loop, const sph_params *p, int nthreads);
 

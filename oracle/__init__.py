@@ -35,7 +35,8 @@ BALSARA_EPS = 1e-4
 
 DENSITY, GRADIENT, FORCE = 0, 1, 2
 LAYOUTS = ("aos", "aos_random", "pack_grad", "pack_force", "pack_shared",
-           "pack_grad_type", "pack_force_type", "pack_shared_type", "soa")
+           "pack_grad_type", "pack_force_type", "pack_shared_type", "soa",
+           "pack_force_repl", "fused")
 FIELD_NAMES = ("x", "v", "a", "mass", "h", "u", "u_dt", "rho", "time_bin",
                "alpha_visc", "alpha_diff", "rho_dh", "wcount", "wcount_dh",
                "div_v", "rot_v", "f_gradh", "pressure", "soundspeed", "balsara",

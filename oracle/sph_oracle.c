@@ -674,7 +674,8 @@ static const int FIELD_CLASS[F_NUM] = {0, 1, 1, 1, 1, 1, 1, 1, 2, 1, 1, 1, 1, 1,
 
 enum {
     L_AOS, L_AOS_RANDOM, L_PACK_GRAD, L_PACK_FORCE, L_PACK_SHARED,
-    L_PACK_GRAD_TYPE, L_PACK_FORCE_TYPE, L_PACK_SHARED_TYPE, L_SOA, L_NUM
+    L_PACK_GRAD_TYPE, L_PACK_FORCE_TYPE, L_PACK_SHARED_TYPE, L_SOA,
+    L_PACK_FORCE_REPL, L_FUSED, L_NUM
 };
 
 #define MAXG 64
@@ -732,6 +733,14 @@ static int build_layout(int layout, uint64_t seed, layout_def *L)
     static const int grad_out[] = {F_VSIGG, F_LAPU};
     static const int force_out[] = {F_A, F_UDT, F_HDT, F_VSIG};
     static const int rest[] = {F_PRES, F_CS, F_ID, F_BALLAST};
+    /* replication (Sec. 6 outlook): the density view's inputs stored again */
+    static const int dens_view[] = {F_X, F_V, F_MASS, F_H};
+    /* fused views: each loop's inputs with the outputs its unpack writes */
+    static const int fused_dens[] = {F_X, F_V, F_MASS, F_H, F_RHO, F_RHODH, F_WCOUNT,
+                                     F_WCOUNTDH, F_DIVV, F_ROTV};
+    static const int fused_grad[] = {F_U, F_VSIGG, F_LAPU};
+    static const int fused_force[] = {F_TBIN, F_FGRADH, F_BALS, F_AVISC, F_ADIFF, F_A,
+                                      F_UDT, F_HDT, F_VSIG};
     memset(L, 0, sizeof(*L));
     int by_type = layout == L_PACK_GRAD_TYPE || layout == L_PACK_FORCE_TYPE ||
                   layout == L_PACK_SHARED_TYPE;
@@ -773,6 +782,20 @@ static int build_layout(int layout, uint64_t seed, layout_def *L)
         add_group_typed(L, grad_out, 2, by_type);
         add_group_typed(L, force_out, 4, by_type);
         add_group_typed(L, rest, 4, by_type);
+        break;
+    case L_PACK_FORCE_REPL:
+        add_group(L, dens_view, 4);
+        add_group(L, force_view, 11);
+        add_group(L, dens_out, 5);
+        add_group(L, grad_out, 2);
+        add_group(L, force_out, 4);
+        add_group(L, rest, 4);
+        break;
+    case L_FUSED:
+        add_group(L, fused_dens, 10);
+        add_group(L, fused_grad, 3);
+        add_group(L, fused_force, 9);
+        add_group(L, rest, 4);
         break;
     case L_SOA:
         for (int k = 0; k < F_NUM; ++k) {

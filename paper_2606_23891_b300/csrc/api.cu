@@ -92,6 +92,13 @@ static CompPtr at(sph_store s, int field, int comp) {
     return c;
 }
 
+// The copy of (field, comp) that the pack of `loop` reads.
+static CompPtr at_view(sph_store s, int field, int comp, int loop) {
+    CompPtr c{nullptr, 0};
+    locate_view(s->layout, s->mem, field, comp, loop, &c);
+    return c;
+}
+
 static void lanes(int loop, int in_or_out, int64_t S, char *buf, char **out, int *nl) {
     int64_t off[16];
     int64_t sz[16];
@@ -280,13 +287,42 @@ static int copy_fields(sph_store s, const sph_fields *f, const int64_t *perm, vo
         if (!p) continue;
         const int elem = kFields[fid].elem, cnt = kFields[fid].count;
         for (int c = 0; c < cnt; ++c) {
-            CompPtr dst = at(s, fid, c);
-            k_copy_field<<<grid_for(s->n, 256), 256, 0, st>>>(p, elem * cnt, c * elem, elem, dst,
-                                                              perm, s->n, to_store);
-            if (int rc = launch_check("copy field")) return rc;
+            // into the store: every copy of a replicated field; out: the first
+            CompPtr dst[4];
+            const int ncopy = to_store ? locate_all(s->layout, s->mem, fid, c, dst, 4)
+                                       : (int)locate(s->layout, s->mem, fid, c, dst);
+            for (int k = 0; k < ncopy; ++k) {
+                k_copy_field<<<grid_for(s->n, 256), 256, 0, st>>>(p, elem * cnt, c * elem, elem,
+                                                                  dst[k], perm, s->n, to_store);
+                if (int rc = launch_check("copy field")) return rc;
+            }
         }
     }
     return SPH_OK;
+}
+
+int sph_store_convert(sph_store dst, sph_store src, void *stream) {
+    if (int rc = check_store(dst)) return rc;
+    if (int rc = check_store(src)) return rc;
+    if (dst->n != src->n) return fail(SPH_EINVAL, "stores differ in particle count");
+    if (dst == src) return SPH_OK;
+    ConvArgs a{};
+    for (int fid = 0; fid < F_NUM; ++fid) {
+        const int elem = kFields[fid].elem, cnt = kFields[fid].count;
+        for (int c = 0; c < cnt; ++c) {
+            CompPtr from{nullptr, 0}, to[4];
+            if (!locate(src->layout, src->mem, fid, c, &from)) continue;
+            const int nto = locate_all(dst->layout, dst->mem, fid, c, to, 4);
+            for (int k = 0; k < nto; ++k) {
+                if (a.ncomp == (int)(sizeof(a.c) / sizeof(a.c[0])))
+                    return fail(SPH_EUNSUPPORTED, "layout has too many components to convert");
+                a.c[a.ncomp++] = ConvComp{to[k], from, elem};
+            }
+        }
+    }
+    if (src->n == 0) return SPH_OK;
+    k_convert<<<grid_for(src->n, 256), 256, 0, (cudaStream_t)stream>>>(a, src->n);
+    return launch_check("store convert");
 }
 
 int sph_store_import(sph_store s, const sph_fields *dev_src, const int64_t *dev_perm,
@@ -450,7 +486,7 @@ int sph_pack(sph_store s, sph_tasks t, int loop, int bundle, void *dev_buf_in, v
                                  {F_V, 2}, {F_MASS, 0}, {F_H, 0}, {F_U, 0}, {F_RHO, 0},
                                  {F_FGRADH, 0}, {F_BALS, 0}, {F_AVISC, 0}, {F_ADIFF, 0},
                                  {F_TBIN, 0}};
-    for (int r = 0; r < R_NUM; ++r) a.src[r] = at(s, roles[r][0], roles[r][1]);
+    for (int r = 0; r < R_NUM; ++r) a.src[r] = at_view(s, roles[r][0], roles[r][1], loop);
     for (int d = 0; d < 3; ++d) a.box[d] = t->box[d];
     cudaStream_t st = (cudaStream_t)stream;
     if (nt == 0) return SPH_OK;
@@ -717,6 +753,27 @@ int sph_unpack_host(sph_store s, sph_tasks t, int loop, int bundle, const void *
     return host_unpack(s, t, loop, bundle, (const char *)host_buf_out, nthreads);
 }
 
+int sph_pack_host_fission(sph_store s, sph_tasks t, int loop, int bundle, void *host_buf_in,
+                          int fission, int nthreads) {
+    if (int rc = check_host_bundle(s, t, loop, bundle)) return rc;
+    if (fission < SPH_FISSION_NONE || fission > SPH_FISSION_BY_STRUCT_AND_TYPE)
+        return fail(SPH_EINVAL, "unknown loop-fission variant %d", fission);
+    if (!host_buf_in || !aligned256(host_buf_in))
+        return fail(SPH_EINVAL, "pack buffer must be a 256-byte aligned host pointer");
+    return host_pack_fission(s, t, loop, bundle, (char *)host_buf_in, fission, nthreads);
+}
+
+int sph_unpack_host_fission(sph_store s, sph_tasks t, int loop, int bundle,
+                            const void *host_buf_out, int fission, int nthreads) {
+    if (int rc = check_host_bundle(s, t, loop, bundle)) return rc;
+    if (fission < SPH_FISSION_NONE || fission > SPH_FISSION_BY_STRUCT_AND_TYPE)
+        return fail(SPH_EINVAL, "unknown loop-fission variant %d", fission);
+    if (!host_buf_out || !aligned256(host_buf_out))
+        return fail(SPH_EINVAL, "result buffer must be a 256-byte aligned host pointer");
+    return host_unpack_fission(s, t, loop, bundle, (const char *)host_buf_out, fission,
+                               nthreads);
+}
+
 int sph_init_host(sph_store s, int loop, const sph_params *p, int nthreads) {
     if (int rc = check_host_store(s)) return rc;
     if (int rc = check_loop(loop)) return rc;
@@ -941,7 +998,7 @@ int sph_batch_pack(sph_store s, sph_batch b, int loop, int bundle, void *dev_buf
                                  {F_V, 2}, {F_MASS, 0}, {F_H, 0}, {F_U, 0}, {F_RHO, 0},
                                  {F_FGRADH, 0}, {F_BALS, 0}, {F_AVISC, 0}, {F_ADIFF, 0},
                                  {F_TBIN, 0}};
-    for (int r = 0; r < R_NUM; ++r) a.src[r] = at(s, roles[r][0], roles[r][1]);
+    for (int r = 0; r < R_NUM; ++r) a.src[r] = at_view(s, roles[r][0], roles[r][1], loop);
     a.kernel_gamma = (float)p->kernel_gamma;
     a.gamma = (float)p->gamma;
     double bmax = b->box[0] > b->box[1] ? b->box[0] : b->box[1];

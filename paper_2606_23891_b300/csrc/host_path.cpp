@@ -32,6 +32,13 @@ CompPtr at(sph_store s, int field, int comp) {
     return c;
 }
 
+// The copy of (field, comp) that the pack of `loop` reads.
+CompPtr at_view(sph_store s, int field, int comp, int loop) {
+    CompPtr c{nullptr, 0};
+    locate_view(s->layout, s->mem, field, comp, loop, &c);
+    return c;
+}
+
 int threads(int n) { return n > 0 ? n : omp_get_max_threads(); }
 
 // Kahan step, plain FP32 adds (no multiplies: nothing to contract).
@@ -54,11 +61,12 @@ int host_pack(sph_store s, sph_tasks t, int loop, int b, char *buf, int nthreads
     lane_offsets(loop, 0, t->bundle_slots[b], off);
     char *lane[16];
     for (int k = 0; k < 12; ++k) lane[k] = buf + off[k];
-    CompPtr x[3] = {at(s, F_X, 0), at(s, F_X, 1), at(s, F_X, 2)};
-    CompPtr v[3] = {at(s, F_V, 0), at(s, F_V, 1), at(s, F_V, 2)};
-    CompPtr m = at(s, F_MASS, 0), h = at(s, F_H, 0), u = at(s, F_U, 0), rho = at(s, F_RHO, 0);
-    CompPtr fgh = at(s, F_FGRADH, 0), bal = at(s, F_BALS, 0), av = at(s, F_AVISC, 0),
-            ad = at(s, F_ADIFF, 0), tb = at(s, F_TBIN, 0);
+    auto av_ = [&](int f, int c) { return at_view(s, f, c, loop); };
+    CompPtr x[3] = {av_(F_X, 0), av_(F_X, 1), av_(F_X, 2)};
+    CompPtr v[3] = {av_(F_V, 0), av_(F_V, 1), av_(F_V, 2)};
+    CompPtr m = av_(F_MASS, 0), h = av_(F_H, 0), u = av_(F_U, 0), rho = av_(F_RHO, 0);
+    CompPtr fgh = av_(F_FGRADH, 0), bal = av_(F_BALS, 0), av = av_(F_AVISC, 0),
+            ad = av_(F_ADIFF, 0), tb = av_(F_TBIN, 0);
     const double *box = t->box;
 #pragma omp parallel for schedule(static) num_threads(threads(nthreads))
     for (int64_t ti = t0; ti < t1; ++ti) {
@@ -247,14 +255,20 @@ int host_copy_fields(sph_store s, const sph_fields *f, const int64_t *perm, int 
         if (!lp0) continue;
         const int elem = kFields[fid].elem, cnt = kFields[fid].count;
         for (int c = 0; c < cnt; ++c) {
-            const CompPtr sp = at(s, fid, c);
+            // into the store: every copy of a replicated field; out: the first
+            CompPtr cp[4];
+            const int ncopy = to_store ? locate_all(s->layout, s->mem, fid, c, cp, 4)
+                                       : (int)locate(s->layout, s->mem, fid, c, cp);
+            for (int q = 0; q < ncopy; ++q) {
+                const CompPtr sp = cp[q];
 #pragma omp parallel for schedule(static) num_threads(threads(nthreads))
-            for (int64_t k = 0; k < s->n; ++k) {
-                const int64_t p = perm ? perm[k] : k;
-                char *lp = lp0 + p * (int64_t)(elem * cnt) + c * elem;
-                char *st = sp.ptr + k * sp.stride;
-                if (to_store) memcpy(st, lp, elem);
-                else memcpy(lp, st, elem);
+                for (int64_t k = 0; k < s->n; ++k) {
+                    const int64_t p = perm ? perm[k] : k;
+                    char *lp = lp0 + p * (int64_t)(elem * cnt) + c * elem;
+                    char *st = sp.ptr + k * sp.stride;
+                    if (to_store) memcpy(st, lp, elem);
+                    else memcpy(lp, st, elem);
+                }
             }
         }
     }

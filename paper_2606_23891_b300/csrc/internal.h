@@ -44,6 +44,7 @@ struct Layout {
     int id = -1;
     uint64_t seed = 0;
     std::vector<Group> groups;
+    int view_group[3] = {-1, -1, -1};  // group each loop's pack reads first
 };
 
 // Layout engine (layout.cpp).
@@ -56,6 +57,12 @@ struct CompPtr {
     long long stride;
 };
 bool locate(const Layout &L, char *mem, int field, int comp, CompPtr *out);
+// Every copy of (field, comp) (replicated layouts hold some inputs twice);
+// returns the number found (at most max).
+int locate_all(const Layout &L, char *mem, int field, int comp, CompPtr *out, int max);
+// The copy a loop's pack reads: the one in the loop's view group when the
+// layout names one and it holds the field, else the first.
+bool locate_view(const Layout &L, char *mem, int field, int comp, int loop, CompPtr *out);
 
 // Error reporting (api.cu).
 int fail(int status, const char *fmt, ...);
@@ -169,6 +176,10 @@ int build_tasks(int64_t n, const double *x, const float *h,
 int host_pack(sph_store s, sph_tasks t, int loop, int b, char *buf, int nthreads);
 int host_unpack(sph_store s, sph_tasks t, int loop, int b, const char *buf, int nthreads);
 int host_init(sph_store s, int loop, int active_bin, int nthreads);
+int host_pack_fission(sph_store s, sph_tasks t, int loop, int b, char *buf, int fission,
+                      int nthreads);
+int host_unpack_fission(sph_store s, sph_tasks t, int loop, int b, const char *buf, int fission,
+                        int nthreads);
 int host_ghost(sph_store s, float kernel_gamma, float gamma, float balsara_eps, int nthreads);
 int host_copy_fields(sph_store s, const sph_fields *f, const int64_t *perm, int to_store,
                      int nthreads);

@@ -57,6 +57,14 @@ const std::vector<int> kDensOut = {F_RHODH, F_WCOUNT, F_WCOUNTDH, F_DIVV,
 const std::vector<int> kGradOut = {F_VSIGG, F_LAPU};
 const std::vector<int> kForceOut = {F_A, F_UDT, F_HDT, F_VSIG};
 const std::vector<int> kRest = {F_PRES, F_CS, F_ID, F_BALLAST};
+// replication: the density view's inputs stored again on their own
+const std::vector<int> kDensView = {F_X, F_V, F_MASS, F_H};
+// fused views: each loop's inputs with the outputs its unpack writes
+const std::vector<int> kFusedDens = {F_X, F_V, F_MASS, F_H, F_RHO, F_RHODH, F_WCOUNT,
+                                     F_WCOUNTDH, F_DIVV, F_ROTV};
+const std::vector<int> kFusedGrad = {F_U, F_VSIGG, F_LAPU};
+const std::vector<int> kFusedForce = {F_TBIN, F_FGRADH, F_BALS, F_AVISC, F_ADIFF, F_A,
+                                      F_UDT, F_HDT, F_VSIG};
 
 // SplitMix64 step (Steele, Lea, Flood 2014).
 uint64_t splitmix64_next(uint64_t &s) {
@@ -140,6 +148,16 @@ int build_layout(int layout, uint64_t seed, int64_t n, Layout *out) {
                               &kGradOut, &kForceOut, &kRest})
             push_split(L, *v, typed);
         break;
+    case SPH_SAOS_PACK_FORCE_REPL:
+        for (const auto *v : {&kDensView, &kForceView, &kDensOut, &kGradOut, &kForceOut, &kRest})
+            push(L, *v);
+        L.view_group[SPH_DENSITY] = 0;
+        L.view_group[SPH_GRADIENT] = 1;
+        L.view_group[SPH_FORCE] = 1;
+        break;
+    case SPH_SAOS_FUSED:
+        for (const auto *v : {&kFusedDens, &kFusedGrad, &kFusedForce, &kRest}) push(L, *v);
+        break;
     case SPH_SOA:
         for (int f : kUseOrder) {
             if (f == F_BALLAST || kFields[f].count == 1) {
@@ -184,6 +202,33 @@ bool locate(const Layout &L, char *mem, int field, int comp, CompPtr *out) {
         }
     }
     return false;
+}
+
+static bool member_ptr(const Layout &L, const Group &g, char *mem, int field, int comp,
+                       CompPtr *out) {
+    for (const Member &m : g.mem) {
+        if (m.field != field) continue;
+        if (m.comp >= 0 && m.comp != comp) continue;
+        int extra = m.comp >= 0 ? 0 : comp * kFields[field].elem;
+        out->ptr = mem + g.base + m.offset + extra;
+        out->stride = g.record;
+        return true;
+    }
+    return false;
+}
+
+int locate_all(const Layout &L, char *mem, int field, int comp, CompPtr *out, int max) {
+    int k = 0;
+    for (const Group &g : L.groups)
+        if (k < max && member_ptr(L, g, mem, field, comp, &out[k])) ++k;
+    return k;
+}
+
+bool locate_view(const Layout &L, char *mem, int field, int comp, int loop, CompPtr *out) {
+    if (loop >= 0 && loop < 3 && L.view_group[loop] >= 0 &&
+        member_ptr(L, L.groups[L.view_group[loop]], mem, field, comp, out))
+        return true;
+    return locate(L, mem, field, comp, out);
 }
 
 int lane_sizes(int loop, int in_or_out, int64_t *sz) {

@@ -31,6 +31,32 @@ __global__ void k_copy_field(const char *logical, int lbytes_per_particle,
     }
 }
 
+// Store-to-store layout conversion: every component of every field (every
+// copy of a replicated one) of the destination from the source's first copy.
+struct ConvComp {
+    CompPtr dst, src;
+    int bytes;
+};
+struct ConvArgs {
+    int ncomp;
+    ConvComp c[56];
+};
+
+__global__ void k_convert(ConvArgs a, long long n) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        for (int q = 0; q < a.ncomp; ++q) {
+            const char *sp = a.c[q].src.ptr + k * a.c[q].src.stride;
+            char *dp = a.c[q].dst.ptr + k * a.c[q].dst.stride;
+            const int b = a.c[q].bytes;
+            if (b == 8) *(unsigned long long *)dp = *(const unsigned long long *)sp;
+            else if (b == 4) *(unsigned int *)dp = *(const unsigned int *)sp;
+            else
+                for (int t = 0; t < b; ++t) dp[t] = sp[t];
+        }
+    }
+}
+
 // Zero up to 8 float outputs; with `tb` set only particles with
 // time_bin <= active_bin are touched (force loop).
 struct InitArgs {

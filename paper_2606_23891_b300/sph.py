@@ -16,10 +16,10 @@ LIB_PATH = os.path.join(_HERE, "libsph.so")
 
 SPH_AOS, SPH_AOS_RANDOM, SPH_SAOS_PACK_GRAD, SPH_SAOS_PACK_FORCE, \
     SPH_SAOS_PACK_SHARED, SPH_SAOS_PACK_GRAD_TYPE, SPH_SAOS_PACK_FORCE_TYPE, \
-    SPH_SAOS_PACK_SHARED_TYPE, SPH_SOA = range(9)
+    SPH_SAOS_PACK_SHARED_TYPE, SPH_SOA, SPH_SAOS_PACK_FORCE_REPL, SPH_SAOS_FUSED = range(11)
 LAYOUTS = {"aos": 0, "aos_random": 1, "pack_grad": 2, "pack_force": 3,
            "pack_shared": 4, "pack_grad_type": 5, "pack_force_type": 6,
-           "pack_shared_type": 7, "soa": 8}
+           "pack_shared_type": 7, "soa": 8, "pack_force_repl": 9, "fused": 10}
 SPH_DENSITY, SPH_GRADIENT, SPH_FORCE = 0, 1, 2
 LOOPS = {"density": 0, "gradient": 1, "force": 2}
 STATUS = {0: "SPH_OK", 1: "SPH_EINVAL", 2: "SPH_ENOMEM", 3: "SPH_ECUDA",
@@ -101,6 +101,9 @@ def lib() -> C.CDLL:
         "sph_store_destroy": (i, [p]),
         "sph_store_import": (i, [p, p, p, p]),
         "sph_store_export": (i, [p, p, p, p]),
+        "sph_store_convert": (i, [p, p, p]),
+        "sph_pack_host_fission": (i, [p, p, i, i, p, i, i]),
+        "sph_unpack_host_fission": (i, [p, p, i, i, p, i, i]),
         "sph_tasks_build": (i, [i64, p, p, p, p, p]),
         "sph_tasks_upload": (i, [p]),
         "sph_tasks_info": (i, [p, p]),
@@ -203,6 +206,23 @@ def sph_store_import(s, fields: Fields, dev_perm: int, stream: int = 0) -> None:
 
 def sph_store_export(s, fields: Fields, dev_perm: int, stream: int = 0) -> None:
     _ok(lib().sph_store_export(s, C.byref(fields), dev_perm, stream))
+
+
+FISSION = {"none": 0, "by_struct": 1, "by_element": 2, "by_type": 3, "by_struct_and_type": 4}
+
+
+def sph_pack_host_fission(s, t, loop: int, bundle: int, host_buf: int, fission: int,
+                          nthreads: int = 0) -> None:
+    _ok(lib().sph_pack_host_fission(s, t, loop, bundle, host_buf, fission, nthreads))
+
+
+def sph_unpack_host_fission(s, t, loop: int, bundle: int, host_buf: int, fission: int,
+                            nthreads: int = 0) -> None:
+    _ok(lib().sph_unpack_host_fission(s, t, loop, bundle, host_buf, fission, nthreads))
+
+
+def sph_store_convert(dst, src, stream: int = 0) -> None:
+    _ok(lib().sph_store_convert(dst, src, stream))
 
 
 def sph_tasks_build(n: int, host_x: int, host_h: int, gp: GridParams,

@@ -46,7 +46,7 @@ def test_binding_structs_match_the_header():
     assert C.sizeof(sph.Params) == 40 and C.sizeof(sph.GridParams) == 56
 
 
-@pytest.mark.parametrize("layout", range(9))
+@pytest.mark.parametrize("layout", range(11))
 @pytest.mark.parametrize("seed", [0, 17])
 def test_layout_engine_matches_the_oracle(layout, seed):
     assert sph.sph_layout_group_count(layout, seed) == \

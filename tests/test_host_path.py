@@ -43,7 +43,7 @@ def lane_slices(loop, S):
     return out
 
 
-@pytest.mark.parametrize("layout", range(9))
+@pytest.mark.parametrize("layout", range(11))
 def test_host_store_image_and_round_trip(layout):
     f = fields(3)
     off = HostOffload(f, layout=layout, gpu=False)
@@ -119,3 +119,43 @@ def test_host_init_and_ghost_follow_the_oracle():
     for col, k in ((0, "rho"), (8, "f_gradh"), (9, "pressure"), (10, "soundspeed")):
         np.testing.assert_allclose(got[k], ref[:, col], rtol=2e-6)
     np.testing.assert_allclose(got["balsara"], ref[:, 11], atol=1e-5)
+
+
+@pytest.mark.parametrize("fission", range(5))
+@pytest.mark.parametrize("layout", [0, 6, 8, 9, 10])
+def test_loop_fission_variants_write_the_same_bytes(layout, fission):
+    """Every loop-fission variant of the host pack gives the default pack's
+    buffer, and every variant of the unpack its store (Sec. 3.3)."""
+    f = fields(11)
+    off = HostOffload(f, layout=layout, bundle_max_slots=5000, gpu=False)
+    off.import_fields(f, ALL_FIELDS)
+    ci, cj, sh, cs, bs = off.task_list()
+    buf = off.host_in[0][0]
+    ref = np.empty_like(buf)
+    for loop in range(3):
+        for b in range(len(bs) - 1):
+            buf[:] = 0
+            sph.sph_pack_host(off.store, off.tasks, loop, b, buf.ctypes.data)
+            ref[:] = buf
+            buf[:] = 0
+            sph.sph_pack_host_fission(off.store, off.tasks, loop, b, buf.ctypes.data, fission)
+            np.testing.assert_array_equal(buf, ref)
+    a = HostOffload(f, layout=layout, bundle_max_slots=5000, gpu=False)
+    a.import_fields(f, ALL_FIELDS)
+    out = off.host_out[0][0]
+    for loop in range(3):
+        for b in range(len(bs) - 1):
+            S = oracle.bundle_slots(ci, cj, cs, bs[b], bs[b + 1])
+            lanes = ics.random_result_lanes(oracle.buffer_bytes(loop, 1, S), seed=300 + b)
+            out[: len(lanes)] = lanes
+            sph.sph_unpack_host(a.store, a.tasks, loop, b, out.ctypes.data)
+            sph.sph_unpack_host_fission(off.store, off.tasks, loop, b, out.ctypes.data, fission)
+    np.testing.assert_array_equal(off.store_bytes(), a.store_bytes())
+
+
+def test_loop_fission_rejects_unknown_variants():
+    f = fields(12)
+    off = HostOffload(f, layout=0, gpu=False)
+    buf = off.host_in[0][0]
+    with pytest.raises(sph.SphError):
+        sph.sph_pack_host_fission(off.store, off.tasks, 0, 0, buf.ctypes.data, 5)

@@ -550,7 +550,7 @@ def _ctype(fid, comp):
     return _CT.get(fid, C.c_float)
 
 
-@pytest.mark.parametrize("layout", range(9))
+@pytest.mark.parametrize("layout", range(11))
 def test_layout_records_match_c_struct_rules(layout):
     groups = oracle.layout_groups(layout, seed=7)
     seen = []
@@ -561,7 +561,8 @@ def test_layout_records_match_c_struct_rules(layout):
         for k, (fid, comp, off) in enumerate(mem):
             assert getattr(S, "m%d" % k).offset == off
             seen.append((fid, comp))
-    # every field (or every component, for SoA) is stored exactly once
+    # every field (or every component, for SoA) is stored exactly once, except
+    # the density view's inputs in the replicated layout, stored twice
     names = oracle.FIELD_NAMES
     want = []
     for fid, name in enumerate(names):
@@ -569,6 +570,8 @@ def test_layout_records_match_c_struct_rules(layout):
         if layout == 8 and ncomp == 3:
             want += [(fid, c) for c in range(3)]
         else:
+            want.append((fid, -1))
+        if layout == 9 and name in ("x", "v", "mass", "h"):
             want.append((fid, -1))
     assert sorted(seen) == sorted(want)
 
@@ -592,7 +595,7 @@ def test_random_order_layout_is_a_seeded_shuffle():
     assert a == [fid for fid, _, _ in oracle.layout_groups(1, seed=3)[0][1]]
 
 
-@pytest.mark.parametrize("layout", range(9))
+@pytest.mark.parametrize("layout", range(11))
 def test_store_encoding_reads_back_through_numpy(layout):
     f = ics.perturb(ics.uniform_lattice(n_side=5, jitter=0.3), seed=1, v_amp=1.0)
     rng = np.random.Generator(np.random.PCG64(2))
