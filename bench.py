@@ -50,14 +50,21 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 # DRAM bytes per slot of the interaction kernels from an ncu capture of a
 # smaller case (traffic grows with the slots a launch processes), valid only
 # for the kernel source with this digest (else reported as null)
-NCU_TRAFFIC = {("plain", "kernel", 2): {"bytes_per_unit": 92.1, "src": "e4b699e728bdf76e"}}
+NCU_TRAFFIC = {
+    # DRAM bytes per unit (slot for the per-task kernels, particle otherwise)
+    # from one ncu capture, valid while the kernel's source file is unchanged
+    ("plain", "kernel", 2): {"bytes_per_unit": 92.1, "src": "e4b699e728bdf76e",
+                             "file": "physics_kernels.cuh"},
+    ("list", "list", 0): {"bytes_per_unit": 494.5, "src": "df216f4110881d76",
+                          "file": "list_kernels.cuh"},
+}
 # bytes per particle of the batched pack records (nf float4 + index lanes)
 BATCH_REC = (3 * 16 + 4, 4 * 16 + 4, 5 * 16 + 9)
-GPU_KERNEL_SRC = os.path.join(ROOT, "paper_2606_23891_b300", "csrc", "physics_kernels.cuh")
+CSRC = os.path.join(ROOT, "paper_2606_23891_b300", "csrc")
 
 
-def src_digest() -> str:
-    with open(GPU_KERNEL_SRC, "rb") as fh:
+def src_digest(name: str = "physics_kernels.cuh") -> str:
+    with open(os.path.join(CSRC, name), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
@@ -829,9 +836,14 @@ def run_ours(args, ws, rank, local):
         dur = st[top] / (args.steps * per_step)
         flops = (ncand * FLOPS_CANDIDATE + pairs[2] * FLOPS_EXACT) / per_step
         achieved = flops / (dur * 1e-3) / 1e12
+        tr = NCU_TRAFFIC.get(("list", "list", 0))
+        traffic = (tr["bytes_per_unit"] * n / per_step
+                   if tr and tr["src"] == src_digest(tr["file"]) else None)
         roof = {"kernel": "neighbour-list build", "bound": "alu",
                 "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_source": "ncu DRAM bytes of a 128^3 capture, scaled by particles",
+                "hbm_GBps": (traffic / (dur * 1e-3) / 1e9) if traffic else None,
                 "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"}
     elif stage == "kernel":
         # useful FP32 work only: accepted pairs x the pair body; the candidate
@@ -842,7 +854,7 @@ def run_ours(args, ws, rank, local):
         tr = NCU_TRAFFIC.get((args.head_pipeline, stage, loop))
         units = slots if args.head_pipeline == "plain" else n
         traffic = (tr["bytes_per_unit"] * units / per_step
-                   if tr and tr["src"] == src_digest() else None)
+                   if tr and tr["src"] == src_digest(tr["file"]) else None)
         roof = {"kernel": "%s interaction/%s" % (args.head_pipeline, LOOP_NAMES[loop]),
                 "bound": "alu",
                 "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
