@@ -618,6 +618,66 @@ def run_cosmology(args, ws, peaks):
     return res
 
 
+def run_precision_clustered(args):
+    """The precision study on the clustered recipe (lognormal, tree plan):
+    per-loop error of the mixed-precision list step and of the all-FP64
+    step against the oracle on sampled particles, and both step times."""
+    import torch
+    from paper_2606_23891_b300 import ics
+    from paper_2606_23891_b300.pipeline import Offload
+    f = ics.lognormal(n_side=args.precision_clustered_n_side)
+    off = Offload(f, layout="pack_force_type", plan="tree", leaf_max=128)
+    for _ in range(2):
+        off.list_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    off.list_step()
+    e1.record()
+    torch.cuda.synchronize()
+    mixed_ms = e0.elapsed_time(e1)
+    t = time.perf_counter()
+    oracle_sample(f, args.precision_clustered_sample, 17)
+    sel, ref = oracle_sample.last
+    t = time.perf_counter() - t
+    res = precision_study(off, f, sel, ref, 1, off.list_step)
+    res.update({"workload": "lognormal%d (tree plan)" % args.precision_clustered_n_side,
+                "mixed_ms_per_step": mixed_ms, "oracle_s": t})
+    # the same set kept in pinned host memory and staged through the plan's
+    # bundles (host pack, H2D, batched kernel, D2H, host unpack, 2 streams)
+    if args.host_steps > 0:
+        from paper_2606_23891_b300.pipeline import HostOffload
+        off.batch_step()
+        want = off.export()
+        nleaf = off.binfo["cells"]
+        off.close()
+        del off
+        torch.cuda.empty_cache()
+        host = HostOffload(f, layout="pack_force_type", plan="tree", leaf_max=128,
+                           max_target_cells=max(1, nleaf // 8))
+        host.batch_step()                              # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.host_steps):
+            host.batch_step()
+        torch.cuda.synchronize()
+        ms = 1e3 * (time.perf_counter() - t0) / args.host_steps
+        got = host.export()
+        err = max(float(np.max(np.abs(got[k].astype(np.float64) - want[k])) /
+                        max(float(np.sqrt(np.mean(want[k].astype(np.float64) ** 2))), 1e-30))
+                  for k in ("rho", "a", "u_dt"))
+        res["host_staged"] = {"ms_per_step": ms, "bundles": host.info["nbundles"],
+                              "threads": cpu_cores(),
+                              "max_rms_rel_diff_vs_device": err}
+        host.close()
+    else:
+        off.close()
+        del off
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_adjoint(args, ws):
     """Differentiation workload: gradient of sum |a|^2 + sum (du/dt)^2 with
     respect to x, m, u through density -> ghost -> force, on the Gresho
@@ -908,6 +968,8 @@ def run_ours(args, ws, rank, local):
             v["pair_interactions_per_s"] = sum(pairs) / (v["ms_per_step"] * 1e-3)
     del f
     adj = run_adjoint(args, ws) if args.adjoint_n_side else None
+    prec_cl = (run_precision_clustered(args)
+               if args.precision_clustered_n_side > 0 and rank == 0 and ws == 1 else None)
     cosmo = run_cosmology(args, ws, peaks) if args.cosmo_n_side > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
@@ -940,6 +1002,7 @@ def run_ours(args, ws, rank, local):
         "autotune": tuning,
         "host_staged": staged,
         "precision": precision,
+        "precision_clustered": prec_cl,
         "kernel_dependent_layout": kernel_dependent,
         "cosmology": cosmo,
         "adjoint": adj,
@@ -972,6 +1035,9 @@ def main(argv=None):
                     default=[64, 256], help="Gresho sizes of the adjoint timing ('' skips)")
     ap.add_argument("--adjoint-fd", type=int, default=8,
                     help="particles of the central-difference check of the adjoint")
+    ap.add_argument("--precision-clustered-n-side", type=int, default=256,
+                    help="lognormal set of the clustered precision study (0: skip)")
+    ap.add_argument("--precision-clustered-sample", type=int, default=8)
     ap.add_argument("--precision-steps", type=int, default=2,
                     help="timed steps of the all-FP64 path (0: skip the precision study)")
     ap.add_argument("--pipelines", default="plain,batched,list")

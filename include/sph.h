@@ -468,6 +468,20 @@ int sph_batch_offload_loop_list(sph_store s, sph_batch b, int loop, void *dev_bu
                                 void *dev_buf_out, const void *dev_list, size_t list_bytes,
                                 const sph_params *p, void *stream);
 
+/* Host-staged batched cycle: a host store (sph_store_create_host, in the
+ * plan's particle order) and a batch plan; per bundle, host threads pack
+ * the bundle's records (its cells once each, particles of a cell in store
+ * order) into host_in[k], which goes H2D into dev_in[k] on streams[k], the
+ * batched kernel runs, the results come back D2H into host_out[k] and host
+ * threads fold each target particle's result into the store, bundles
+ * alternating between the two buffer sets.  init before, ghost after the
+ * density loop, on the host.  Buffers: sph_batch_buffer_bytes(b, loop, 0/1)
+ * bytes each (pinned host memory for the transfers to overlap). */
+int sph_batch_offload_loop_host(sph_store s, sph_batch b, int loop, void *const host_in[2],
+                                void *const host_out[2], void *const dev_in[2],
+                                void *const dev_out[2], const sph_params *p,
+                                void *const streams[2], int nthreads);
+
 /* ---- adjoint of density -> ghost -> force (differentiation) --------------
  * Gradient of L = sum_i |a_i|^2 + sum_i (du_i/dt)^2 (active particles) with
  * respect to positions, masses and internal energies, for upstream adjoints

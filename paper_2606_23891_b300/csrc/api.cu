@@ -20,6 +20,7 @@
 #include "fp64_kernels.cuh"
 #include "list_kernels.cuh"
 #include "adjoint_kernels.cuh"
+#include "host_batch.cuh"
 
 namespace sph {
 
@@ -1419,5 +1420,70 @@ int sph_batch_adjoint(sph_store s, sph_batch b, void *dev_buf_in, const void *de
         return rc;
     k_adj_scatter<<<g, 256, 0, st>>>(a);
     return launch_check("adjoint scatter");
+}
+
+// ---- host-staged batched cycle ----------------------------------------------
+int sph_batch_offload_loop_host(sph_store s, sph_batch b, int loop, void *const host_in[2],
+                                void *const host_out[2], void *const dev_in[2],
+                                void *const dev_out[2], const sph_params *p,
+                                void *const streams[2], int nthreads) {
+    if (int rc = check_host_store(s)) return rc;
+    if (!b) return fail(SPH_EINVAL, "NULL batch handle");
+    if (int rc = check_loop(loop)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (s->n != b->n) return fail(SPH_EINVAL, "store and batch disagree on particle count");
+    if (!host_in || !host_out || !dev_in || !dev_out || !streams)
+        return fail(SPH_EINVAL, "NULL buffer or stream array");
+    for (int k = 0; k < 2; ++k)
+        if (!aligned256(host_in[k]) || !aligned256(host_out[k]) || !aligned256(dev_in[k]) ||
+            !aligned256(dev_out[k]) || !host_in[k] || !host_out[k] || !dev_in[k] || !dev_out[k])
+            return fail(SPH_EINVAL, "buffers must be non-NULL and 256-byte aligned");
+    if (int rc = host_init(s, loop, p->active_bin, nthreads)) return rc;
+    const int nb = (int)b->bundles.size();
+    cudaStream_t st[2] = {(cudaStream_t)streams[0], (cudaStream_t)streams[1]};
+    cudaEvent_t done[2] = {nullptr, nullptr};
+    int rc = SPH_OK;
+    for (int k = 0; k < 2 && rc == SPH_OK; ++k)
+        rc = cuda_check(cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming), "event");
+    std::vector<int> ids;
+    for (int bi = 0; bi < nb; ++bi)
+        if (b->bundles[bi].nitems > 0) ids.push_back(bi);
+    const int nq = (int)ids.size();
+    for (int q = 0; q < nq && rc == SPH_OK; ++q) {
+        const int k = q & 1, bi = ids[q];
+        // buffers k were last used by bundle q-2, whose results were folded
+        // after its event completed in the previous iteration
+        if ((rc = host_batch_pack(s, b, loop, bi, (char *)host_in[k], p, nthreads))) break;
+        const size_t in_b = (size_t)host_batch_in_bytes(b, loop, bi);
+        const size_t out_b = (size_t)host_batch_out_bytes(b, loop, bi);
+        if ((rc = cuda_check(cudaMemcpyAsync(dev_in[k], host_in[k], in_b,
+                                             cudaMemcpyHostToDevice, st[k]), "H2D")))
+            break;
+        if ((rc = sph_batch_interact(b, loop, bi, dev_in[k], dev_out[k], p, st[k]))) break;
+        if ((rc = cuda_check(cudaMemcpyAsync(host_out[k], dev_out[k], out_b,
+                                             cudaMemcpyDeviceToHost, st[k]), "D2H")))
+            break;
+        if ((rc = cuda_check(cudaEventRecord(done[k], st[k]), "event record"))) break;
+        if (q >= 1) {
+            if ((rc = cuda_check(cudaEventSynchronize(done[k ^ 1]), "event wait"))) break;
+            if ((rc = host_batch_unpack(s, b, loop, ids[q - 1], (const char *)host_out[k ^ 1],
+                                        nthreads)))
+                break;
+        }
+    }
+    if (rc == SPH_OK && nq > 0) {
+        const int k = (nq - 1) & 1;
+        rc = cuda_check(cudaEventSynchronize(done[k]), "event wait");
+        if (rc == SPH_OK)
+            rc = host_batch_unpack(s, b, loop, ids[nq - 1], (const char *)host_out[k], nthreads);
+    }
+    if (rc != SPH_OK) {
+        cudaStreamSynchronize(st[0]);
+        cudaStreamSynchronize(st[1]);
+    }
+    for (int k = 0; k < 2; ++k)
+        if (done[k]) cudaEventDestroy(done[k]);
+    if (rc == SPH_OK && loop == SPH_DENSITY) rc = sph_ghost_host(s, SPH_DENSITY, p, nthreads);
+    return rc;
 }
 }  // extern "C"

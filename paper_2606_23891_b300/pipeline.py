@@ -405,36 +405,87 @@ class HostOffload:
 
     def __init__(self, fields: dict, layout="aos", seed: int = 0, box=(1.0, 1.0, 1.0),
                  bundle_max_slots: int = 0, ncell=(0, 0, 0),
-                 params: sph.Params | None = None, gpu: bool = True, nthreads: int = 0):
+                 params: sph.Params | None = None, gpu: bool = True, nthreads: int = 0,
+                 plan: str = "grid", leaf_max: int = 128, max_target_cells: int = 0,
+                 threads: int = 128):
+        """plan "grid": the per-task cycle's cells and tasks (and, through
+        batch_step, the batched cycle on them); plan "tree": octree leaves
+        for clustered sets, batched cycle only (needs the GPU)."""
         self.layout = sph.LAYOUTS[layout] if isinstance(layout, str) else int(layout)
         self.params = params or sph.params()
         self.nthreads = nthreads
         self.gpu = gpu
+        self.plan = plan
         x = np.ascontiguousarray(fields["x"], np.float64)
         h = np.ascontiguousarray(fields["h"], np.float32)
         self.n = n = x.shape[0]
-        gp = sph.grid_params(box, self.params.kernel_gamma, ncell, bundle_max_slots)
         self.perm = np.empty(n, np.int64)
-        self.tasks = sph.sph_tasks_build(n, x.ctypes.data, h.ctypes.data, gp,
-                                         self.perm.ctypes.data)
-        self.info = sph.sph_tasks_info(self.tasks)
+        self.tasks = self.bplan = None
+        if plan == "tree":
+            if not gpu:
+                raise ValueError("the tree plan lives on the device: gpu=True")
+            self.bplan = sph.sph_batch_build_tree(n, x.ctypes.data, h.ctypes.data, box,
+                                                  self.params.kernel_gamma, leaf_max,
+                                                  max_target_cells, threads,
+                                                  self.perm.ctypes.data)
+            self.info = dict(sph.sph_batch_info(self.bplan))
+        else:
+            gp = sph.grid_params(box, self.params.kernel_gamma, ncell, bundle_max_slots)
+            self.tasks = sph.sph_tasks_build(n, x.ctypes.data, h.ctypes.data, gp,
+                                             self.perm.ctypes.data)
+            self.info = sph.sph_tasks_info(self.tasks)
         self.nbytes = sph.sph_store_bytes(n, self.layout, seed)
         self.mem, self._mem_owner = aligned_host(self.nbytes, pinned=gpu)
         self.store = sph.sph_store_create_host(n, self.layout, seed, self.mem.ctypes.data,
                                                self.nbytes)
-        nin = max(sph.sph_buffer_bytes(self.tasks, l, 0) for l in range(3))
-        nout = max(sph.sph_buffer_bytes(self.tasks, l, 1) for l in range(3))
-        self.nin, self.nout = nin, nout
-        self.host_in = [aligned_host(nin, pinned=gpu) for _ in range(2)]
-        self.host_out = [aligned_host(nout, pinned=gpu) for _ in range(2)]
+        self.host_in = self.host_out = None
+        if self.tasks is not None:
+            nin = max(sph.sph_buffer_bytes(self.tasks, l, 0) for l in range(3))
+            nout = max(sph.sph_buffer_bytes(self.tasks, l, 1) for l in range(3))
+            self.nin, self.nout = nin, nout
+            self.host_in = [aligned_host(nin, pinned=gpu) for _ in range(2)]
+            self.host_out = [aligned_host(nout, pinned=gpu) for _ in range(2)]
         if gpu:
+            self.streams = [torch.cuda.Stream() for _ in range(2)]
+        if gpu and self.tasks is not None:
             sph.sph_tasks_upload(self.tasks)
             self.dev_in = [torch.empty(max(nin, 256), dtype=torch.uint8, device="cuda")
                            for _ in range(2)]
             self.dev_out = [torch.empty(max(nout, 256), dtype=torch.uint8, device="cuda")
                             for _ in range(2)]
-            self.streams = [torch.cuda.Stream() for _ in range(2)]
         self.import_fields(fields)
+
+    def batch(self, max_target_cells: int = 0, threads: int = 128) -> None:
+        """Batched plan of the grid's cells (the tree plan is built already)."""
+        if self.plan == "tree":
+            return
+        if self.bplan is not None:
+            sph.sph_batch_destroy(self.bplan)
+        self.bplan = sph.sph_batch_build(self.tasks, max_target_cells, threads)
+        self.bbufs = None
+
+    def batch_loop(self, loop: int) -> None:
+        if self.bplan is None:
+            self.batch()
+        if getattr(self, "bbufs", None) is None:
+            nin = max(sph.sph_batch_buffer_bytes(self.bplan, l, 0) for l in range(3))
+            nout = max(sph.sph_batch_buffer_bytes(self.bplan, l, 1) for l in range(3))
+            self.bbufs = (
+                [aligned_host(nin, pinned=True) for _ in range(2)],
+                [aligned_host(nout, pinned=True) for _ in range(2)],
+                [torch.empty(max(nin, 256), dtype=torch.uint8, device="cuda") for _ in range(2)],
+                [torch.empty(max(nout, 256), dtype=torch.uint8, device="cuda") for _ in range(2)])
+        hin, hout, din, dout = self.bbufs
+        sph.sph_batch_offload_loop_host(
+            self.store, self.bplan, loop, [b[0].ctypes.data for b in hin],
+            [b[0].ctypes.data for b in hout], [d.data_ptr() for d in din],
+            [d.data_ptr() for d in dout], self.params, [s.cuda_stream for s in self.streams],
+            self.nthreads)
+
+    def batch_step(self) -> None:
+        """The batched cycle from the host store (host-staged)."""
+        for loop in (sph.SPH_DENSITY, sph.SPH_GRADIENT, sph.SPH_FORCE):
+            self.batch_loop(loop)
 
     def import_fields(self, fields: dict, names=INPUTS) -> None:
         keep = {}
@@ -487,6 +538,10 @@ class HostOffload:
         if getattr(self, "tasks", None) is not None:
             sph.sph_tasks_destroy(self.tasks)
             self.tasks = None
+        if getattr(self, "bplan", None) is not None:
+            sph.sph_batch_destroy(self.bplan)
+            self.bplan = None
+        self.bbufs = None
 
     def __del__(self):
         try:

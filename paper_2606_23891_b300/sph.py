@@ -137,6 +137,7 @@ def lib() -> C.CDLL:
         "sph_batch_offload_loop_list": (i, [p, p, i, p, p, p, sz, p, p]),
         "sph_batch_list_interact": (i, [p, i, i, p, p, p, sz, p, p]),
         "sph_batch_adjoint_bytes": (sz, [p]),
+        "sph_batch_offload_loop_host": (i, [p, p, i, p, p, p, p, p, p, i]),
         "sph_batch_adjoint": (i, [p, p, p, p, sz, p, sz, p, p, p, p, p, p, p, p]),
         "sph_tree_plan": (i, [i64, p, p, p, p, p, p, p, p, i64, p]),
         "sph_batch_count_pairs": (i, [p, p, i, p, p, p, p]),
@@ -418,6 +419,14 @@ def sph_batch_list_interact(b, loop: int, bundle: int, dev_in: int, dev_out: int
                             list_bytes: int, p: Params, stream: int = 0):
     _ok(lib().sph_batch_list_interact(b, loop, bundle, dev_in, dev_out, dev_list, list_bytes,
                                       C.byref(p), stream))
+
+
+def sph_batch_offload_loop_host(s, b, loop: int, host_in, host_out, dev_in, dev_out,
+                                p: Params, streams, nthreads: int = 0):
+    arr = C.c_void_p * 2
+    _ok(lib().sph_batch_offload_loop_host(s, b, loop, arr(*host_in), arr(*host_out),
+                                          arr(*dev_in), arr(*dev_out), C.byref(p),
+                                          arr(*streams), nthreads))
 
 
 def sph_batch_adjoint_bytes(b) -> int:

@@ -37,3 +37,39 @@ def test_host_staged_gresho_slice():
     host = HostOffload(f, layout="pack_shared_type", bundle_max_slots=20000)
     host.step()
     check_physics(f, host.export())
+
+
+# ------------------------------------------------ host-staged batched cycle --
+@pytest.mark.parametrize("mtc", [0, 50])
+def test_host_staged_batched_on_the_tree_plan(mtc):
+    """A clustered set kept in pinned host memory, staged through the tree
+    plan's bundles (the clustered host-staged configuration)."""
+    from paper_2606_23891_b300 import sph
+    f = ics.lognormal(n_side=24, seed=33)
+    host = HostOffload(f, layout="pack_force_type", plan="tree", max_target_cells=mtc)
+    if mtc:
+        assert sph.sph_batch_info(host.bplan)["nbundles"] > 4
+    host.batch_step()
+    got = host.export()
+    check_physics(f, got)
+    dev = Offload(f, layout="pack_force_type", plan="tree")
+    dev.batch_step()
+    want = dev.export()
+    for k in want:
+        assert rms_err(got[k], want[k]) <= 1e-5, k
+
+
+def test_host_staged_batched_on_the_grid_with_inactive_particles():
+    from paper_2606_23891_b300 import sph
+    f = ragged(24, 9)
+    f["time_bin"][::3] = 5
+    P = sph.params(active_bin=2)
+    host = HostOffload(f, layout=8, params=P)
+    host.batch(max_target_cells=40)
+    pre = {"a": np.full((f["x"].shape[0], 3), 7.0, np.float32)}
+    host.import_fields(pre, ("a",))
+    host.batch_step()
+    got = host.export()
+    inactive = f["time_bin"] > 2
+    assert np.all(got["a"][inactive] == 7.0)
+    check_physics(f, got, sel=np.nonzero(~inactive)[0], active_bin=2)
