@@ -277,7 +277,10 @@ class StepTimer:
             self.launches += 1
             for b in range(nb):
                 e0 = self.ev() if record else None
-                if batched:
+                if lists:
+                    sph.sph_batch_pack_list(off.store, off.bplan, loop, b,
+                                            off.bbuf_in.data_ptr(), off.params, st)
+                elif batched:
                     sph.sph_batch_pack(off.store, off.bplan, loop, b, off.bbuf_in.data_ptr(),
                                        off.params, st)
                 else:

@@ -459,8 +459,13 @@ size_t sph_batch_list_bytes(sph_batch b, int64_t chunks);
 int sph_batch_list_build(sph_store s, sph_batch b, void *dev_buf_in, void *dev_list,
                          size_t list_bytes, const sph_params *p, void *stream);
 int sph_batch_list_status(const void *dev_list, int64_t *chunks_needed, int *overflow);
-/* One bundle's list loop (after sph_batch_pack of the same loop and bundle);
- * results land in dev_buf_out for sph_batch_unpack. */
+/* The pack of the list loops: the density view as sph_batch_pack, the
+ * gradient and force views as compact records (c and P recomputed in the
+ * loop from u and rho, so each gathered j record is 48 / 64 bytes). */
+int sph_batch_pack_list(sph_store s, sph_batch b, int loop, int bundle, void *dev_buf_in,
+                        const sph_params *p, void *stream);
+/* One bundle's list loop (after sph_batch_pack_list of the same loop and
+ * bundle); results land in dev_buf_out for sph_batch_unpack. */
 int sph_batch_list_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in,
                             void *dev_buf_out, const void *dev_list, size_t list_bytes,
                             const sph_params *p, void *stream);

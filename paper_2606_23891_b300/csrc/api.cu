@@ -981,8 +981,21 @@ size_t sph_batch_buffer_bytes(sph_batch b, int loop, int in_or_out) {
     return (size_t)BLayout<SPH_FORCE>::bytes(S, C);
 }
 
+static int batch_pack(sph_store s, sph_batch b, int loop, int bundle, void *dev_buf_in,
+                      const sph_params *p, void *stream, bool compact);
+
 int sph_batch_pack(sph_store s, sph_batch b, int loop, int bundle, void *dev_buf_in,
                    const sph_params *p, void *stream) {
+    return batch_pack(s, b, loop, bundle, dev_buf_in, p, stream, false);
+}
+
+int sph_batch_pack_list(sph_store s, sph_batch b, int loop, int bundle, void *dev_buf_in,
+                        const sph_params *p, void *stream) {
+    return batch_pack(s, b, loop, bundle, dev_buf_in, p, stream, true);
+}
+
+static int batch_pack(sph_store s, sph_batch b, int loop, int bundle, void *dev_buf_in,
+                      const sph_params *p, void *stream, bool compact) {
     if (int rc = check_store(s)) return rc;
     if (int rc = check_batch(b, bundle)) return rc;
     if (int rc = check_loop(loop)) return rc;
@@ -1009,7 +1022,9 @@ int sph_batch_pack(sph_store s, sph_batch b, int loop, int bundle, void *dev_buf
     cudaStream_t st = (cudaStream_t)stream;
     const unsigned g = (unsigned)bb.ncells;
     if (loop == SPH_DENSITY) k_bpack<SPH_DENSITY><<<g, 128, 0, st>>>(a);
+    else if (loop == SPH_GRADIENT && compact) k_bpack<SPH_GRADIENT, true><<<g, 128, 0, st>>>(a);
     else if (loop == SPH_GRADIENT) k_bpack<SPH_GRADIENT><<<g, 128, 0, st>>>(a);
+    else if (compact) k_bpack<SPH_FORCE, true><<<g, 128, 0, st>>>(a);
     else k_bpack<SPH_FORCE><<<g, 128, 0, st>>>(a);
     return launch_check("batch pack");
 }
@@ -1324,7 +1339,7 @@ int sph_batch_offload_loop_list(sph_store s, sph_batch b, int loop, void *dev_bu
     if (int rc = check_loop(loop)) return rc;
     if (int rc = sph_init(s, loop, p, stream)) return rc;
     for (int k = 0; k < (int)b->bundles.size(); ++k) {
-        if (int rc = sph_batch_pack(s, b, loop, k, dev_buf_in, p, stream)) return rc;
+        if (int rc = sph_batch_pack_list(s, b, loop, k, dev_buf_in, p, stream)) return rc;
         if (int rc = sph_batch_list_interact(b, loop, k, dev_buf_in, dev_buf_out, dev_list,
                                              list_bytes, p, stream))
             return rc;

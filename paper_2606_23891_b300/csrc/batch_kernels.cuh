@@ -72,7 +72,16 @@ struct StoreSrc {
     }
 };
 
+// Compact records of the neighbour-list loops, which gather whole j records
+// per pair (fewer float4 lanes gathered; c and P are recomputed from u, rho):
+//   gradient: [0] hi H  [1] lo m/rho  [2] v u
+//   force:    [0] hi 1/H  [1] lo m  [2] v u  [3] rho  A = f P / rho^2  alpha_visc B  alpha_diff
 template <int LOOP>
+struct NFC {
+    static constexpr int value = LOOP == SPH_DENSITY ? 3 : (LOOP == SPH_GRADIENT ? 3 : 4);
+};
+
+template <int LOOP, bool COMPACT = false>
 __device__ __forceinline__ void make_record(const BPackArgs &a, long long p, float4 *r,
                                             float &hf) {
     double x[3];
@@ -85,6 +94,20 @@ __device__ __forceinline__ void make_record(const BPackArgs &a, long long p, flo
     split_f64(x[2], hz, lz);
     const float H = a.kernel_gamma * h;
     if (LOOP == SPH_DENSITY) u = 0.f;
+    if (COMPACT && LOOP != SPH_DENSITY) {
+        r[1] = make_float4(lx, ly, lz, LOOP == SPH_GRADIENT ? vm.w / rho : vm.w);
+        r[2] = make_float4(vm.x, vm.y, vm.z, u);
+        hf = 0.f;
+        if (LOOP == SPH_GRADIENT) {
+            r[0] = make_float4(hx, hy, hz, H);
+        } else {
+            const float P = (a.gamma - 1.f) * rho * u;
+            r[0] = make_float4(hx, hy, hz, 1.f / H);
+            r[3] = make_float4(rho, fgh * P / (rho * rho), av * bal, ad);
+            hf = h * (fgh / rho);
+        }
+        return;
+    }
     if (LOOP == SPH_FORCE) {
         const float Hp = H + a.delta;
         r[0] = make_float4(hx, hy, hz, Hp * Hp);
@@ -107,10 +130,10 @@ __device__ __forceinline__ void make_record(const BPackArgs &a, long long p, flo
     }
 }
 
-template <int LOOP>
+template <int LOOP, bool COMPACT = false>
 __global__ void __launch_bounds__(128) k_bpack(BPackArgs a) {
     using BL = BLayout<LOOP>;
-    constexpr int nf = BL::nf;
+    constexpr int nf = COMPACT ? NFC<LOOP>::value : BL::nf;
     constexpr int kChunksMax = kBSortMax / 32;
     __shared__ float red[6][4];
     __shared__ float hred[4];
@@ -213,9 +236,9 @@ __global__ void __launch_bounds__(128) k_bpack(BPackArgs a) {
         }
         if (k >= C.n) continue;
         const long long p = (long long)C.p0 + k;
-        float4 r[nf];
+        float4 r[BL::nf];
         float hf;
-        make_record<LOOP>(a, p, r, hf);
+        make_record<LOOP, COMPACT>(a, p, r, hf);
         const long long sl = (long long)C.slot + pos;
         for (int f = 0; f < nf; ++f)
             reinterpret_cast<float4 *>(a.buf + BL::rec(f, a.S))[sl] = r[f];

@@ -250,11 +250,99 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
 }
 
 // ---------------------------------------------------------------- loops --
+// Pair bodies of the gradient and force loops on compact records (the same
+// sums as Acc<LOOP>, with c = sqrt(gamma (gamma - 1) u) and P = (gamma - 1)
+// rho u recomputed from the gathered u and rho).
+template <int LOOP>
+struct AccL : Acc<LOOP> {};
+
+template <>
+struct AccL<SPH_GRADIENT> {
+    float vsig, slap, ci, ui, Hinv, gg;
+    __device__ __forceinline__ void init(const float4 *own, float, const PhysArgs &pa) {
+        vsig = 0.f;
+        slap = 0.f;
+        Hinv = 1.f / own[0].w;
+        gg = pa.gamma * (pa.gamma - 1.f);
+        ui = own[2].w;
+        ci = sqrtf(gg * ui);
+    }
+    __device__ __forceinline__ void body(const float4 *own, const float4 *oth, float dx,
+                                         float dy, float dz, float r2, const PhysArgs &a) {
+        const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        const float q = r2 * rinv * Hinv;
+        float w, dw;
+        spline(q, w, dw);
+        const float wdot = ((own[2].x - oth[2].x) * dx + (own[2].y - oth[2].y) * dy +
+                            (own[2].z - oth[2].z) * dz) * rinv;
+        const float vs = ci + sqrtf(gg * oth[2].w) - a.beta * fminf(0.f, wdot);
+        vsig = fmaxf(vsig, vs);
+        slap = fmaf(oth[1].w * (ui - oth[2].w), dw * rinv, slap);
+    }
+    __device__ __forceinline__ void write(const PhysArgs &a, long long s, const float4 *) const {
+        const float n4 = kNorm * Hinv * Hinv * Hinv * Hinv;
+        reinterpret_cast<float2 *>(a.out[0])[s] = make_float2(vsig, 2.f * n4 * slap);
+    }
+};
+
+template <>
+struct AccL<SPH_FORCE> {
+    float ax, ay, az, udt, hsum, vsig;
+    float Hinv, n4i, gg, g1, ci, Pi_;
+    __device__ __forceinline__ void init(const float4 *own, float, const PhysArgs &pa) {
+        ax = ay = az = udt = hsum = vsig = 0.f;
+        Hinv = own[0].w;
+        n4i = kNorm * Hinv * Hinv * Hinv * Hinv;
+        gg = pa.gamma * (pa.gamma - 1.f);
+        g1 = pa.gamma - 1.f;
+        ci = sqrtf(gg * own[2].w);
+        Pi_ = g1 * own[3].x * own[2].w;
+    }
+    __device__ __forceinline__ void body(const float4 *own, const float4 *oth, float dx,
+                                         float dy, float dz, float r2, const PhysArgs &a) {
+        const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        const float r = r2 * rinv;
+        const float qi = r * Hinv;
+        const float hj = oth[0].w;
+        const float qj = r * hj;
+        float w, dwi, dwj;
+        spline(qi, w, dwi);
+        if (!(qi < 1.f)) dwi = 0.f;
+        spline(qj, w, dwj);
+        if (!(qj < 1.f)) dwj = 0.f;
+        const float Fi = n4i * dwi;
+        const float Fj = kNorm * hj * hj * hj * hj * dwj;
+        const float wdot = ((own[2].x - oth[2].x) * dx + (own[2].y - oth[2].y) * dy +
+                            (own[2].z - oth[2].z) * dz) * rinv;
+        const float mu = fminf(0.f, wdot);
+        const float Fbar = 0.5f * (Fi + Fj);
+        const float rhobar = 0.5f * (own[3].x + oth[3].x);
+        const float rhobar_inv = 1.f / rhobar;
+        const float alpha = 0.5f * (own[3].z + oth[3].z);
+        const float cj = sqrtf(gg * oth[2].w);
+        const float vs = ci + cj - a.beta * mu;
+        const float Pv = -alpha * vs * mu * rhobar_inv;
+        const float mj = oth[1].w;
+        const float sc = own[3].y * Fi + oth[3].y * Fj + Pv * Fbar;
+        const float f = mj * sc * rinv;
+        ax = fmaf(-f, dx, ax);
+        ay = fmaf(-f, dy, ay);
+        az = fmaf(-f, dz, az);
+        const float Pj = g1 * oth[3].x * oth[2].w;
+        const float alphaD = 0.5f * (own[3].w + oth[3].w);
+        const float cond = alphaD * sqrtf(fabsf(Pi_ - Pj) * rhobar_inv) *
+                           (own[2].w - oth[2].w) * Fbar * rhobar_inv;
+        udt = fmaf(mj, fmaf(own[3].y * Fi, wdot, fmaf(0.5f * Pv * Fbar, wdot, cond)), udt);
+        hsum = fmaf(mj * wdot, Fi, hsum);
+        vsig = fmaxf(vsig, vs);
+    }
+};
+
 template <int LOOP, int T>
 __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? SPH_BMINB_FORCE : 1024) / T)
     k_bloop(BInteractArgs a, ListView L, long long item0) {
     using BL = BLayout<LOOP>;
-    constexpr int nf = NF<LOOP>::value;
+    constexpr int nf = NFC<LOOP>::value;     // compact records (k_bpack<LOOP, true>)
     const int lane = threadIdx.x & 31;
     const float4 *rec[nf];
 #pragma unroll
@@ -272,12 +360,13 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? SPH_BMINB_FORCE : 1024
         const bool valid = i < C.n;
         const long long slot = (long long)C.slot + i;
         float4 own[nf];
-        Acc<LOOP> acc;
+        AccL<LOOP> acc;
         bool active = false;
         if (valid) {
 #pragma unroll
             for (int f = 0; f < nf; ++f) own[f] = rec[f][slot];
-            acc.init(own, a.delta);
+            if constexpr (LOOP == SPH_DENSITY) acc.init(own, a.delta);
+            else acc.init(own, a.delta, a.pa);
             active = LOOP != SPH_FORCE ||
                      (int)reinterpret_cast<const int8_t *>(a.in + BL::tb(a.S))[slot] <= a.active_bin;
         } else {

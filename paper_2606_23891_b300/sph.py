@@ -124,6 +124,7 @@ def lib() -> C.CDLL:
         "sph_batch_info": (i, [p, p]),
         "sph_batch_buffer_bytes": (sz, [p, i, i]),
         "sph_batch_pack": (i, [p, p, i, i, p, p, p]),
+        "sph_batch_pack_list": (i, [p, p, i, i, p, p, p]),
         "sph_batch_interact": (i, [p, i, i, p, p, p, p]),
         "sph_batch_unpack": (i, [p, p, i, i, p, p, p]),
         "sph_batch_offload_loop": (i, [p, p, i, p, p, p, p]),
@@ -413,6 +414,10 @@ def sph_batch_list_status(dev_list: int):
     need, ovf = C.c_int64(), C.c_int()
     _ok(lib().sph_batch_list_status(dev_list, C.byref(need), C.byref(ovf)))
     return need.value, ovf.value
+
+
+def sph_batch_pack_list(s, b, loop: int, bundle: int, dev_in: int, p: Params, stream: int = 0):
+    _ok(lib().sph_batch_pack_list(s, b, loop, bundle, dev_in, C.byref(p), stream))
 
 
 def sph_batch_list_interact(b, loop: int, bundle: int, dev_in: int, dev_out: int, dev_list: int,
