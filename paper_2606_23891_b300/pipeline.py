@@ -398,6 +398,71 @@ def host_fields_struct(arrays: dict) -> sph.Fields:
     return F
 
 
+class StreamingSteps:
+    """End-to-end steps from pinned host inputs to pinned host results with
+    the copies overlapped: while step k computes on the offload's stream,
+    step k+1's inputs travel host -> device on one copy stream and step k-1's
+    results device -> host on another.  Each step still copies its inputs in
+    and its results out; two device staging sets alternate between steps."""
+
+    def __init__(self, off: "Offload", step_fn, names_in=INPUTS, names_out=OUTPUTS):
+        self.off = off
+        self.step_fn = step_fn
+        self.names_in, self.names_out = tuple(names_in), tuple(names_out)
+        dev = off.device
+        self.dev_in = []
+        for _ in range(2):
+            d = {}
+            for name in self.names_in:
+                dt, k = field_spec(name)
+                shape = (off.n, k) if k > 1 else (off.n,)
+                d[name] = torch.empty(shape, dtype=torch.from_numpy(np.zeros(0, dt)).dtype,
+                                      device=dev)
+            self.dev_in.append(d)
+        self.dev_out = [off.device_fields(self.names_out) for _ in range(2)]
+        self.s_in = torch.cuda.Stream(dev)
+        self.s_out = torch.cuda.Stream(dev)
+        ev = lambda: torch.cuda.Event()
+        self.in_ready = [ev() for _ in range(2)]
+        self.in_free = [ev() for _ in range(2)]
+        self.out_ready = [ev() for _ in range(2)]
+        self.out_free = [ev() for _ in range(2)]
+        self.k = 0
+
+    def bytes_per_step(self):
+        h2d = sum(t.numel() * t.element_size() for t in self.dev_in[0].values())
+        d2h = sum(t.numel() * t.element_size() for t in self.dev_out[0].values())
+        return h2d, d2h
+
+    def step(self, pin_in: dict, pin_out: dict) -> None:
+        """Enqueue one step: H2D of pin_in, the step, D2H into pin_out."""
+        b = self.k & 1
+        comp = torch.cuda.current_stream(self.off.device)
+        di, do = self.dev_in[b], self.dev_out[b]
+        self.s_in.wait_event(self.in_free[b])
+        with torch.cuda.stream(self.s_in):
+            for name in self.names_in:
+                di[name].copy_(pin_in[name], non_blocking=True)
+            self.in_ready[b].record(self.s_in)
+        comp.wait_event(self.in_ready[b])
+        self.off.import_device(di)
+        self.in_free[b].record(comp)
+        self.step_fn()
+        comp.wait_event(self.out_free[b])
+        sph.sph_store_export(self.off.store, fields_struct(do), self.off.d_perm.data_ptr(),
+                             self.off.stream)
+        self.out_ready[b].record(comp)
+        self.s_out.wait_event(self.out_ready[b])
+        with torch.cuda.stream(self.s_out):
+            for name in self.names_out:
+                pin_out[name].copy_(do[name], non_blocking=True)
+            self.out_free[b].record(self.s_out)
+        self.k += 1
+
+    def drain(self) -> None:
+        torch.cuda.current_stream(self.off.device).wait_stream(self.s_out)
+
+
 class HostOffload:
     """A particle set in a host-memory store (the paper's host side) with the
     host-staged double-buffered cycle.  Without a GPU only the host calls

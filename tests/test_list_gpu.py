@@ -92,3 +92,42 @@ def test_list_pool_overflow_is_reported_and_recovered():
     with pytest.raises(sph.SphError):             # buffer below the fixed tables
         sph.sph_batch_list_build(off.store, off.bplan, off.bbuf_in.data_ptr(), buf.data_ptr(),
                                  256, off.params, off.stream)
+
+
+def test_streaming_steps_give_each_steps_results():
+    """Overlapped end-to-end steps: step k's results in pinned memory equal a
+    plain list step on step k's inputs, with the copies of neighbouring
+    steps in flight."""
+    from paper_2606_23891_b300.pipeline import INPUTS, StreamingSteps, field_spec
+    base = ragged(12, 60)
+    fs = []
+    for k in range(3):        # same positions (the plan holds), other v and u
+        f = {key: v.copy() for key, v in base.items()}
+        rng = np.random.Generator(np.random.PCG64(70 + k))
+        f["v"] += rng.uniform(-0.2, 0.2, f["v"].shape).astype(np.float32)
+        f["u"] *= rng.uniform(0.8, 1.2, f["u"].shape).astype(np.float32)
+        fs.append(f)
+    off = Offload(fs[0], layout=6)
+    off.batch()
+    ref = []
+    for f in fs:
+        off.import_fields(f)
+        off.list_step()
+        ref.append(off.export())
+    ss = StreamingSteps(off, off.list_step)
+    pins_in, pins_out = [], []
+    for f in fs:
+        d = {}
+        for name in INPUTS:
+            dt, _ = field_spec(name)
+            d[name] = torch.from_numpy(np.ascontiguousarray(f[name], dt)).pin_memory()
+        pins_in.append(d)
+        pins_out.append({k: torch.empty(v.shape, dtype=v.dtype).pin_memory()
+                         for k, v in ss.dev_out[0].items()})
+    for k in range(3):
+        ss.step(pins_in[k], pins_out[k])
+    ss.drain()
+    torch.cuda.synchronize()
+    for k in range(3):
+        for name, v in ref[k].items():
+            np.testing.assert_array_equal(pins_out[k][name].numpy(), v, err_msg=name)
