@@ -64,7 +64,7 @@ def test_adjoint_with_inactive_particles():
     act = torch.tensor(np.asarray(f["time_bin"]) <= 2, device=dev)
     L = ((a.double() ** 2).sum(dim=1) + udt.double() ** 2)[act].sum()
     L.backward()
-    assert abs(float(L) - ref_loss) <= 1e-5 * ref_loss
+    assert abs(L.item() - ref_loss) <= 1e-5 * ref_loss
     assert norm_err(x.grad.cpu().numpy(), rx) <= 1e-4
     assert norm_err(m.grad.cpu().numpy(), rm) <= 1e-4
     assert norm_err(u.grad.cpu().numpy(), ru) <= 1e-4
