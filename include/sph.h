@@ -360,13 +360,16 @@ int sph_offload_loop_host(sph_store s, sph_tasks t, int loop, void *const host_i
  * needs (targets and their periodic neighbours) is packed once per bundle
  * (positions already split for the FP32 kernels), and one persistent launch
  * works through (target cell, particle chunk) items in longest-first order,
- * each computing its particles' sums over all 27 neighbour cells.  Unpack
+ * each computing its particles' sums over all the target's neighbour
+ * entries (the 27 periodic neighbour cells of the grid plan, or the
+ * box-distance entries of the tree plan).  Unpack
  * adds each target particle's single result into the store (no per-slot
  * reduction).  Outputs agree with the per-task cycle to rounding (the sum
  * order over neighbours differs). */
 typedef struct {
     int64_t max_target_cells;  /* target cells per bundle, <= 0: all */
-    int32_t threads;           /* CTA size and particle chunk: 64, 128, 256 */
+    int32_t threads;           /* CTA size of the persistent kernels: 64, 128, 256
+                                  (a work item is one warp of 32 particles) */
     int32_t reserved;          /* must be 0 */
 } sph_batch_params;
 

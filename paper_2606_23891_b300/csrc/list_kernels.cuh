@@ -1,7 +1,7 @@
 // Neighbour-list variant of the batched interaction kernels.
 //
-// The tile kernels (k_binteract) test every candidate of the 27 neighbour
-// cells (or leaf entries) again in each of the three loops, and run the pair
+// The tile kernels (k_binteract) test every candidate of a target's neighbour
+// entries (cells or leaves) again in each of the three loops, and run the pair
 // body per lane over that lane's own hits, so lanes with fewer hits idle.
 // Here the candidate tests run once per step:
 //
