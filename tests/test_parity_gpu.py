@@ -337,3 +337,38 @@ def test_gresho_256_conservation(gresho_full):
     assert abs(kin.sum() + th.sum()) <= 1e-4 * (np.abs(kin).sum() + np.abs(th).sum())
     # the paper's cell statistics for this workload (Sec. 3.4)
     assert off.info["max_cell"] == 73 and off.info["nonempty_cells"] == 64 ** 3
+
+
+# ------------------------------------- full-size, the pipelines the bench times --
+@pytest.mark.parametrize("threads", [128, 256])
+def test_gresho_256_list_pipeline_sampled_parity(cuda, threads):
+    """The headline configuration: Gresho256, pack-force-type store, one
+    bundle, the neighbour-list step, both CTA sizes the autotuner picks from."""
+    from bench import BENCH_LAYOUT
+    f = ics.gresho()
+    off = Offload(f, layout=BENCH_LAYOUT)
+    off.batch(threads=threads)
+    off.list_step()
+    got = off.export()
+    rng = np.random.Generator(np.random.PCG64(2607))
+    n = f["x"].shape[0]
+    sel = np.unique(np.concatenate([rng.integers(0, n, 8),
+                                    np.nonzero(f["x"][:, 2] > 1 - 2e-3)[0][:2]]))
+    check_physics(f, got, sel)
+    m = f["mass"].astype(np.float64)
+    a = got["a"].astype(np.float64)
+    assert np.all(np.abs((m[:, None] * a).sum(0)) <= 1e-5 * (m[:, None] * np.abs(a)).sum(0))
+
+
+def test_lognormal_376_tree_list_sampled_parity(cuda):
+    """The clustered workload at full size (53.2M particles) on the tree plan
+    the bench tunes, list step, against the oracle on sampled particles."""
+    f = ics.lognormal(n_side=376)
+    off = Offload(f, layout="pack_force_type", plan="tree", leaf_max=256)
+    off.list_step()
+    got = off.export(("rho", "rho_dh", "wcount", "wcount_dh", "div_v", "rot_v", "f_gradh",
+                      "pressure", "soundspeed", "balsara", "v_sig_grad", "laplace_u", "a",
+                      "u_dt", "h_dt", "v_sig"))
+    rng = np.random.Generator(np.random.PCG64(3760))
+    sel = np.sort(rng.choice(f["x"].shape[0], 4, replace=False))
+    check_physics(f, got, sel)
