@@ -338,8 +338,12 @@ struct AccL<SPH_FORCE> {
     }
 };
 
+// Resident threads per SM the list loops are compiled for (measured at
+// Gresho256: density and gradient gain from 48 warps per SM at 40 registers,
+// the force body needs its 61 registers and runs best at 32 warps).
+constexpr int kLLoopMinThreads[3] = {1536, 1536, 1024};
 template <int LOOP, int T>
-__global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? SPH_BMINB_FORCE : 1024) / T)
+__global__ void __launch_bounds__(T, kLLoopMinThreads[LOOP] / T)
     k_bloop(BInteractArgs a, ListView L, long long item0) {
     using BL = BLayout<LOOP>;
     constexpr int nf = NFC<LOOP>::value;     // compact records (k_bpack<LOOP, true>)
