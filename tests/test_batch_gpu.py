@@ -10,13 +10,13 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2606_23891_b300.pipeline import Offload  # noqa: E402
-from test_parity_gpu import CONFIGS, check_physics, ragged, rms_err  # noqa: E402
+from test_parity_gpu import PARITY_CASES, check_physics, ragged, rms_err  # noqa: E402
 
 
 @pytest.mark.parametrize("threads", [64, 128, 256])
-@pytest.mark.parametrize("case", sorted(CONFIGS))
+@pytest.mark.parametrize("case", sorted(PARITY_CASES))
 def test_batched_pass_matches_the_oracle(case, threads):
-    f = CONFIGS[case]()
+    f = PARITY_CASES[case]()
     off = Offload(f, layout="pack_force_type")
     off.batch(threads=threads)
     off.batch_step()

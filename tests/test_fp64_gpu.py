@@ -26,7 +26,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2606_23891_b300.pipeline import Offload  # noqa: E402
-from test_parity_gpu import CONFIGS, check_physics  # noqa: E402
+from test_parity_gpu import PARITY_CASES, check_physics  # noqa: E402
 
 TIGHT = ("rho", "wcount", "pressure", "soundspeed", "v_sig_grad", "v_sig")
 MID = ("f_gradh", "balsara", "rho_dh", "wcount_dh")
@@ -43,9 +43,9 @@ def fp64_bars(err):
 
 
 @pytest.mark.parametrize("mtc", [0, 29])
-@pytest.mark.parametrize("case", sorted(CONFIGS))
+@pytest.mark.parametrize("case", sorted(PARITY_CASES))
 def test_fp64_pass_matches_the_oracle(case, mtc):
-    f = CONFIGS[case]()
+    f = PARITY_CASES[case]()
     off = Offload(f, layout="pack_force_type")
     off.batch(max_target_cells=mtc)
     off.fp64_step()
@@ -95,7 +95,7 @@ def test_fp64_inactive_particles_and_large_cells():
 
 
 def test_fp64_steps_are_reproducible():
-    f = CONFIGS["ragged12"]()
+    f = PARITY_CASES["ragged12"]()
     off = Offload(f, layout=0)
     off.batch(max_target_cells=50)
     off.fp64_step()
@@ -107,7 +107,7 @@ def test_fp64_steps_are_reproducible():
 
 
 def test_fp64_api_rejects_misuse():
-    f = CONFIGS["ragged12"]()
+    f = PARITY_CASES["ragged12"]()
     off = Offload(f, layout=0)
     off.batch()
     n_in = sph.sph_batch_buffer_bytes_fp64(off.bplan, 0)

@@ -1,6 +1,6 @@
 """GPU path vs the CPU oracle, through the C-ABI on the same seeded inputs.
 
-Bars (see the design doc for the derivations):
+Bars (each with the arithmetic behind it in the comments below):
   store import/export, pack, unpack : bit-exact
   rho, wcount, f_gradh, pressure, soundspeed : rel <= 1e-5
   rho_dh : |err| <= 1e-5 * 3 rho / H (its natural scale; it is a cancelling
@@ -200,7 +200,7 @@ def check_physics(f, got, sel=None, box=(1.0, 1.0, 1.0), active_bin=0, bands=Fal
     return ref, lo, hi
 
 
-CONFIGS = {
+PARITY_CASES = {
     "lattice16": lambda: ics.uniform_lattice(),          # the tiny plain case
     "ragged12": lambda: ragged(12, 5),
     "ragged24": lambda: ragged(24, 8),
@@ -209,9 +209,9 @@ CONFIGS = {
 
 
 @pytest.mark.parametrize("layout", [0, 6])
-@pytest.mark.parametrize("case", sorted(CONFIGS))
+@pytest.mark.parametrize("case", sorted(PARITY_CASES))
 def test_full_pass_matches_the_oracle(cuda, case, layout):
-    f = CONFIGS[case]()
+    f = PARITY_CASES[case]()
     off = Offload(f, layout=layout)
     off.step()
     got = off.export()
