@@ -355,11 +355,12 @@ def run_e2e(off, f, steps, warmup, pipeline="plain"):
     (pipeline.StreamingSteps)."""
     import torch
     from paper_2606_23891_b300 import sph
-    from paper_2606_23891_b300.pipeline import INPUTS, OUTPUTS, StreamingSteps, field_spec
+    from paper_2606_23891_b300.pipeline import (STEP_INPUTS, STEP_RESULTS, StreamingSteps,
+                                                field_spec)
     timer = StepTimer(off, pipeline)
-    ss = StreamingSteps(off, lambda: timer.step(record=False))
+    ss = StreamingSteps(off, lambda: timer.step(record=False), STEP_INPUTS, STEP_RESULTS)
     pin_in = {}
-    for name in INPUTS:
+    for name in STEP_INPUTS:
         dt, k = field_spec(name)
         pin_in[name] = torch.from_numpy(np.ascontiguousarray(f[name], dt)).pin_memory()
     pin_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory()
@@ -988,7 +989,9 @@ def run_ours(args, ws, rank, local):
         },
         "e2e": {"value": sum(pairs) * ws / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_ms},
+                "ms_per_step": e2e_ms,
+                "copied": "in: x v m h u alpha_visc alpha_diff time_bin; "
+                          "out: rho a du/dt dh/dt v_sig (the step's results)"},
         "gpu_launches": timer.launches,
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -18,6 +18,10 @@ _TORCH_DT = {np.dtype(np.float64): torch.float64, np.dtype(np.float32): torch.fl
 _FIELD_DT = {"x": (np.float64, 3), "v": (np.float32, 3), "a": (np.float32, 3),
              "rot_v": (np.float32, 3), "time_bin": (np.int8, 1), "id": (np.int64, 1)}
 INPUTS = ("x", "v", "mass", "h", "u", "alpha_visc", "alpha_diff", "time_bin", "id")
+# the fields a step reads, and the results an integrator takes from it (the
+# other outputs are intermediates that later loops of the same step consume)
+STEP_INPUTS = ("x", "v", "mass", "h", "u", "alpha_visc", "alpha_diff", "time_bin")
+STEP_RESULTS = ("rho", "a", "u_dt", "h_dt", "v_sig")
 OUTPUTS = ("rho", "rho_dh", "wcount", "wcount_dh", "div_v", "rot_v", "f_gradh",
            "pressure", "soundspeed", "balsara", "v_sig_grad", "laplace_u", "a",
            "u_dt", "h_dt", "v_sig")
