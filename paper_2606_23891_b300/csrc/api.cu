@@ -1337,6 +1337,13 @@ int sph_batch_offload_loop_list(sph_store s, sph_batch b, int loop, void *dev_bu
     if (int rc = check_store(s)) return rc;
     if (!b) return fail(SPH_EINVAL, "NULL batch handle");
     if (int rc = check_loop(loop)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (s->n != b->n) return fail(SPH_EINVAL, "store and batch disagree on particle count");
+    if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_buf_out || !aligned256(dev_buf_out) ||
+        !dev_list || !aligned256(dev_list))
+        return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
+    if ((int64_t)list_bytes < ListLayout::fixed((int64_t)b->items.size()) + 512)
+        return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
     if (int rc = sph_init(s, loop, p, stream)) return rc;
     for (int k = 0; k < (int)b->bundles.size(); ++k) {
         if (int rc = sph_batch_pack_list(s, b, loop, k, dev_buf_in, p, stream)) return rc;

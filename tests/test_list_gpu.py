@@ -131,3 +131,41 @@ def test_streaming_steps_give_each_steps_results():
     for k in range(3):
         for name, v in ref[k].items():
             np.testing.assert_array_equal(pins_out[k][name].numpy(), v, err_msg=name)
+
+
+def test_list_and_batch_api_reject_misuse():
+    f = ragged(12, 52)
+    off = Offload(f, layout=0)
+    off.batch()
+    off.list_step()
+    b, st = off.bplan, off.stream
+    lb = off.blist_bytes
+    with pytest.raises(sph.SphError):          # misaligned list buffer
+        sph.sph_batch_list_build(off.store, b, off.bbuf_in.data_ptr(),
+                                 off.blist.data_ptr() + 8, lb, off.params, st)
+    with pytest.raises(sph.SphError):          # list buffer below its fixed tables
+        sph.sph_batch_offload_loop_list(off.store, b, 1, off.bbuf_in.data_ptr(),
+                                        off.bbuf_out.data_ptr(), off.blist.data_ptr(), 512,
+                                        off.params, st)
+    with pytest.raises(sph.SphError):          # bundle out of range
+        sph.sph_batch_list_interact(b, 1, 5, off.bbuf_in.data_ptr(), off.bbuf_out.data_ptr(),
+                                    off.blist.data_ptr(), lb, off.params, st)
+    with pytest.raises(sph.SphError):          # unknown loop
+        sph.sph_batch_pack_list(off.store, b, 3, 0, off.bbuf_in.data_ptr(), off.params, st)
+    with pytest.raises(sph.SphError):          # a device store on the host-staged call
+        sph.sph_batch_offload_loop_host(off.store, b, 0, [1, 1], [1, 1], [1, 1], [1, 1],
+                                        off.params, [0, 0])
+    with pytest.raises(sph.SphError):          # stores of different particle counts
+        g = ragged(8, 53)
+        other = Offload(g, layout=0)
+        sph.sph_store_convert(other.store, off.store, st)
+    with pytest.raises(sph.SphError):          # tree plan with a support above half the box
+        bad = {k: v.copy() for k, v in f.items()}
+        bad["h"][0] = 0.3
+        Offload(bad, plan="tree")
+    sph.sph_sync(st)
+    # the failed calls left nothing behind: the step still matches
+    a = off.export()
+    off.list_step()
+    for k, v in off.export().items():
+        np.testing.assert_array_equal(v, a[k])
