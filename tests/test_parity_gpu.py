@@ -372,3 +372,63 @@ def test_lognormal_376_tree_list_sampled_parity(cuda):
     rng = np.random.Generator(np.random.PCG64(3760))
     sel = np.sort(rng.choice(f["x"].shape[0], 4, replace=False))
     check_physics(f, got, sel)
+
+
+# -------------------------------------------- views, outputs, poisoned buffers --
+VIEW = {0: ("x", "v", "mass", "h"), 1: ("x", "v", "mass", "h", "u", "rho"),
+        2: ("x", "v", "mass", "h", "u", "rho", "time_bin", "f_gradh", "balsara",
+            "alpha_visc", "alpha_diff")}
+STEP_OUTPUTS = ("rho", "rho_dh", "wcount", "wcount_dh", "div_v", "rot_v", "f_gradh",
+                "pressure", "soundspeed", "balsara", "v_sig_grad", "laplace_u", "a", "u_dt",
+                "h_dt", "v_sig")
+
+
+@pytest.mark.parametrize("layout", [0, 6, 8, 9, 10])
+@pytest.mark.parametrize("loop", [0, 1, 2])
+def test_pack_reads_only_its_view(cuda, layout, loop):
+    """Table 1: a loop's pack reads exactly its view.  Every other field of the
+    store is overwritten with other values; the packed lanes do not change."""
+    f = randomise_all(ragged(), 17)
+    off = Offload(f, layout=layout, seed=3, bundle_max_slots=6000)
+    off.import_fields(f, ALL_FIELDS)
+    others = [k for k in ALL_FIELDS if k not in VIEW[loop] and k != "id"]
+    junk = randomise_all(ragged(), 99)
+    off.import_fields(junk, others)
+    ci, cj, sh, cs, bs = off.task_list()
+    for b in range(len(bs) - 1):
+        off.pack(loop, b)
+        sph.sph_sync(off.stream)
+        got = off.buf_in.cpu().numpy()
+        ref = oracle.pack(loop, f, off.perm, cs, ci, cj, sh, int(bs[b]), int(bs[b + 1]))
+        S = oracle.bundle_slots(ci, cj, cs, bs[b], bs[b + 1])
+        for sl in lane_slices(loop, 0, S):
+            np.testing.assert_array_equal(got[sl], ref[sl])
+
+
+@pytest.mark.parametrize("pipeline", ["plain", "batched", "list"])
+def test_a_step_writes_only_its_outputs_and_ignores_poisoned_buffers(cuda, pipeline):
+    """A step leaves every non-output field of the store bit-identical, and it
+    writes every slot it reads back: buffers (and the list pool) filled with
+    NaN bytes before the step give the same results."""
+    f = randomise_all(ragged(), 21)
+    off = Offload(f, layout=6, bundle_max_slots=5000)
+    off.import_fields(f, ALL_FIELDS)
+    step = {"plain": off.step, "batched": off.batch_step, "list": off.list_step}[pipeline]
+    if pipeline != "plain":
+        off.batch(max_target_cells=60)
+    keep = [k for k in ALL_FIELDS if k not in STEP_OUTPUTS]
+    before = off.export(keep)
+    step()
+    ref = off.export(STEP_OUTPUTS)
+    after = off.export(keep)
+    for k in keep:
+        np.testing.assert_array_equal(after[k], before[k], err_msg=k)
+    # the list pool keeps its size; its header, tables and chunks are poisoned too
+    for buf in (off.buf_in, off.buf_out, getattr(off, "bbuf_in", None),
+                getattr(off, "bbuf_out", None), getattr(off, "blist", None)):
+        if buf is not None:
+            buf.fill_(0xFF)
+    step()
+    got = off.export(STEP_OUTPUTS)
+    for k in STEP_OUTPUTS:
+        np.testing.assert_array_equal(got[k], ref[k], err_msg=k)
