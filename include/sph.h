@@ -69,7 +69,7 @@ enum sph_status {
     SPH_ENOMEM = 2,       /* host or device metadata allocation failed */
     SPH_ECUDA = 3,        /* a CUDA runtime call failed */
     SPH_EBOUNDS = 4,      /* a kernel saw an index outside its buffers */
-    SPH_ETIMEOUT = 5,     /* a bounded device wait ran out */
+    SPH_ETIMEOUT = 5,     /* a bounded device wait ran out (no current kernel waits) */
     SPH_EUNSUPPORTED = 6  /* valid request the library cannot serve */
 };
 
@@ -268,6 +268,16 @@ int sph_offload_loop(sph_store s, sph_tasks t, int loop, void *dev_buf_in,
 int sph_count_pairs(sph_tasks t, int loop, int bundle, const void *dev_buf_in,
                     const sph_params *p, unsigned long long *dev_count,
                     void *stream);
+
+/* Host-side fault injection, for tests of the error paths (no device fault
+ * is ever caused): the countdown-th library use of `site` from now fails
+ * once, as if the CUDA call had failed, and the call reports it (device
+ * allocation of plan metadata: SPH_ENOMEM; metadata copy: SPH_ECUDA) after
+ * releasing what it had set up.  SPH_FAULT_NONE or countdown 0 disarms.
+ * The environment variable SPH_FAULT_INJECT=alloc:N or copy:N arms a site
+ * the same way when the library is loaded. */
+enum sph_fault_site { SPH_FAULT_NONE = 0, SPH_FAULT_DEVICE_ALLOC = 1, SPH_FAULT_COPY = 2 };
+int sph_fault_inject(int site, int countdown);
 
 /* Wait for `stream` and report errors latched by kernels: SPH_EBOUNDS (an
  * index outside its buffers), SPH_ETIMEOUT (a bounded wait ran out),

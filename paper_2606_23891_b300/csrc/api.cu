@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <new>
 
 #include "internal.h"
@@ -84,6 +85,48 @@ static int check_params(const sph_params *p) {
     if (!(p->kernel_gamma > 0.0) || !(p->gamma > 1.0))
         return fail(SPH_EINVAL, "params: kernel_gamma > 0 and gamma > 1 required");
     return SPH_OK;
+}
+
+// Host-side fault injection (tests of the error paths; no device fault):
+// the armed site fails on its countdown-th use, once.
+static std::atomic<int> g_fault_site{0}, g_fault_countdown{0};
+
+// SPH_FAULT_INJECT=alloc:N or copy:N arms a site when the library loads.
+static const int g_fault_env = [] {
+    const char *e = getenv("SPH_FAULT_INJECT");
+    if (!e) return 0;
+    int site = 0;
+    if (!strncmp(e, "alloc:", 6)) site = SPH_FAULT_DEVICE_ALLOC;
+    else if (!strncmp(e, "copy:", 5)) site = SPH_FAULT_COPY;
+    const int n = site ? atoi(strchr(e, ':') + 1) : 0;
+    if (site && n > 0) {
+        g_fault_countdown.store(n);
+        g_fault_site.store(site);
+    } else {
+        fprintf(stderr, "libsph: SPH_FAULT_INJECT=%s not understood (alloc:N or copy:N)\n", e);
+    }
+    return site;
+}();
+
+static bool fault_fires(int site) {
+    if (g_fault_site.load() != site) return false;
+    if (g_fault_countdown.fetch_sub(1) != 1) return false;
+    g_fault_site.store(0);
+    return true;
+}
+
+// Device allocation and upload of plan metadata, failing where injected.
+static int upload_meta(void **dst, const void *src, size_t bytes, const char *what) {
+    if (bytes == 0) return SPH_OK;
+    if (fault_fires(SPH_FAULT_DEVICE_ALLOC) || cudaMalloc(dst, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *dst = nullptr;
+        return fail(SPH_ENOMEM, "device allocation of %s (%zu bytes)", what, bytes);
+    }
+    if (fault_fires(SPH_FAULT_COPY))
+        return fail(SPH_ECUDA, "%s: injected copy failure", what);
+    if (!src) return cuda_check(cudaMemset(*dst, 0, bytes), what);
+    return cuda_check(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), what);
 }
 
 // Store address of (field, comp); every field exists in every layout.
@@ -370,12 +413,7 @@ int sph_tasks_upload(sph_tasks t) {
     free_device(t);
     int rc;
     auto up = [&](void **dst, const void *src, size_t bytes, const char *what) -> int {
-        if (bytes == 0) return SPH_OK;
-        if (cudaMalloc(dst, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(SPH_ENOMEM, "device allocation of %s (%zu bytes)", what, bytes);
-        }
-        return cuda_check(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), what);
+        return upload_meta(dst, src, bytes, what);
     };
     if ((rc = up((void **)&t->d_tasks, t->tdev.data(), t->tdev.size() * sizeof(TaskDev),
                  "tasks")) ||
@@ -870,13 +908,7 @@ static void batch_free(sph_batch b) {
 // Copy a built plan to the current device; frees and deletes it on failure.
 static int batch_upload(sph_batch b, int rc, sph_batch *out) {
     auto up = [&](void **dst, const void *src, size_t bytes, const char *what) -> int {
-        if (bytes == 0) return SPH_OK;
-        if (cudaMalloc(dst, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(SPH_ENOMEM, "device allocation of %s (%zu bytes)", what, bytes);
-        }
-        if (!src) return cuda_check(cudaMemset(*dst, 0, bytes), what);
-        return cuda_check(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), what);
+        return upload_meta(dst, src, bytes, what);
     };
     if (rc == SPH_OK &&
         ((rc = up((void **)&b->d_cells, b->cells.data(), b->cells.size() * sizeof(BCellDev),
@@ -1507,5 +1539,13 @@ int sph_batch_offload_loop_host(sph_store s, sph_batch b, int loop, void *const 
         if (done[k]) cudaEventDestroy(done[k]);
     if (rc == SPH_OK && loop == SPH_DENSITY) rc = sph_ghost_host(s, SPH_DENSITY, p, nthreads);
     return rc;
+}
+
+int sph_fault_inject(int site, int countdown) {
+    if (site < 0 || site > SPH_FAULT_COPY || countdown < 0)
+        return fail(SPH_EINVAL, "fault_inject: unknown site or negative countdown");
+    g_fault_countdown.store(countdown);
+    g_fault_site.store(countdown > 0 ? site : 0);
+    return SPH_OK;
 }
 }  // extern "C"

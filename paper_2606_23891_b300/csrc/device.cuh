@@ -56,61 +56,6 @@ __device__ __forceinline__ void split_f64(double x, float &hi, float &lo) {
     lo = l;
 }
 
-// ---- TMA bulk copies and mbarriers (inline PTX, sm_90+) ------------------
-__device__ __forceinline__ unsigned int smem_u32(const void *p) {
-    return (unsigned int)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned int count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-// make the initialised barrier visible to the async (TMA) proxy
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// order this thread's earlier generic-proxy shared accesses before later
-// async-proxy (TMA) writes to the same shared memory
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned int bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-// 1-D bulk copy global -> shared, completion counted on `bar` (16-byte
-// aligned addresses, size a multiple of 16)
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned int bytes,
-                                         unsigned long long *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned int parity) {
-    unsigned int ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Wait for phase `parity` of `bar` for at most `limit` clock cycles; false on
-// timeout (the caller latches an error and leaves instead of hanging).
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned int parity,
-                                                  long long limit) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > limit) return false;
-    return true;
-}
-
 // Cubic spline shape w(q) and its derivative, for q < 1 (callers mask q >= 1).
 __device__ __forceinline__ void spline(float q, float &w, float &dw) {
     const float t = 1.f - q;

@@ -485,6 +485,7 @@ class HostOffload:
         self.nthreads = nthreads
         self.gpu = gpu
         self.plan = plan
+        self.seed, self.box, self.leaf_max = seed, tuple(float(b) for b in box), leaf_max
         x = np.ascontiguousarray(fields["x"], np.float64)
         h = np.ascontiguousarray(fields["h"], np.float32)
         self.n = n = x.shape[0]

@@ -102,6 +102,7 @@ def lib() -> C.CDLL:
         "sph_store_import": (i, [p, p, p, p]),
         "sph_store_export": (i, [p, p, p, p]),
         "sph_store_convert": (i, [p, p, p]),
+        "sph_fault_inject": (i, [i, i]),
         "sph_pack_host_fission": (i, [p, p, i, i, p, i, i]),
         "sph_unpack_host_fission": (i, [p, p, i, i, p, i, i]),
         "sph_tasks_build": (i, [i64, p, p, p, p, p]),
@@ -221,6 +222,13 @@ def sph_pack_host_fission(s, t, loop: int, bundle: int, host_buf: int, fission: 
 def sph_unpack_host_fission(s, t, loop: int, bundle: int, host_buf: int, fission: int,
                             nthreads: int = 0) -> None:
     _ok(lib().sph_unpack_host_fission(s, t, loop, bundle, host_buf, fission, nthreads))
+
+
+SPH_FAULT_NONE, SPH_FAULT_DEVICE_ALLOC, SPH_FAULT_COPY = 0, 1, 2
+
+
+def sph_fault_inject(site: int, countdown: int) -> None:
+    _ok(lib().sph_fault_inject(site, countdown))
 
 
 def sph_store_convert(dst, src, stream: int = 0) -> None:
