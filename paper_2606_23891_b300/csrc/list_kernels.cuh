@@ -18,7 +18,7 @@
 //           places in the pool vary, so results are reproducible.
 // k_bloop   persistent warps over the items again: each lane walks its list,
 //           gathers the j records of the loop's view from the bundle buffer
-//           (read-only path), applies the periodic image shift (decided from
+//           (read-only path, the list loads running ahead), applies the periodic image shift (decided from
 //           the hi-part separation: supports are below half the box, so the
 //           image is unique) as an exact two-float add, and runs the pair body.
 //           Lanes' lists differ in length by the neighbour-count scatter only.
@@ -339,9 +339,10 @@ struct AccL<SPH_FORCE> {
 };
 
 // Resident threads per SM the list loops are compiled for (measured at
-// Gresho256: density and gradient gain from 48 warps per SM at 40 registers,
-// the force body needs its 61 registers and runs best at 32 warps).
-constexpr int kLLoopMinThreads[3] = {1536, 1536, 1024};
+// Gresho256: density and gradient gain from 48 warps per SM at 40 registers;
+// the force loop, with its j record prefetched, runs best at 28 warps and
+// 72 registers).
+constexpr int kLLoopMinThreads[3] = {1536, 1536, 896};
 template <int LOOP, int T>
 __global__ void __launch_bounds__(T, kLLoopMinThreads[LOOP] / T)
     k_bloop(BInteractArgs a, ListView L, long long item0) {
@@ -380,32 +381,70 @@ __global__ void __launch_bounds__(T, kLLoopMinThreads[LOOP] / T)
         const int cnt = valid && active && !broken ? (int)L.lcount[gitem * 32 + lane] : 0;
         const int maxc = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
         uint32_t chunk = L.first[gitem];
-#pragma unroll 1
-        for (int k = 0; k < maxc; ++k) {
-            if (k > 0 && k % kLPer == 0) chunk = L.next[chunk];
-            if (k >= cnt) continue;
-            const uint32_t ent = __ldg(&L.entries[(long long)chunk * kLChunk + (k % kLPer) * 32 + lane]);
-            if (LOOP != SPH_FORCE && !(ent & 0x80000000u)) continue;
-            const long long js = (long long)(ent & 0x7fffffffu);
-            float4 oth[nf];
+        int kl = 0;  // next list position to load
+        auto next_ent = [&]() -> uint32_t {
+            uint32_t e = 0u;
+            if (kl < cnt)
+                e = __ldg(&L.entries[(long long)chunk * kLChunk + (kl % kLPer) * 32 + lane]);
+            ++kl;
+            if (kl % kLPer == 0 && kl < maxc) chunk = L.next[chunk];
+            return e;
+        };
+        auto uses = [&](uint32_t e, int k) {
+            return k < cnt && (LOOP == SPH_FORCE || (e & 0x80000000u) != 0u);
+        };
+        auto gather = [&](float4 *o, uint32_t e) {
 #pragma unroll
-            for (int f = 0; f < nf; ++f) oth[f] = __ldg(&rec[f][js]);
+            for (int f = 0; f < nf; ++f) o[f] = __ldg(&rec[f][e & 0x7fffffffu]);
+        };
+        auto pair = [&](float4 *oth) {
             // periodic image: the hi-part separation exceeds half the box
-            {
-                const float ax = own[0].x - oth[0].x, ay = own[0].y - oth[0].y,
-                            az = own[0].z - oth[0].z;
-                if (ax > a.half[0]) add2(oth[0].x, oth[1].x, a.shift_hi[0], a.shift_lo[0]);
-                else if (ax < -a.half[0]) add2(oth[0].x, oth[1].x, -a.shift_hi[0], -a.shift_lo[0]);
-                if (ay > a.half[1]) add2(oth[0].y, oth[1].y, a.shift_hi[1], a.shift_lo[1]);
-                else if (ay < -a.half[1]) add2(oth[0].y, oth[1].y, -a.shift_hi[1], -a.shift_lo[1]);
-                if (az > a.half[2]) add2(oth[0].z, oth[1].z, a.shift_hi[2], a.shift_lo[2]);
-                else if (az < -a.half[2]) add2(oth[0].z, oth[1].z, -a.shift_hi[2], -a.shift_lo[2]);
-            }
+            const float ax = own[0].x - oth[0].x, ay = own[0].y - oth[0].y,
+                        az = own[0].z - oth[0].z;
+            if (ax > a.half[0]) add2(oth[0].x, oth[1].x, a.shift_hi[0], a.shift_lo[0]);
+            else if (ax < -a.half[0]) add2(oth[0].x, oth[1].x, -a.shift_hi[0], -a.shift_lo[0]);
+            if (ay > a.half[1]) add2(oth[0].y, oth[1].y, a.shift_hi[1], a.shift_lo[1]);
+            else if (ay < -a.half[1]) add2(oth[0].y, oth[1].y, -a.shift_hi[1], -a.shift_lo[1]);
+            if (az > a.half[2]) add2(oth[0].z, oth[1].z, a.shift_hi[2], a.shift_lo[2]);
+            else if (az < -a.half[2]) add2(oth[0].z, oth[1].z, -a.shift_hi[2], -a.shift_lo[2]);
             const float dx = (own[0].x - oth[0].x) + (own[1].x - oth[1].x);
             const float dy = (own[0].y - oth[0].y) + (own[1].y - oth[1].y);
             const float dz = (own[0].z - oth[0].z) + (own[1].z - oth[1].z);
             const float r2 = dx * dx + dy * dy + dz * dz;
             acc.body(own, oth, dx, dy, dz, r2, a.pa);
+        };
+        // The entry loads run ahead of the gathers they feed: one list
+        // position ahead in the density and gradient loops; in the force loop
+        // the entries run two ahead and the j record one ahead, which the
+        // force body's registers leave room for at 28 warps per SM.
+        if constexpr (LOOP == SPH_FORCE) {
+            uint32_t e = next_ent();
+            float4 nxt[nf];
+            bool un = uses(e, 0);
+            if (un) gather(nxt, e);
+            e = next_ent();
+#pragma unroll 1
+            for (int k = 0; k < maxc; ++k) {
+                float4 oth[nf];
+#pragma unroll
+                for (int f = 0; f < nf; ++f) oth[f] = nxt[f];
+                const bool u = un;
+                un = uses(e, k + 1);
+                if (un) gather(nxt, e);
+                e = next_ent();
+                if (u) pair(oth);
+            }
+        } else {
+            uint32_t e = next_ent();
+#pragma unroll 1
+            for (int k = 0; k < maxc; ++k) {
+                const uint32_t cur = e;
+                e = next_ent();
+                if (!uses(cur, k)) continue;
+                float4 oth[nf];
+                gather(oth, cur);
+                pair(oth);
+            }
         }
         if (valid) {
             if constexpr (LOOP == SPH_DENSITY) {
