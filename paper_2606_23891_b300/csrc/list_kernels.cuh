@@ -401,12 +401,15 @@ __global__ void __launch_bounds__(T, kLLoopMinThreads[LOOP] / T)
             // periodic image: the hi-part separation exceeds half the box
             const float ax = own[0].x - oth[0].x, ay = own[0].y - oth[0].y,
                         az = own[0].z - oth[0].z;
-            if (ax > a.half[0]) add2(oth[0].x, oth[1].x, a.shift_hi[0], a.shift_lo[0]);
-            else if (ax < -a.half[0]) add2(oth[0].x, oth[1].x, -a.shift_hi[0], -a.shift_lo[0]);
-            if (ay > a.half[1]) add2(oth[0].y, oth[1].y, a.shift_hi[1], a.shift_lo[1]);
-            else if (ay < -a.half[1]) add2(oth[0].y, oth[1].y, -a.shift_hi[1], -a.shift_lo[1]);
-            if (az > a.half[2]) add2(oth[0].z, oth[1].z, a.shift_hi[2], a.shift_lo[2]);
-            else if (az < -a.half[2]) add2(oth[0].z, oth[1].z, -a.shift_hi[2], -a.shift_lo[2]);
+            // (one test on the common path; the shift itself is rare)
+            if (fabsf(ax) > a.half[0] || fabsf(ay) > a.half[1] || fabsf(az) > a.half[2]) {
+                if (ax > a.half[0]) add2(oth[0].x, oth[1].x, a.shift_hi[0], a.shift_lo[0]);
+                else if (ax < -a.half[0]) add2(oth[0].x, oth[1].x, -a.shift_hi[0], -a.shift_lo[0]);
+                if (ay > a.half[1]) add2(oth[0].y, oth[1].y, a.shift_hi[1], a.shift_lo[1]);
+                else if (ay < -a.half[1]) add2(oth[0].y, oth[1].y, -a.shift_hi[1], -a.shift_lo[1]);
+                if (az > a.half[2]) add2(oth[0].z, oth[1].z, a.shift_hi[2], a.shift_lo[2]);
+                else if (az < -a.half[2]) add2(oth[0].z, oth[1].z, -a.shift_hi[2], -a.shift_lo[2]);
+            }
             const float dx = (own[0].x - oth[0].x) + (own[1].x - oth[1].x);
             const float dy = (own[0].y - oth[0].y) + (own[1].y - oth[1].y);
             const float dz = (own[0].z - oth[0].z) + (own[1].z - oth[1].z);
