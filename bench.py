@@ -259,22 +259,21 @@ class StepTimer:
         return e
 
     def step(self, record: bool):
+        """The stages of one step.  The batched and list pipelines write each
+        particle's result in their unpack (no init pass); the list pipeline
+        builds each bundle's lists from the density loop's pack."""
         from paper_2606_23891_b300 import sph
         off = self.off
         lists = self.pipeline == "list"
         batched = self.pipeline in ("batched", "list")
         nb = off.binfo["nbundles"] if batched else off.nbundles()
         st = off.stream
-        if lists:
-            e0 = self.ev() if record else None
-            off.list_build()
-            e1 = self.ev() if record else None
-            self.launches += 2 * nb
-            if record:
-                self.recs.append((-1, e0, e1, e1, e1))
+        if lists and getattr(off, "blist", None) is None:
+            off.list_build()            # sizes the list pool (first step only)
         for loop in range(3):
-            sph.sph_init(off.store, loop, off.params, st)
-            self.launches += 1
+            if not batched:
+                sph.sph_init(off.store, loop, off.params, st)
+                self.launches += 1
             for b in range(nb):
                 e0 = self.ev() if record else None
                 if lists:
@@ -286,6 +285,13 @@ class StepTimer:
                 else:
                     off.pack(loop, b)
                 e1 = self.ev() if record else None
+                e1b = e1
+                if lists and loop == 0:
+                    sph.sph_batch_list_build_bundle(off.store, off.bplan, b,
+                                                    off.bbuf_in.data_ptr(), off.blist.data_ptr(),
+                                                    off.blist_bytes, off.params, st)
+                    self.launches += 1
+                    e1b = self.ev() if record else None
                 if lists:
                     sph.sph_batch_list_interact(off.bplan, loop, b, off.bbuf_in.data_ptr(),
                                                 off.bbuf_out.data_ptr(), off.blist.data_ptr(),
@@ -297,14 +303,15 @@ class StepTimer:
                     off.interact(loop, b)
                 e2 = self.ev() if record else None
                 if batched:
-                    sph.sph_batch_unpack(off.store, off.bplan, loop, b, off.bbuf_out.data_ptr(),
-                                         off.bbuf_in.data_ptr(), st)
+                    sph.sph_batch_unpack_write(off.store, off.bplan, loop, b,
+                                               off.bbuf_out.data_ptr(), off.bbuf_in.data_ptr(),
+                                               off.params, st)
                 else:
                     off.unpack(loop, b)
                 e3 = self.ev() if record else None
                 self.launches += 3
                 if record:
-                    self.recs.append((loop, e0, e1, e2, e3))
+                    self.recs.append((loop, e0, e1, e1b, e2, e3))
             if loop == 0:
                 sph.sph_ghost(off.store, 0, off.params, st)
                 self.launches += 1
@@ -312,12 +319,11 @@ class StepTimer:
     def stage_ms(self):
         out = {(s, l): 0.0 for s in ("pack", "kernel", "unpack") for l in range(3)}
         cnt = {l: 0 for l in range(3)}
-        for loop, e0, e1, e2, e3 in self.recs:
-            if loop < 0:        # neighbour-list build (once per step, all bundles)
-                out[("list", 0)] = out.get(("list", 0), 0.0) + e0.elapsed_time(e1)
-                continue
+        for loop, e0, e1, e1b, e2, e3 in self.recs:
             out[("pack", loop)] += e0.elapsed_time(e1)
-            out[("kernel", loop)] += e1.elapsed_time(e2)
+            if e1b is not e1:   # the bundle's list build, from the density pack
+                out[("list", 0)] = out.get(("list", 0), 0.0) + e1.elapsed_time(e1b)
+            out[("kernel", loop)] += e1b.elapsed_time(e2)
             out[("unpack", loop)] += e2.elapsed_time(e3)
             cnt[loop] += 1
         return out, cnt

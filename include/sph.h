@@ -395,11 +395,23 @@ int sph_batch_pack(sph_store s, sph_batch b, int loop, int bundle, void *dev_buf
                    const sph_params *p, void *stream);
 int sph_batch_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in,
                        void *dev_buf_out, const sph_params *p, void *stream);
+/* Adds each target particle's result of one bundle into the store (maxima
+ * for the signal velocities), as the per-task unpack does; the store's
+ * outputs of the loop must be initialised (sph_init) before the first
+ * bundle. */
 int sph_batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const void *dev_buf_out,
                      const void *dev_buf_in, void *stream);
-/* init, then per bundle pack -> interact -> unpack, then the ghost after
- * density; enqueues only (no host synchronisation), so it can be recorded
- * into a CUDA graph after a first call. */
+/* The same result without sph_init: each target particle's outputs are
+ * written as the fold onto an initialised store would leave them (0 + v,
+ * max(0, v); inactive particles of the force loop keep theirs).  Valid
+ * because a batched plan holds every particle's cell as a target in exactly
+ * one bundle, so one bundle's result is the particle's whole sum. */
+int sph_batch_unpack_write(sph_store s, sph_batch b, int loop, int bundle,
+                           const void *dev_buf_out, const void *dev_buf_in, const sph_params *p,
+                           void *stream);
+/* Per bundle pack -> interact -> unpack (written, no init pass), then the
+ * ghost after density; enqueues only (no host synchronisation), so it can be
+ * recorded into a CUDA graph after a first call. */
 int sph_batch_offload_loop(sph_store s, sph_batch b, int loop, void *dev_buf_in,
                            void *dev_buf_out, const sph_params *p, void *stream);
 int sph_batch_destroy(sph_batch b);
@@ -471,6 +483,13 @@ int sph_batch_count_pairs(sph_store s, sph_batch b, int loop, void *dev_buf_in,
 size_t sph_batch_list_bytes(sph_batch b, int64_t chunks);
 int sph_batch_list_build(sph_store s, sph_batch b, void *dev_buf_in, void *dev_list,
                          size_t list_bytes, const sph_params *p, void *stream);
+/* One bundle's part of sph_batch_list_build, from a dev_buf_in that already
+ * holds this bundle's density pack (sph_batch_pack_list, loop 0), so the
+ * density loop's pack serves the build too.  Bundle 0 resets the list
+ * header: build the bundles of a step in order, 0 first. */
+int sph_batch_list_build_bundle(sph_store s, sph_batch b, int bundle, const void *dev_buf_in,
+                                void *dev_list, size_t list_bytes, const sph_params *p,
+                                void *stream);
 int sph_batch_list_status(const void *dev_list, int64_t *chunks_needed, int *overflow);
 /* The pack of the list loops: the density view as sph_batch_pack, the
  * gradient and force views as compact records (c and P recomputed in the
@@ -485,6 +504,15 @@ int sph_batch_list_interact(sph_batch b, int loop, int bundle, const void *dev_b
 int sph_batch_offload_loop_list(sph_store s, sph_batch b, int loop, void *dev_buf_in,
                                 void *dev_buf_out, const void *dev_list, size_t list_bytes,
                                 const sph_params *p, void *stream);
+/* A whole step of the list cycle in one call: per bundle the density pack,
+ * that bundle's list build from it, the density list loop and its unpack;
+ * the ghost; then the gradient and force loops as sph_batch_offload_loop_list.
+ * Enqueues only.  A list pool that runs out is reported by sph_sync
+ * (SPH_ENOMEM) and sph_batch_list_status, as for sph_batch_list_build; the
+ * step's loops then skip all pairs. */
+int sph_batch_offload_step_list(sph_store s, sph_batch b, void *dev_buf_in, void *dev_buf_out,
+                                void *dev_list, size_t list_bytes, const sph_params *p,
+                                void *stream);
 
 /* Host-staged batched cycle: a host store (sph_store_create_host, in the
  * plan's particle order) and a batch plan; per bundle, host threads pack
@@ -509,7 +537,8 @@ int sph_batch_offload_loop_host(sph_store s, sph_batch b, int loop, void *const 
  * identity).  Smoothing lengths, velocities and the switches' coefficients
  * are held fixed.  Preconditions: a plan of one bundle, the store holding the
  * results of the list cycle (sph_batch_list_build then the three
- * sph_batch_offload_loop_list calls) on the current inputs, and that list
+ * sph_batch_offload_loop_list calls, or sph_batch_offload_step_list) on the
+ * current inputs, and that list
  * buffer.  Scratch: sph_batch_adjoint_bytes(b) bytes (0 when the plan has
  * more than one bundle).  Every particle gathers both directions of its
  * pairs from its list: no atomics, deterministic.  FP32 arithmetic. */

@@ -1113,8 +1113,8 @@ int sph_batch_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in
     return dispatch_binteract<SPH_FORCE>(b->threads, a, st);
 }
 
-int sph_batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const void *dev_buf_out,
-                     const void *dev_buf_in, void *stream) {
+static int batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const void *dev_buf_out,
+                        const void *dev_buf_in, bool write, int active_bin, void *stream) {
     if (int rc = check_store(s)) return rc;
     if (int rc = check_batch(b, bundle)) return rc;
     if (int rc = check_loop(loop)) return rc;
@@ -1129,6 +1129,8 @@ int sph_batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const void 
                        : loop == SPH_GRADIENT ? BLayout<SPH_GRADIENT>::perm(S)
                                               : BLayout<SPH_FORCE>::perm(S);
     a.perm = reinterpret_cast<const int32_t *>((const char *)dev_buf_in + perm_off);
+    a.tb = reinterpret_cast<const int8_t *>((const char *)dev_buf_in + BLayout<SPH_FORCE>::tb(S));
+    a.active_bin = active_bin;
     a.S = S;
     int k = 0;
     if (loop == SPH_DENSITY) {
@@ -1144,20 +1146,41 @@ int sph_batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const void 
     if (bb.ntargets == 0) return SPH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const unsigned g = (unsigned)bb.ntargets;
-    if (loop == SPH_DENSITY) k_bunpack<SPH_DENSITY><<<g, 128, 0, st>>>(a);
-    else if (loop == SPH_GRADIENT) k_bunpack<SPH_GRADIENT><<<g, 128, 0, st>>>(a);
-    else k_bunpack<SPH_FORCE><<<g, 128, 0, st>>>(a);
+    if (write) {
+        if (loop == SPH_DENSITY) k_bunpack<SPH_DENSITY, true><<<g, 128, 0, st>>>(a);
+        else if (loop == SPH_GRADIENT) k_bunpack<SPH_GRADIENT, true><<<g, 128, 0, st>>>(a);
+        else k_bunpack<SPH_FORCE, true><<<g, 128, 0, st>>>(a);
+    } else {
+        if (loop == SPH_DENSITY) k_bunpack<SPH_DENSITY><<<g, 128, 0, st>>>(a);
+        else if (loop == SPH_GRADIENT) k_bunpack<SPH_GRADIENT><<<g, 128, 0, st>>>(a);
+        else k_bunpack<SPH_FORCE><<<g, 128, 0, st>>>(a);
+    }
     return launch_check("batch unpack");
+}
+
+int sph_batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const void *dev_buf_out,
+                     const void *dev_buf_in, void *stream) {
+    return batch_unpack(s, b, loop, bundle, dev_buf_out, dev_buf_in, false, 0, stream);
+}
+
+int sph_batch_unpack_write(sph_store s, sph_batch b, int loop, int bundle,
+                           const void *dev_buf_out, const void *dev_buf_in, const sph_params *p,
+                           void *stream) {
+    if (int rc = check_params(p)) return rc;
+    return batch_unpack(s, b, loop, bundle, dev_buf_out, dev_buf_in, true, p->active_bin, stream);
 }
 
 int sph_batch_offload_loop(sph_store s, sph_batch b, int loop, void *dev_buf_in,
                            void *dev_buf_out, const sph_params *p, void *stream) {
-    if (int rc = sph_init(s, loop, p, stream)) return rc;
+    if (int rc = check_store(s)) return rc;
     if (!b) return fail(SPH_EINVAL, "NULL batch handle");
+    if (int rc = check_loop(loop)) return rc;
+    if (int rc = check_params(p)) return rc;
     for (int k = 0; k < (int)b->bundles.size(); ++k) {
         if (int rc = sph_batch_pack(s, b, loop, k, dev_buf_in, p, stream)) return rc;
         if (int rc = sph_batch_interact(b, loop, k, dev_buf_in, dev_buf_out, p, stream)) return rc;
-        if (int rc = sph_batch_unpack(s, b, loop, k, dev_buf_out, dev_buf_in, stream)) return rc;
+        if (int rc = sph_batch_unpack_write(s, b, loop, k, dev_buf_out, dev_buf_in, p, stream))
+            return rc;
     }
     return sph_ghost(s, loop, p, stream);
 }
@@ -1310,21 +1333,40 @@ int sph_batch_list_build(sph_store s, sph_batch b, void *dev_buf_in, void *dev_l
     const int64_t NI = (int64_t)b->items.size();
     if ((int64_t)list_bytes < ListLayout::fixed(NI) + 512)
         return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
-    cudaStream_t st = (cudaStream_t)stream;
-    ListView L = ListLayout::view(dev_list, NI, (int64_t)list_bytes);
-    if (int rc = cuda_check(cudaMemsetAsync(L.hdr, 0, sizeof(ListHdr), st), "reset list header"))
-        return rc;
     for (int k = 0; k < (int)b->bundles.size(); ++k) {
-        const BatchBundle &bb = b->bundles[k];
-        if (bb.nitems == 0) continue;
         if (int rc = sph_batch_pack(s, b, SPH_DENSITY, k, dev_buf_in, p, stream)) return rc;
-        BInteractArgs a = interact_args(b, k, dev_buf_in, nullptr, p);
-        if (int rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st),
-                                "reset work queue"))
+        if (int rc = sph_batch_list_build_bundle(s, b, k, dev_buf_in, dev_list, list_bytes, p,
+                                                 stream))
             return rc;
-        if (int rc = dispatch_blist(b->threads, a, L, bb.item0, st)) return rc;
     }
     return SPH_OK;
+}
+
+int sph_batch_list_build_bundle(sph_store s, sph_batch b, int bundle, const void *dev_buf_in,
+                                void *dev_list, size_t list_bytes, const sph_params *p,
+                                void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (int rc = check_batch(b, bundle)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (s->n != b->n) return fail(SPH_EINVAL, "store and batch disagree on particle count");
+    if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_list || !aligned256(dev_list))
+        return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
+    const int64_t NI = (int64_t)b->items.size();
+    if ((int64_t)list_bytes < ListLayout::fixed(NI) + 512)
+        return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
+    cudaStream_t st = (cudaStream_t)stream;
+    ListView L = ListLayout::view(dev_list, NI, (int64_t)list_bytes);
+    if (bundle == 0)
+        if (int rc = cuda_check(cudaMemsetAsync(L.hdr, 0, sizeof(ListHdr), st),
+                                "reset list header"))
+            return rc;
+    const BatchBundle &bb = b->bundles[bundle];
+    if (bb.nitems == 0) return SPH_OK;
+    BInteractArgs a = interact_args(b, bundle, dev_buf_in, nullptr, p);
+    if (int rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st),
+                            "reset work queue"))
+        return rc;
+    return dispatch_blist(b->threads, a, L, bb.item0, st);
 }
 
 int sph_batch_list_status(const void *dev_list, int64_t *chunks_needed, int *overflow) {
@@ -1376,15 +1418,47 @@ int sph_batch_offload_loop_list(sph_store s, sph_batch b, int loop, void *dev_bu
         return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
     if ((int64_t)list_bytes < ListLayout::fixed((int64_t)b->items.size()) + 512)
         return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
-    if (int rc = sph_init(s, loop, p, stream)) return rc;
     for (int k = 0; k < (int)b->bundles.size(); ++k) {
         if (int rc = sph_batch_pack_list(s, b, loop, k, dev_buf_in, p, stream)) return rc;
         if (int rc = sph_batch_list_interact(b, loop, k, dev_buf_in, dev_buf_out, dev_list,
                                              list_bytes, p, stream))
             return rc;
-        if (int rc = sph_batch_unpack(s, b, loop, k, dev_buf_out, dev_buf_in, stream)) return rc;
+        if (int rc = sph_batch_unpack_write(s, b, loop, k, dev_buf_out, dev_buf_in, p, stream))
+            return rc;
     }
     return sph_ghost(s, loop, p, stream);
+}
+
+int sph_batch_offload_step_list(sph_store s, sph_batch b, void *dev_buf_in, void *dev_buf_out,
+                                void *dev_list, size_t list_bytes, const sph_params *p,
+                                void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (!b) return fail(SPH_EINVAL, "NULL batch handle");
+    if (int rc = check_params(p)) return rc;
+    if (s->n != b->n) return fail(SPH_EINVAL, "store and batch disagree on particle count");
+    if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_buf_out || !aligned256(dev_buf_out) ||
+        !dev_list || !aligned256(dev_list))
+        return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
+    if ((int64_t)list_bytes < ListLayout::fixed((int64_t)b->items.size()) + 512)
+        return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
+    for (int k = 0; k < (int)b->bundles.size(); ++k) {
+        if (int rc = sph_batch_pack_list(s, b, SPH_DENSITY, k, dev_buf_in, p, stream)) return rc;
+        if (int rc = sph_batch_list_build_bundle(s, b, k, dev_buf_in, dev_list, list_bytes, p,
+                                                 stream))
+            return rc;
+        if (int rc = sph_batch_list_interact(b, SPH_DENSITY, k, dev_buf_in, dev_buf_out,
+                                             dev_list, list_bytes, p, stream))
+            return rc;
+        if (int rc = sph_batch_unpack_write(s, b, SPH_DENSITY, k, dev_buf_out, dev_buf_in, p,
+                                            stream))
+            return rc;
+    }
+    if (int rc = sph_ghost(s, SPH_DENSITY, p, stream)) return rc;
+    for (int loop : {SPH_GRADIENT, SPH_FORCE})
+        if (int rc = sph_batch_offload_loop_list(s, b, loop, dev_buf_in, dev_buf_out, dev_list,
+                                                 list_bytes, p, stream))
+            return rc;
+    return SPH_OK;
 }
 
 

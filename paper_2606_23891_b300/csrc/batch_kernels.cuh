@@ -456,36 +456,45 @@ struct BUnpackArgs {
     const BTargetDev *targets;
     const char *out;
     const int32_t *perm;
+    const int8_t *tb;   // force, WRITE: the pack's time-bin lane
+    int active_bin;
     long long S;
     CompPtr dst[8];
 };
 
-// One CTA per target cell: add each particle's result into the store (the
-// single-term case of the per-task fold; maxima for signal velocities).
-template <int LOOP>
+// One CTA per target cell.  Default: add each particle's result into the
+// store (the single-term case of the per-task fold; maxima for signal
+// velocities).  WRITE: store the result as that fold does onto a freshly
+// initialised store (0 + v, max(0, v)), so no initialisation pass is needed:
+// a batched plan gives every particle all its pairs in the one bundle that
+// holds its cell as a target.  Inactive particles keep their force outputs,
+// as the initialisation would have left them.
+template <int LOOP, bool WRITE = false>
 __global__ void __launch_bounds__(128) k_bunpack(BUnpackArgs a) {
     const BCellDev C = a.cells[a.targets[blockIdx.x].cell];
     const long long r16 = (a.S * 16 + 255) / 256 * 256;
     for (int k = threadIdx.x; k < C.n; k += blockDim.x) {
         const long long sl = (long long)C.slot + k;
         const long long p = a.perm[sl];
+        auto base = [&](const CompPtr &d) { return WRITE ? 0.f : ld<float>(d, p); };
         if constexpr (LOOP == SPH_DENSITY) {
             const float4 o0 = reinterpret_cast<const float4 *>(a.out)[sl];
             const float4 o1 = reinterpret_cast<const float4 *>(a.out + r16)[sl];
             const float v[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
 #pragma unroll
-            for (int q = 0; q < 8; ++q) st<float>(a.dst[q], p, ld<float>(a.dst[q], p) + v[q]);
+            for (int q = 0; q < 8; ++q) st<float>(a.dst[q], p, base(a.dst[q]) + v[q]);
         } else if constexpr (LOOP == SPH_GRADIENT) {
             const float2 o = reinterpret_cast<const float2 *>(a.out)[sl];
-            st<float>(a.dst[0], p, fmaxf(ld<float>(a.dst[0], p), o.x));
-            st<float>(a.dst[1], p, ld<float>(a.dst[1], p) + o.y);
+            st<float>(a.dst[0], p, fmaxf(base(a.dst[0]), o.x));
+            st<float>(a.dst[1], p, base(a.dst[1]) + o.y);
         } else {
+            if (WRITE && (int)a.tb[sl] > a.active_bin) continue;
             const float4 o0 = reinterpret_cast<const float4 *>(a.out)[sl];
             const float2 o1 = reinterpret_cast<const float2 *>(a.out + r16)[sl];
             const float v[5] = {o0.x, o0.y, o0.z, o0.w, o1.x};
 #pragma unroll
-            for (int q = 0; q < 5; ++q) st<float>(a.dst[q], p, ld<float>(a.dst[q], p) + v[q]);
-            st<float>(a.dst[5], p, fmaxf(ld<float>(a.dst[5], p), o1.y));
+            for (int q = 0; q < 5; ++q) st<float>(a.dst[q], p, base(a.dst[q]) + v[q]);
+            st<float>(a.dst[5], p, fmaxf(base(a.dst[5]), o1.y));
         }
     }
 }

@@ -348,10 +348,14 @@ class Offload:
                                         self.blist_bytes, self.params, self.stream)
 
     def list_step(self) -> None:
-        """Lists, then density -> ghost -> gradient -> force over them."""
-        self.list_build()
-        for loop in (sph.SPH_DENSITY, sph.SPH_GRADIENT, sph.SPH_FORCE):
-            self.list_loop(loop)
+        """Lists, then density -> ghost -> gradient -> force over them, in one
+        library call (the density pack serves the list build too).  The first
+        call sizes the list pool with a separate build."""
+        if getattr(self, "blist", None) is None:
+            self.list_build()
+        sph.sph_batch_offload_step_list(self.store, self.bplan, self.bbuf_in.data_ptr(),
+                                        self.bbuf_out.data_ptr(), self.blist.data_ptr(),
+                                        self.blist_bytes, self.params, self.stream)
 
     def close_batch(self) -> None:
         self.f64_in = self.f64_out = None

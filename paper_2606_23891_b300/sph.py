@@ -128,6 +128,7 @@ def lib() -> C.CDLL:
         "sph_batch_pack_list": (i, [p, p, i, i, p, p, p]),
         "sph_batch_interact": (i, [p, i, i, p, p, p, p]),
         "sph_batch_unpack": (i, [p, p, i, i, p, p, p]),
+        "sph_batch_unpack_write": (i, [p, p, i, i, p, p, p, p]),
         "sph_batch_offload_loop": (i, [p, p, i, p, p, p, p]),
         "sph_batch_destroy": (i, [p]),
         "sph_batch_buffer_bytes_fp64": (sz, [p, i]),
@@ -135,8 +136,10 @@ def lib() -> C.CDLL:
         "sph_batch_plan_info": (i, [p, p]),
         "sph_batch_list_bytes": (sz, [p, i64]),
         "sph_batch_list_build": (i, [p, p, p, p, sz, p, p]),
+        "sph_batch_list_build_bundle": (i, [p, p, i, p, p, sz, p, p]),
         "sph_batch_list_status": (i, [p, p, p]),
         "sph_batch_offload_loop_list": (i, [p, p, i, p, p, p, sz, p, p]),
+        "sph_batch_offload_step_list": (i, [p, p, p, p, p, sz, p, p]),
         "sph_batch_list_interact": (i, [p, i, i, p, p, p, sz, p, p]),
         "sph_batch_adjoint_bytes": (sz, [p]),
         "sph_batch_offload_loop_host": (i, [p, p, i, p, p, p, p, p, p, i]),
@@ -418,6 +421,12 @@ def sph_batch_list_build(s, b, dev_in: int, dev_list: int, list_bytes: int, p: P
     _ok(lib().sph_batch_list_build(s, b, dev_in, dev_list, list_bytes, C.byref(p), stream))
 
 
+def sph_batch_list_build_bundle(s, b, bundle: int, dev_in: int, dev_list: int,
+                                list_bytes: int, p: Params, stream: int = 0):
+    _ok(lib().sph_batch_list_build_bundle(s, b, bundle, dev_in, dev_list, list_bytes,
+                                          C.byref(p), stream))
+
+
 def sph_batch_list_status(dev_list: int):
     need, ovf = C.c_int64(), C.c_int()
     _ok(lib().sph_batch_list_status(dev_list, C.byref(need), C.byref(ovf)))
@@ -460,6 +469,12 @@ def sph_batch_offload_loop_list(s, b, loop: int, dev_in: int, dev_out: int, dev_
                                           C.byref(p), stream))
 
 
+def sph_batch_offload_step_list(s, b, dev_in: int, dev_out: int, dev_list: int,
+                                list_bytes: int, p: Params, stream: int = 0):
+    _ok(lib().sph_batch_offload_step_list(s, b, dev_in, dev_out, dev_list, list_bytes,
+                                          C.byref(p), stream))
+
+
 def sph_batch_info(b) -> dict:
     info = (C.c_int64 * 6)()
     _ok(lib().sph_batch_info(b, info))
@@ -482,6 +497,11 @@ def sph_batch_interact(b, loop: int, bundle: int, dev_in: int, dev_out: int, p: 
 
 def sph_batch_unpack(s, b, loop: int, bundle: int, dev_out: int, dev_in: int, stream: int = 0):
     _ok(lib().sph_batch_unpack(s, b, loop, bundle, dev_out, dev_in, stream))
+
+
+def sph_batch_unpack_write(s, b, loop: int, bundle: int, dev_out: int, dev_in: int, p: Params,
+                           stream: int = 0):
+    _ok(lib().sph_batch_unpack_write(s, b, loop, bundle, dev_out, dev_in, C.byref(p), stream))
 
 
 def sph_batch_offload_loop(s, b, loop: int, dev_in: int, dev_out: int, p: Params,

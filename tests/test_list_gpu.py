@@ -169,3 +169,110 @@ def test_list_and_batch_api_reject_misuse():
     off.list_step()
     for k, v in off.export().items():
         np.testing.assert_array_equal(v, a[k])
+
+
+def _poisoned_outputs(f, seed):
+    """Random values in every output field, so that a field the step should
+    leave alone (inactive particles) shows if it was written."""
+    from paper_2606_23891_b300.pipeline import OUTPUTS, field_spec
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = {}
+    for k in OUTPUTS:
+        dt, c = field_spec(k)
+        shape = (len(f["x"]), c) if c > 1 else (len(f["x"]),)
+        lo = 0.0 if k.startswith("v_sig") else -3.0     # signal velocities are >= 0
+        out[k] = rng.uniform(lo, 3.0, shape).astype(dt)
+    return out
+
+
+@pytest.mark.parametrize("plan, mtc", [("grid", 0), ("grid", 37), ("tree", 101)])
+def test_written_unpack_equals_init_then_fold(plan, mtc):
+    """The unpack that writes each particle's result leaves the store byte for
+    byte as sph_init followed by the adding unpack does (the cycles' former
+    form), inactive particles of the force loop included; and the one-call
+    list step equals the build followed by the three loop calls."""
+    f = ics.lognormal(n_side=20, seed=44) if plan == "tree" else ragged(14, 46)
+    f["time_bin"] = (np.arange(len(f["x"])) % 3).astype(np.int8)
+    prm = sph.params(active_bin=1)
+    poison = _poisoned_outputs(f, 9)
+    offs = []
+    for _ in range(3):
+        o = Offload(f, layout=6, plan=plan, params=prm)
+        o.batch(max_target_cells=mtc)
+        o.import_fields(poison, tuple(poison))
+        offs.append(o)
+    fold, loops, step = offs
+    # init + adding unpack, bundle by bundle
+    fold.list_build()
+    for loop in range(3):
+        sph.sph_init(fold.store, loop, prm, fold.stream)
+        for b in range(fold.binfo["nbundles"]):
+            sph.sph_batch_pack_list(fold.store, fold.bplan, loop, b, fold.bbuf_in.data_ptr(),
+                                    prm, fold.stream)
+            sph.sph_batch_list_interact(fold.bplan, loop, b, fold.bbuf_in.data_ptr(),
+                                        fold.bbuf_out.data_ptr(), fold.blist.data_ptr(),
+                                        fold.blist_bytes, prm, fold.stream)
+            sph.sph_batch_unpack(fold.store, fold.bplan, loop, b, fold.bbuf_out.data_ptr(),
+                                 fold.bbuf_in.data_ptr(), fold.stream)
+        sph.sph_ghost(fold.store, loop, prm, fold.stream)
+    # the build, then the three loop calls (written unpack)
+    loops.list_build()
+    for loop in range(3):
+        loops.list_loop(loop)
+    # the one-call step
+    step.list_step()
+    want = fold.store_bytes()
+    assert np.array_equal(loops.store_bytes(), want)
+    assert np.array_equal(step.store_bytes(), want)
+    got = step.export(("a", "u_dt", "v_sig"))
+    inactive = f["time_bin"] > 1
+    for k in got:
+        assert np.array_equal(got[k][inactive], poison[k][inactive]), k
+
+
+def test_written_unpack_in_the_tile_cycle_equals_init_then_fold():
+    f = ragged(14, 47)
+    f["time_bin"] = (np.arange(len(f["x"])) % 2).astype(np.int8)
+    prm = sph.params(active_bin=0)
+    poison = _poisoned_outputs(f, 10)
+    a = Offload(f, layout=2, params=prm)
+    b = Offload(f, layout=2, params=prm)
+    for o in (a, b):
+        o.batch(max_target_cells=29)
+        o.import_fields(poison, tuple(poison))
+    for loop in range(3):
+        sph.sph_init(a.store, loop, prm, a.stream)
+        for k in range(a.binfo["nbundles"]):
+            sph.sph_batch_pack(a.store, a.bplan, loop, k, a.bbuf_in.data_ptr(), prm, a.stream)
+            sph.sph_batch_interact(a.bplan, loop, k, a.bbuf_in.data_ptr(),
+                                   a.bbuf_out.data_ptr(), prm, a.stream)
+            sph.sph_batch_unpack(a.store, a.bplan, loop, k, a.bbuf_out.data_ptr(),
+                                 a.bbuf_in.data_ptr(), a.stream)
+        sph.sph_ghost(a.store, loop, prm, a.stream)
+    b.batch_step()
+    assert np.array_equal(b.store_bytes(), a.store_bytes())
+
+
+def test_one_call_step_rejects_misuse_before_any_work():
+    f = ragged(12, 54)
+    off = Offload(f, layout=0)
+    off.batch()
+    off.list_step()
+    before = off.store_bytes()
+    b, st, lb = off.bplan, off.stream, off.blist_bytes
+    with pytest.raises(sph.SphError):          # misaligned result buffer
+        sph.sph_batch_offload_step_list(off.store, b, off.bbuf_in.data_ptr(),
+                                        off.bbuf_out.data_ptr() + 4, off.blist.data_ptr(), lb,
+                                        off.params, st)
+    with pytest.raises(sph.SphError):          # list buffer below its fixed tables
+        sph.sph_batch_offload_step_list(off.store, b, off.bbuf_in.data_ptr(),
+                                        off.bbuf_out.data_ptr(), off.blist.data_ptr(), 512,
+                                        off.params, st)
+    with pytest.raises(sph.SphError):          # bundle out of range
+        sph.sph_batch_list_build_bundle(off.store, b, 1, off.bbuf_in.data_ptr(),
+                                        off.blist.data_ptr(), lb, off.params, st)
+    with pytest.raises(sph.SphError):          # unknown loop
+        sph.sph_batch_unpack_write(off.store, b, 3, 0, off.bbuf_out.data_ptr(),
+                                   off.bbuf_in.data_ptr(), off.params, st)
+    sph.sph_sync(st)
+    assert np.array_equal(off.store_bytes(), before)
