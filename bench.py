@@ -260,8 +260,9 @@ class StepTimer:
 
     def step(self, record: bool):
         """The stages of one step.  The batched and list pipelines write each
-        particle's result in their unpack (no init pass); the list pipeline
-        builds each bundle's lists from the density loop's pack."""
+        particle's result in their unpack (no init pass; the density unpack
+        applies the ghost); the list pipeline builds each bundle's lists from
+        the density loop's pack."""
         from paper_2606_23891_b300 import sph
         off = self.off
         lists = self.pipeline == "list"
@@ -302,17 +303,17 @@ class StepTimer:
                 else:
                     off.interact(loop, b)
                 e2 = self.ev() if record else None
-                if batched:
+                if batched:     # the density unpack applies the ghost too
                     sph.sph_batch_unpack_write(off.store, off.bplan, loop, b,
                                                off.bbuf_out.data_ptr(), off.bbuf_in.data_ptr(),
-                                               off.params, st)
+                                               off.params, int(loop == 0), st)
                 else:
                     off.unpack(loop, b)
                 e3 = self.ev() if record else None
                 self.launches += 3
                 if record:
                     self.recs.append((loop, e0, e1, e1b, e2, e3))
-            if loop == 0:
+            if loop == 0 and not batched:
                 sph.sph_ghost(off.store, 0, off.params, st)
                 self.launches += 1
 

@@ -403,15 +403,19 @@ int sph_batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const void 
                      const void *dev_buf_in, void *stream);
 /* The same result without sph_init: each target particle's outputs are
  * written as the fold onto an initialised store would leave them (0 + v,
- * max(0, v); inactive particles of the force loop keep theirs).  Valid
- * because a batched plan holds every particle's cell as a target in exactly
- * one bundle, so one bundle's result is the particle's whole sum. */
+ * max(0, v); inactive particles of the force loop keep theirs, which equals
+ * the fold for signal velocities >= 0).  Valid because a batched plan holds
+ * every particle's cell as a target in exactly one bundle, so one bundle's
+ * result is the particle's whole sum.  with_ghost != 0 (density loop only):
+ * the bundle's targets also get the ghost, bit for bit as sph_ghost after
+ * the last bundle would give, so no separate ghost pass is needed. */
 int sph_batch_unpack_write(sph_store s, sph_batch b, int loop, int bundle,
                            const void *dev_buf_out, const void *dev_buf_in, const sph_params *p,
-                           void *stream);
-/* Per bundle pack -> interact -> unpack (written, no init pass), then the
- * ghost after density; enqueues only (no host synchronisation), so it can be
- * recorded into a CUDA graph after a first call. */
+                           int with_ghost, void *stream);
+/* Per bundle pack -> interact -> unpack (written, no init pass; after the
+ * density loop with the ghost fused); enqueues only (no host
+ * synchronisation), so it can be recorded into a CUDA graph after a first
+ * call. */
 int sph_batch_offload_loop(sph_store s, sph_batch b, int loop, void *dev_buf_in,
                            void *dev_buf_out, const sph_params *p, void *stream);
 int sph_batch_destroy(sph_batch b);
@@ -471,7 +475,8 @@ int sph_batch_count_pairs(sph_store s, sph_batch b, int loop, void *dev_buf_in,
  * stores, for every target particle, the bundle slots of the j with
  * r < max(H_i, H_j) (flagged when r < H_i), decided exactly as the loops
  * decide; sph_batch_offload_loop_list then runs each loop over the lists
- * (pack -> list loop -> unpack per bundle, ghost after density).  Results
+ * (pack -> list loop -> unpack per bundle, the ghost fused into the
+ * density unpack).  Results
  * equal the batched cycle's up to the rounding order of r^2.
  * The list buffer (caller memory, 256-byte aligned) holds a header, per-item
  * tables and a pool of chunks of 2048 entries; sph_batch_list_bytes(b, c)
@@ -505,8 +510,9 @@ int sph_batch_offload_loop_list(sph_store s, sph_batch b, int loop, void *dev_bu
                                 void *dev_buf_out, const void *dev_list, size_t list_bytes,
                                 const sph_params *p, void *stream);
 /* A whole step of the list cycle in one call: per bundle the density pack,
- * that bundle's list build from it, the density list loop and its unpack;
- * the ghost; then the gradient and force loops as sph_batch_offload_loop_list.
+ * that bundle's list build from it, the density list loop and its unpack
+ * with the ghost; then the gradient and force loops as
+ * sph_batch_offload_loop_list.
  * Enqueues only.  A list pool that runs out is reported by sph_sync
  * (SPH_ENOMEM) and sph_batch_list_status, as for sph_batch_list_build; the
  * step's loops then skip all pairs. */

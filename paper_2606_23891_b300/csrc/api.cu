@@ -1114,7 +1114,8 @@ int sph_batch_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in
 }
 
 static int batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const void *dev_buf_out,
-                        const void *dev_buf_in, bool write, int active_bin, void *stream) {
+                        const void *dev_buf_in, bool write, bool ghost, const sph_params *p,
+                        void *stream) {
     if (int rc = check_store(s)) return rc;
     if (int rc = check_batch(b, bundle)) return rc;
     if (int rc = check_loop(loop)) return rc;
@@ -1130,8 +1131,21 @@ static int batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const vo
                                               : BLayout<SPH_FORCE>::perm(S);
     a.perm = reinterpret_cast<const int32_t *>((const char *)dev_buf_in + perm_off);
     a.tb = reinterpret_cast<const int8_t *>((const char *)dev_buf_in + BLayout<SPH_FORCE>::tb(S));
-    a.active_bin = active_bin;
+    a.active_bin = p ? p->active_bin : 0;
     a.S = S;
+    ghost = ghost && loop == SPH_DENSITY;
+    if (ghost) {
+        a.gin[0] = at(s, F_MASS, 0);
+        a.gin[1] = at(s, F_H, 0);
+        a.gin[2] = at(s, F_U, 0);
+        a.gout[0] = at(s, F_FGRADH, 0);
+        a.gout[1] = at(s, F_PRES, 0);
+        a.gout[2] = at(s, F_CS, 0);
+        a.gout[3] = at(s, F_BALS, 0);
+        a.kernel_gamma = (float)p->kernel_gamma;
+        a.gamma = (float)p->gamma;
+        a.balsara_eps = (float)p->balsara_eps;
+    }
     int k = 0;
     if (loop == SPH_DENSITY) {
         for (int f : {F_RHO, F_RHODH, F_WCOUNT, F_WCOUNTDH, F_DIVV}) a.dst[k++] = at(s, f, 0);
@@ -1146,7 +1160,9 @@ static int batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const vo
     if (bb.ntargets == 0) return SPH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const unsigned g = (unsigned)bb.ntargets;
-    if (write) {
+    if (ghost) {
+        k_bunpack<SPH_DENSITY, true, true><<<g, 128, 0, st>>>(a);
+    } else if (write) {
         if (loop == SPH_DENSITY) k_bunpack<SPH_DENSITY, true><<<g, 128, 0, st>>>(a);
         else if (loop == SPH_GRADIENT) k_bunpack<SPH_GRADIENT, true><<<g, 128, 0, st>>>(a);
         else k_bunpack<SPH_FORCE, true><<<g, 128, 0, st>>>(a);
@@ -1160,14 +1176,16 @@ static int batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const vo
 
 int sph_batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const void *dev_buf_out,
                      const void *dev_buf_in, void *stream) {
-    return batch_unpack(s, b, loop, bundle, dev_buf_out, dev_buf_in, false, 0, stream);
+    return batch_unpack(s, b, loop, bundle, dev_buf_out, dev_buf_in, false, false, nullptr,
+                        stream);
 }
 
 int sph_batch_unpack_write(sph_store s, sph_batch b, int loop, int bundle,
                            const void *dev_buf_out, const void *dev_buf_in, const sph_params *p,
-                           void *stream) {
+                           int with_ghost, void *stream) {
     if (int rc = check_params(p)) return rc;
-    return batch_unpack(s, b, loop, bundle, dev_buf_out, dev_buf_in, true, p->active_bin, stream);
+    return batch_unpack(s, b, loop, bundle, dev_buf_out, dev_buf_in, true, with_ghost != 0, p,
+                        stream);
 }
 
 int sph_batch_offload_loop(sph_store s, sph_batch b, int loop, void *dev_buf_in,
@@ -1179,10 +1197,11 @@ int sph_batch_offload_loop(sph_store s, sph_batch b, int loop, void *dev_buf_in,
     for (int k = 0; k < (int)b->bundles.size(); ++k) {
         if (int rc = sph_batch_pack(s, b, loop, k, dev_buf_in, p, stream)) return rc;
         if (int rc = sph_batch_interact(b, loop, k, dev_buf_in, dev_buf_out, p, stream)) return rc;
-        if (int rc = sph_batch_unpack_write(s, b, loop, k, dev_buf_out, dev_buf_in, p, stream))
+        if (int rc = sph_batch_unpack_write(s, b, loop, k, dev_buf_out, dev_buf_in, p, 1,
+                                            stream))
             return rc;
     }
-    return sph_ghost(s, loop, p, stream);
+    return SPH_OK;
 }
 
 int sph_batch_destroy(sph_batch b) {
@@ -1423,10 +1442,11 @@ int sph_batch_offload_loop_list(sph_store s, sph_batch b, int loop, void *dev_bu
         if (int rc = sph_batch_list_interact(b, loop, k, dev_buf_in, dev_buf_out, dev_list,
                                              list_bytes, p, stream))
             return rc;
-        if (int rc = sph_batch_unpack_write(s, b, loop, k, dev_buf_out, dev_buf_in, p, stream))
+        if (int rc = sph_batch_unpack_write(s, b, loop, k, dev_buf_out, dev_buf_in, p, 1,
+                                            stream))
             return rc;
     }
-    return sph_ghost(s, loop, p, stream);
+    return SPH_OK;
 }
 
 int sph_batch_offload_step_list(sph_store s, sph_batch b, void *dev_buf_in, void *dev_buf_out,
@@ -1449,11 +1469,10 @@ int sph_batch_offload_step_list(sph_store s, sph_batch b, void *dev_buf_in, void
         if (int rc = sph_batch_list_interact(b, SPH_DENSITY, k, dev_buf_in, dev_buf_out,
                                              dev_list, list_bytes, p, stream))
             return rc;
-        if (int rc = sph_batch_unpack_write(s, b, SPH_DENSITY, k, dev_buf_out, dev_buf_in, p,
+        if (int rc = sph_batch_unpack_write(s, b, SPH_DENSITY, k, dev_buf_out, dev_buf_in, p, 1,
                                             stream))
             return rc;
     }
-    if (int rc = sph_ghost(s, SPH_DENSITY, p, stream)) return rc;
     for (int loop : {SPH_GRADIENT, SPH_FORCE})
         if (int rc = sph_batch_offload_loop_list(s, b, loop, dev_buf_in, dev_buf_out, dev_list,
                                                  list_bytes, p, stream))

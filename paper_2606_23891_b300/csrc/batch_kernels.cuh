@@ -17,6 +17,7 @@
 #pragma once
 #include "device.cuh"
 #include "physics_kernels.cuh"
+#include "store_kernels.cuh"
 
 namespace sph {
 
@@ -460,6 +461,9 @@ struct BUnpackArgs {
     int active_bin;
     long long S;
     CompPtr dst[8];
+    CompPtr gin[3];     // GHOST: mass, h, u
+    CompPtr gout[4];    // GHOST: f_gradh, pressure, soundspeed, balsara
+    float kernel_gamma, gamma, balsara_eps;
 };
 
 // One CTA per target cell.  Default: add each particle's result into the
@@ -468,8 +472,9 @@ struct BUnpackArgs {
 // initialised store (0 + v, max(0, v)), so no initialisation pass is needed:
 // a batched plan gives every particle all its pairs in the one bundle that
 // holds its cell as a target.  Inactive particles keep their force outputs,
-// as the initialisation would have left them.
-template <int LOOP, bool WRITE = false>
+// as the initialisation would have left them.  GHOST (density, WRITE): the
+// ghost's arithmetic follows on the written sums, as sph_ghost would give.
+template <int LOOP, bool WRITE = false, bool GHOST = false>
 __global__ void __launch_bounds__(128) k_bunpack(BUnpackArgs a) {
     const BCellDev C = a.cells[a.targets[blockIdx.x].cell];
     const long long r16 = (a.S * 16 + 255) / 256 * 256;
@@ -481,8 +486,25 @@ __global__ void __launch_bounds__(128) k_bunpack(BUnpackArgs a) {
             const float4 o0 = reinterpret_cast<const float4 *>(a.out)[sl];
             const float4 o1 = reinterpret_cast<const float4 *>(a.out + r16)[sl];
             const float v[8] = {o0.x, o0.y, o0.z, o0.w, o1.x, o1.y, o1.z, o1.w};
+            if constexpr (GHOST) {
+                float sums[8], g[11];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) st<float>(a.dst[q], p, base(a.dst[q]) + v[q]);
+                for (int q = 0; q < 8; ++q) sums[q] = 0.f + v[q];
+                ghost_point(sums, ld<float>(a.gin[0], p), ld<float>(a.gin[1], p),
+                            ld<float>(a.gin[2], p), a.kernel_gamma, a.gamma, a.balsara_eps, g);
+                // dst: rho, rho_dh, wcount, wcount_dh, div_v, rot_v (3)
+                st<float>(a.dst[0], p, g[0]);
+                st<float>(a.dst[1], p, g[1]);
+                st<float>(a.dst[2], p, g[2]);
+                st<float>(a.dst[3], p, sums[3]);
+#pragma unroll
+                for (int q = 4; q < 8; ++q) st<float>(a.dst[q], p, g[q - 1]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) st<float>(a.gout[q], p, g[7 + q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) st<float>(a.dst[q], p, base(a.dst[q]) + v[q]);
+            }
         } else if constexpr (LOOP == SPH_GRADIENT) {
             const float2 o = reinterpret_cast<const float2 *>(a.out)[sl];
             st<float>(a.dst[0], p, fmaxf(base(a.dst[0]), o.x));

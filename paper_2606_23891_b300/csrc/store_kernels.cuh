@@ -82,40 +82,54 @@ struct GhostArgs {
     float kernel_gamma, gamma, balsara_eps;
 };
 
+// The ghost's arithmetic for one particle, from its raw density sums s[8]
+// (rho, rho_dh, wcount, wcount_dh, div_v, rot_v) and m, h, u; g[11] receives
+// rho, rho_dh, wcount, div_v, rot_v (3), f_gradh, pressure, soundspeed,
+// balsara.
+__device__ __forceinline__ void ghost_point(const float *s, float m, float h, float u,
+                                            float kernel_gamma, float gamma, float balsara_eps,
+                                            float *g) {
+    const float H = kernel_gamma * h;
+    const float Hinv = 1.f / H;
+    const float Hinv3 = Hinv * Hinv * Hinv;
+    const float rho = s[0] + m * kNorm * Hinv3;
+    const float rho_dh = s[1] - 3.f * m * kNorm * Hinv3 * Hinv;
+    const float wcount = s[2] + 32.f / 3.f;
+    const float rinv = 1.f / rho;
+    const float div = s[4] * rinv;
+    const float r0 = s[5] * rinv;
+    const float r1 = s[6] * rinv;
+    const float r2 = s[7] * rinv;
+    const float omega = 1.f + H * rho_dh * rinv * (1.f / 3.f);
+    const float pres = (gamma - 1.f) * rho * u;
+    const float cs = sqrtf(gamma * (gamma - 1.f) * u);
+    const float arot = sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
+    const float adiv = fabsf(div);
+    const float bal = adiv / (adiv + arot + balsara_eps * cs / h);
+    g[0] = rho;
+    g[1] = rho_dh;
+    g[2] = wcount;
+    g[3] = div;
+    g[4] = r0;
+    g[5] = r1;
+    g[6] = r2;
+    g[7] = 1.f / omega;
+    g[8] = pres;
+    g[9] = cs;
+    g[10] = bal;
+}
+
 __global__ void k_ghost(GhostArgs a, long long n) {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
-        const float m = ld<float>(a.f[0], p);
-        const float h = ld<float>(a.f[1], p);
-        const float u = ld<float>(a.f[2], p);
-        const float H = a.kernel_gamma * h;
-        const float Hinv = 1.f / H;
-        const float Hinv3 = Hinv * Hinv * Hinv;
-        float rho = ld<float>(a.f[3], p) + m * kNorm * Hinv3;
-        float rho_dh = ld<float>(a.f[4], p) - 3.f * m * kNorm * Hinv3 * Hinv;
-        float wcount = ld<float>(a.f[5], p) + 32.f / 3.f;
-        const float rinv = 1.f / rho;
-        const float div = ld<float>(a.f[6], p) * rinv;
-        const float r0 = ld<float>(a.f[7], p) * rinv;
-        const float r1 = ld<float>(a.f[8], p) * rinv;
-        const float r2 = ld<float>(a.f[9], p) * rinv;
-        const float omega = 1.f + H * rho_dh * rinv * (1.f / 3.f);
-        const float pres = (a.gamma - 1.f) * rho * u;
-        const float cs = sqrtf(a.gamma * (a.gamma - 1.f) * u);
-        const float arot = sqrtf(r0 * r0 + r1 * r1 + r2 * r2);
-        const float adiv = fabsf(div);
-        const float bal = adiv / (adiv + arot + a.balsara_eps * cs / h);
-        st<float>(a.f[3], p, rho);
-        st<float>(a.f[4], p, rho_dh);
-        st<float>(a.f[5], p, wcount);
-        st<float>(a.f[6], p, div);
-        st<float>(a.f[7], p, r0);
-        st<float>(a.f[8], p, r1);
-        st<float>(a.f[9], p, r2);
-        st<float>(a.f[10], p, 1.f / omega);
-        st<float>(a.f[11], p, pres);
-        st<float>(a.f[12], p, cs);
-        st<float>(a.f[13], p, bal);
+        const float sums[8] = {ld<float>(a.f[3], p), ld<float>(a.f[4], p), ld<float>(a.f[5], p),
+                               0.f, ld<float>(a.f[6], p), ld<float>(a.f[7], p),
+                               ld<float>(a.f[8], p), ld<float>(a.f[9], p)};
+        float g[11];
+        ghost_point(sums, ld<float>(a.f[0], p), ld<float>(a.f[1], p), ld<float>(a.f[2], p),
+                    a.kernel_gamma, a.gamma, a.balsara_eps, g);
+#pragma unroll
+        for (int q = 0; q < 11; ++q) st<float>(a.f[3 + q], p, g[q]);
     }
 }
 

@@ -128,7 +128,7 @@ def lib() -> C.CDLL:
         "sph_batch_pack_list": (i, [p, p, i, i, p, p, p]),
         "sph_batch_interact": (i, [p, i, i, p, p, p, p]),
         "sph_batch_unpack": (i, [p, p, i, i, p, p, p]),
-        "sph_batch_unpack_write": (i, [p, p, i, i, p, p, p, p]),
+        "sph_batch_unpack_write": (i, [p, p, i, i, p, p, p, i, p]),
         "sph_batch_offload_loop": (i, [p, p, i, p, p, p, p]),
         "sph_batch_destroy": (i, [p]),
         "sph_batch_buffer_bytes_fp64": (sz, [p, i]),
@@ -500,8 +500,9 @@ def sph_batch_unpack(s, b, loop: int, bundle: int, dev_out: int, dev_in: int, st
 
 
 def sph_batch_unpack_write(s, b, loop: int, bundle: int, dev_out: int, dev_in: int, p: Params,
-                           stream: int = 0):
-    _ok(lib().sph_batch_unpack_write(s, b, loop, bundle, dev_out, dev_in, C.byref(p), stream))
+                           with_ghost: int = 0, stream: int = 0):
+    _ok(lib().sph_batch_unpack_write(s, b, loop, bundle, dev_out, dev_in, C.byref(p),
+                                     with_ghost, stream))
 
 
 def sph_batch_offload_loop(s, b, loop: int, dev_in: int, dev_out: int, p: Params,

@@ -273,6 +273,6 @@ def test_one_call_step_rejects_misuse_before_any_work():
                                         off.blist.data_ptr(), lb, off.params, st)
     with pytest.raises(sph.SphError):          # unknown loop
         sph.sph_batch_unpack_write(off.store, b, 3, 0, off.bbuf_out.data_ptr(),
-                                   off.bbuf_in.data_ptr(), off.params, st)
+                                   off.bbuf_in.data_ptr(), off.params, stream=st)
     sph.sph_sync(st)
     assert np.array_equal(off.store_bytes(), before)
