@@ -326,6 +326,14 @@ static int copy_fields(sph_store s, const sph_fields *f, const int64_t *perm, vo
     void *const *ptrs = reinterpret_cast<void *const *>(f);
     const int nfields = (int)(sizeof(sph_fields) / sizeof(void *));
     cudaStream_t st = (cudaStream_t)stream;
+    // every requested component in one launch (a second one past kCopyMax)
+    CopyArgs a{};
+    auto flush = [&]() -> int {
+        if (a.ncomp == 0) return SPH_OK;
+        k_copy_fields<<<grid_for(s->n, 256), 256, 0, st>>>(a, perm, s->n, to_store);
+        a.ncomp = 0;
+        return launch_check("copy fields");
+    };
     for (int fid = 0; fid < nfields && fid < F_BALLAST; ++fid) {
         const char *p = (const char *)ptrs[fid];
         if (!p) continue;
@@ -336,13 +344,13 @@ static int copy_fields(sph_store s, const sph_fields *f, const int64_t *perm, vo
             const int ncopy = to_store ? locate_all(s->layout, s->mem, fid, c, dst, 4)
                                        : (int)locate(s->layout, s->mem, fid, c, dst);
             for (int k = 0; k < ncopy; ++k) {
-                k_copy_field<<<grid_for(s->n, 256), 256, 0, st>>>(p, elem * cnt, c * elem, elem,
-                                                                  dst[k], perm, s->n, to_store);
-                if (int rc = launch_check("copy field")) return rc;
+                if (a.ncomp == kCopyMax)
+                    if (int rc = flush()) return rc;
+                a.c[a.ncomp++] = CopyComp{p, elem * cnt, c * elem, elem, dst[k]};
             }
         }
     }
-    return SPH_OK;
+    return flush();
 }
 
 int sph_store_convert(sph_store dst, sph_store src, void *stream) {

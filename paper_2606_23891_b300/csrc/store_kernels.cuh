@@ -6,26 +6,42 @@
 
 namespace sph {
 
-// Copy `bytes` per particle between a logical field component and a store
-// member: to_store != 0 moves src[perm[k]] -> store[k], else the reverse.
-__global__ void k_copy_field(const char *logical, int lbytes_per_particle,
-                             int comp_offset, int bytes, CompPtr store,
-                             const int64_t *perm, long long n, int to_store) {
+// Copy field components between logical arrays (one element of `bytes` per
+// component, lbytes per particle) and store members: to_store != 0 moves
+// logical[perm[k]] -> store[k], else the reverse.  All requested components
+// go in one pass: each thread moves every component of its particle, so the
+// record parts of one particle are written (or read) together and the
+// permutation is read once.
+struct CopyComp {
+    const char *logical;
+    int lbytes, loff, bytes;
+    CompPtr store;
+};
+constexpr int kCopyMax = 48;
+struct CopyArgs {
+    int ncomp;
+    CopyComp c[kCopyMax];
+};
+
+__global__ void k_copy_fields(CopyArgs a, const int64_t *perm, long long n, int to_store) {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const long long p = perm ? perm[k] : k;
-        char *lp = const_cast<char *>(logical) + p * lbytes_per_particle + comp_offset;
-        char *sp = store.ptr + k * store.stride;
-        if (bytes == 8) {
-            if (to_store) *(unsigned long long *)sp = *(const unsigned long long *)lp;
-            else *(unsigned long long *)lp = *(const unsigned long long *)sp;
-        } else if (bytes == 4) {
-            if (to_store) *(unsigned int *)sp = *(const unsigned int *)lp;
-            else *(unsigned int *)lp = *(const unsigned int *)sp;
-        } else {
-            for (int b = 0; b < bytes; ++b) {
-                if (to_store) sp[b] = lp[b];
-                else lp[b] = sp[b];
+        for (int q = 0; q < a.ncomp; ++q) {
+            const CopyComp &C = a.c[q];
+            char *lp = const_cast<char *>(C.logical) + p * C.lbytes + C.loff;
+            char *sp = C.store.ptr + k * C.store.stride;
+            if (C.bytes == 8) {
+                if (to_store) *(unsigned long long *)sp = *(const unsigned long long *)lp;
+                else *(unsigned long long *)lp = *(const unsigned long long *)sp;
+            } else if (C.bytes == 4) {
+                if (to_store) *(unsigned int *)sp = *(const unsigned int *)lp;
+                else *(unsigned int *)lp = *(const unsigned int *)sp;
+            } else {
+                for (int b = 0; b < C.bytes; ++b) {
+                    if (to_store) sp[b] = lp[b];
+                    else lp[b] = sp[b];
+                }
             }
         }
     }
