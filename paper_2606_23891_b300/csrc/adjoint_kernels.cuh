@@ -251,12 +251,16 @@ __global__ void __launch_bounds__(128, 4) k_adj_pairs(AdjArgs a) {
         const int cnt = valid && !broken ? (int)a.L.lcount[gitem * 32 + lane] : 0;
         const int maxc = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
         uint32_t chunk = a.L.first[gitem];
+        // each lane's next list entry is loaded one pair ahead of its use
+        uint32_t ent_n = cnt > 0 ? __ldg(&a.L.entries[(long long)chunk * kLChunk + lane]) : 0u;
 #pragma unroll 1
         for (int k = 0; k < maxc; ++k) {
-            if (k > 0 && k % kLPer == 0) chunk = a.L.next[chunk];
+            const uint32_t ent = ent_n;
+            const int k1 = k + 1;
+            if (k1 < maxc && k1 % kLPer == 0) chunk = a.L.next[chunk];
+            if (k1 < cnt)
+                ent_n = __ldg(&a.L.entries[(long long)chunk * kLChunk + (k1 % kLPer) * 32 + lane]);
             if (k >= cnt) continue;
-            const uint32_t ent =
-                __ldg(&a.L.entries[(long long)chunk * kLChunk + (k % kLPer) * 32 + lane]);
             const long long js = (long long)(ent & 0x7fffffffu);
             float4 oth[kAdjRec];
 #pragma unroll
