@@ -183,13 +183,18 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
 #pragma unroll
                 for (int w = 0; w < kWTile / 32; ++w) {
                     unsigned int m = cw[w], h = 0;
-                    while (m) {
+                    while (m) {     // two candidates per iteration (the second may repeat the first)
                         const int b = __ffs(m) - 1;
                         m &= m - 1;
-                        const float4 pj = sm[0][32 * w + b];
+                        const int b2 = m ? __ffs(m) - 1 : b;
+                        m &= m - 1;
+                        const float4 pj = sm[0][32 * w + b], pk = sm[0][32 * w + b2];
                         const float dx = o0.x - pj.x, dy = o0.y - pj.y, dz = o0.z - pj.z;
+                        const float ex = o0.x - pk.x, ey = o0.y - pk.y, ez = o0.z - pk.z;
                         const float r2 = dx * dx + dy * dy + dz * dz;
-                        h |= r2 < fmaxf(Hpre2, pj.w) ? (1u << b) : 0u;
+                        const float s2 = ex * ex + ey * ey + ez * ez;
+                        h |= (r2 < fmaxf(Hpre2, pj.w) ? (1u << b) : 0u) |
+                             (s2 < fmaxf(Hpre2, pk.w) ? (1u << b2) : 0u);
                     }
                     if (self && (i - j0) >= 32 * w && (i - j0) < 32 * w + 32)
                         h &= ~(1u << (i - j0 - 32 * w));
