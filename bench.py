@@ -133,13 +133,21 @@ def dist_env():
 
 
 def barrier_max(value: float, ws: int) -> float:
+    """The maximum of `value` over the ranks (every rank gets it)."""
     if ws == 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(units_per_rank: float, ms_max: float, ws: int) -> float:
+    """Whole-job throughput: the units all ranks processed (each rank a full
+    replica) over the slowest rank's time."""
+    return units_per_rank * ws / (ms_max * 1e-3)
 
 
 def barrier(ws: int):
@@ -573,7 +581,7 @@ def run_cosmology(args, ws, peaks):
                 loops[LOOP_NAMES[l]] = {"pack_ms": pk, "kernel_ms": kr, "unpack_ms": up,
                                         "kernel_useful_fp32_TFLOPs":
                                             pairs[l] * FLOPS_PAIR[l] / (kr * 1e-3) / 1e12}
-            r = {"ms_per_step": ms, "pair_interactions_per_s": sum(pairs) * ws / (ms * 1e-3),
+            r = {"ms_per_step": ms, "pair_interactions_per_s": job_rate(sum(pairs), ms, ws),
                  "loops": loops}
             if ("list", 0) in st:
                 r["list_build_ms"] = st[("list", 0)] / args.steps
@@ -597,7 +605,7 @@ def run_cosmology(args, ws, peaks):
     torch.cuda.synchronize()
     gms = barrier_max(g0.elapsed_time(g1), ws) / args.steps
     res["cuda_graph"] = {"ms_per_step": gms,
-                         "pair_interactions_per_s": sum(pairs) * ws / (gms * 1e-3)}
+                         "pair_interactions_per_s": job_rate(sum(pairs), gms, ws)}
     del gs
     st, cnt, ms, launches = head
     top = max(st, key=lambda k: st[k])
@@ -824,7 +832,7 @@ def run_ours(args, ws, rank, local):
                 "kernel_useful_fp32_TFLOPs": pairs[l] * FLOPS_PAIR[l] / (kr * 1e-3) / 1e12,
             }
         res = {"ms_per_step": ms_step,
-               "pair_interactions_per_s": sum(pairs) * ws / (ms_step * 1e-3), "loops": loops}
+               "pair_interactions_per_s": job_rate(sum(pairs), ms_step, ws), "loops": loops}
         if ("list", 0) in st:
             res["list_build_ms"] = st[("list", 0)] / args.steps
         return res
@@ -868,7 +876,7 @@ def run_ours(args, ws, rank, local):
     off, total_ms, timer, cl, st, cnt = head
     ms_step = total_ms / args.steps
     kernel_dependent = layout_phase_study(per_layout, convert_ms, args.layouts[0])
-    value = sum(pairs) * ws / (ms_step * 1e-3)
+    value = job_rate(sum(pairs), ms_step, ws)
     graph = None
     if args.head_pipeline in ("batched", "list"):
         # the same step recorded once into a CUDA graph and replayed
@@ -885,7 +893,7 @@ def run_ours(args, ws, rank, local):
         g1.record()
         torch.cuda.synchronize()
         gms = barrier_max(g0.elapsed_time(g1), ws) / args.steps
-        graph = {"ms_per_step": gms, "pair_interactions_per_s": sum(pairs) * ws / (gms * 1e-3)}
+        graph = {"ms_per_step": gms, "pair_interactions_per_s": job_rate(sum(pairs), gms, ws)}
         del gs
     # dominant kernel of the headline layout
     top = max(st, key=lambda k: st[k])
@@ -994,7 +1002,7 @@ def run_ours(args, ws, rank, local):
             "parallelism": "replicas" if ws > 1 else "single GPU",
             "task_build_s": t_build,
         },
-        "e2e": {"value": sum(pairs) * ws / (e2e_ms * 1e-3), "unit": UNIT,
+        "e2e": {"value": job_rate(sum(pairs), e2e_ms, ws), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_ms,
                 "copied": "in: x v m h u alpha_visc alpha_diff time_bin; "
