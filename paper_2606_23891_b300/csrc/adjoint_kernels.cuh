@@ -250,21 +250,44 @@ __global__ void __launch_bounds__(128, 4) k_adj_pairs(AdjArgs a) {
         float gx = 0.f, gy = 0.f, gz = 0.f, gm = 0.f, gu = 0.f, grho = 0.f, gf = 0.f, gB = 0.f;
         const int cnt = valid && !broken ? (int)a.L.lcount[gitem * 32 + lane] : 0;
         const int maxc = __reduce_max_sync(0xffffffffu, (unsigned)cnt);
+        // the list entries run two pairs ahead and the partner's record one
+        // pair ahead of their use (the loads' latency hides behind a pair)
         uint32_t chunk = a.L.first[gitem];
-        // each lane's next list entry is loaded one pair ahead of its use
-        uint32_t ent_n = cnt > 0 ? __ldg(&a.L.entries[(long long)chunk * kLChunk + lane]) : 0u;
+        int kl = 0;
+        auto next_ent = [&]() -> uint32_t {
+            uint32_t e = 0u;
+            if (kl < cnt)
+                e = __ldg(&a.L.entries[(long long)chunk * kLChunk + (kl % kLPer) * 32 + lane]);
+            ++kl;
+            if (kl % kLPer == 0 && kl < maxc) chunk = a.L.next[chunk];
+            return e;
+        };
+        uint32_t e = next_ent(), en = e;
+        float4 nxt[kAdjRec];
+        bool un = 0 < cnt;
+        if (un) {
+#pragma unroll
+            for (int f = 0; f < kAdjRec; ++f)
+                nxt[f] = __ldg(&a.rec[kAdjRec * (long long)(e & 0x7fffffffu) + f]);
+        }
+        e = next_ent();
 #pragma unroll 1
         for (int k = 0; k < maxc; ++k) {
-            const uint32_t ent = ent_n;
-            const int k1 = k + 1;
-            if (k1 < maxc && k1 % kLPer == 0) chunk = a.L.next[chunk];
-            if (k1 < cnt)
-                ent_n = __ldg(&a.L.entries[(long long)chunk * kLChunk + (k1 % kLPer) * 32 + lane]);
-            if (k >= cnt) continue;
-            const long long js = (long long)(ent & 0x7fffffffu);
             float4 oth[kAdjRec];
 #pragma unroll
-            for (int f = 0; f < kAdjRec; ++f) oth[f] = __ldg(&a.rec[kAdjRec * js + f]);
+            for (int f = 0; f < kAdjRec; ++f) oth[f] = nxt[f];
+            const uint32_t ent = en;
+            const bool u = un;
+            un = k + 1 < cnt;
+            if (un) {
+#pragma unroll
+                for (int f = 0; f < kAdjRec; ++f)
+                    nxt[f] = __ldg(&a.rec[kAdjRec * (long long)(e & 0x7fffffffu) + f]);
+            }
+            en = e;
+            e = next_ent();
+            if (!u) continue;
+            const long long js = (long long)(ent & 0x7fffffffu);
             float dx, dy, dz;
             image_sep(own, oth, a, dx, dy, dz);
             const float r2 = dx * dx + dy * dy + dz * dz;
