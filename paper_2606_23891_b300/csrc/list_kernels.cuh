@@ -343,11 +343,13 @@ struct AccL<SPH_FORCE> {
     }
 };
 
-// Resident threads per SM the list loops are compiled for (measured at
-// Gresho256: density and gradient gain from 48 warps per SM at 40 registers;
-// the force loop, with its j record prefetched, runs best at 28 warps and
-// 72 registers).
-constexpr int kLLoopMinThreads[3] = {1536, 1536, 896};
+// Resident threads per SM the list loops are compiled for, measured at
+// Gresho256.  All three loops run best at 28 warps per SM.  Density and
+// gradient are bound by L1 on their gathers, and with their list entries
+// loaded ahead, fewer warps thrash L1 less than the 48 they were tuned for
+// before; 24 and 32 warps tie.  The force loop prefetches its j record at
+// 72 registers.
+constexpr int kLLoopMinThreads[3] = {896, 896, 896};
 template <int LOOP, int T>
 __global__ void __launch_bounds__(T, kLLoopMinThreads[LOOP] / T)
     k_bloop(BInteractArgs a, ListView L, long long item0) {
