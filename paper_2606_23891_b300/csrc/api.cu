@@ -215,14 +215,26 @@ int launch_persistent(Kernel kernel, int threads, int nitems, cudaStream_t st, c
     return launch_check(what);
 }
 
-template <int LOOP>
-int dispatch_bloop(int threads, const BInteractArgs &a, const ListView &L, long long item0,
-                   cudaStream_t st) {
+template <int LOOP, int W>
+int dispatch_bloop_w(int threads, const BInteractArgs &a, const ListView &L, long long item0,
+                     cudaStream_t st) {
     if (threads == 64)
-        return launch_persistent(k_bloop<LOOP, 64>, 64, a.nitems, st, "list loop", a, L, item0);
+        return launch_persistent(k_bloop<LOOP, 64, W>, 64, a.nitems, st, "list loop", a, L,
+                                 item0);
     if (threads == 256)
-        return launch_persistent(k_bloop<LOOP, 256>, 256, a.nitems, st, "list loop", a, L, item0);
-    return launch_persistent(k_bloop<LOOP, 128>, 128, a.nitems, st, "list loop", a, L, item0);
+        return launch_persistent(k_bloop<LOOP, 256, W>, 256, a.nitems, st, "list loop", a, L,
+                                 item0);
+    return launch_persistent(k_bloop<LOOP, 128, W>, 128, a.nitems, st, "list loop", a, L, item0);
+}
+
+// The list loops' residency by plan kind (grid: 28 warps per SM, tree: 48).
+template <int LOOP>
+int dispatch_bloop(sph_batch b, const BInteractArgs &a, const ListView &L, long long item0,
+                   cudaStream_t st) {
+    if constexpr (LOOP != SPH_FORCE)
+        if (b->kind == 1)
+            return dispatch_bloop_w<LOOP, kLLoopWarpsTree>(b->threads, a, L, item0, st);
+    return dispatch_bloop_w<LOOP, kLLoopWarpsGrid>(b->threads, a, L, item0, st);
 }
 
 inline int dispatch_blist(int threads, const BInteractArgs &a, const ListView &L, long long item0,
@@ -1427,9 +1439,9 @@ int sph_batch_list_interact(sph_batch b, int loop, int bundle, const void *dev_b
     if (int rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st),
                             "reset work queue"))
         return rc;
-    if (loop == SPH_DENSITY) return dispatch_bloop<SPH_DENSITY>(b->threads, a, L, bb.item0, st);
-    if (loop == SPH_GRADIENT) return dispatch_bloop<SPH_GRADIENT>(b->threads, a, L, bb.item0, st);
-    return dispatch_bloop<SPH_FORCE>(b->threads, a, L, bb.item0, st);
+    if (loop == SPH_DENSITY) return dispatch_bloop<SPH_DENSITY>(b, a, L, bb.item0, st);
+    if (loop == SPH_GRADIENT) return dispatch_bloop<SPH_GRADIENT>(b, a, L, bb.item0, st);
+    return dispatch_bloop<SPH_FORCE>(b, a, L, bb.item0, st);
 }
 
 int sph_batch_offload_loop_list(sph_store s, sph_batch b, int loop, void *dev_buf_in,

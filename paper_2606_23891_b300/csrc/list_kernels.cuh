@@ -343,15 +343,16 @@ struct AccL<SPH_FORCE> {
     }
 };
 
-// Resident threads per SM the list loops are compiled for, measured at
-// Gresho256.  All three loops run best at 28 warps per SM.  Density and
-// gradient are bound by L1 on their gathers, and with their list entries
-// loaded ahead, fewer warps thrash L1 less than the 48 they were tuned for
-// before; 24 and 32 warps tie.  The force loop prefetches its j record at
-// 72 registers.
-constexpr int kLLoopMinThreads[3] = {896, 896, 896};
-template <int LOOP, int T>
-__global__ void __launch_bounds__(T, kLLoopMinThreads[LOOP] / T)
+// Resident warps per SM the list loops are compiled for (WARPS), measured.  The
+// force loop runs at 28, with its j record prefetched at 72 registers.  The
+// density and gradient loops are bound by L1 on their gathers: on the
+// uniform Gresho set 28 warps thrash L1 less than 48 (6.25 / 5.81 against
+// 6.74 / 6.32 ms), while on the clustered lognormal set, whose lanes' list
+// lengths differ more, 48 warps hide more (step 133.5 against 135.7 ms).  So
+// grid plans use 28 and tree plans 48.
+constexpr int kLLoopWarpsGrid = 28, kLLoopWarpsTree = 48;
+template <int LOOP, int T, int WARPS>
+__global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
     k_bloop(BInteractArgs a, ListView L, long long item0) {
     using BL = BLayout<LOOP>;
     constexpr int nf = NFC<LOOP>::value;     // compact records (k_bpack<LOOP, true>)
