@@ -1073,11 +1073,13 @@ static int batch_pack(sph_store s, sph_batch b, int loop, int bundle, void *dev_
     if (bb.ncells == 0) return SPH_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const unsigned g = (unsigned)bb.ncells;
-    if (loop == SPH_DENSITY) k_bpack<SPH_DENSITY><<<g, 128, 0, st>>>(a);
-    else if (loop == SPH_GRADIENT && compact) k_bpack<SPH_GRADIENT, true><<<g, 128, 0, st>>>(a);
-    else if (loop == SPH_GRADIENT) k_bpack<SPH_GRADIENT><<<g, 128, 0, st>>>(a);
-    else if (compact) k_bpack<SPH_FORCE, true><<<g, 128, 0, st>>>(a);
-    else k_bpack<SPH_FORCE><<<g, 128, 0, st>>>(a);
+    // one CTA per cell; 64 threads suit cells of a few dozen particles
+    // (measured against 128: faster on the uniform and the clustered sets)
+    if (loop == SPH_DENSITY) k_bpack<SPH_DENSITY><<<g, 64, 0, st>>>(a);
+    else if (loop == SPH_GRADIENT && compact) k_bpack<SPH_GRADIENT, true><<<g, 64, 0, st>>>(a);
+    else if (loop == SPH_GRADIENT) k_bpack<SPH_GRADIENT><<<g, 64, 0, st>>>(a);
+    else if (compact) k_bpack<SPH_FORCE, true><<<g, 64, 0, st>>>(a);
+    else k_bpack<SPH_FORCE><<<g, 64, 0, st>>>(a);
     return launch_check("batch pack");
 }
 
@@ -1181,15 +1183,15 @@ static int batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const vo
     cudaStream_t st = (cudaStream_t)stream;
     const unsigned g = (unsigned)bb.ntargets;
     if (ghost) {
-        k_bunpack<SPH_DENSITY, true, true><<<g, 128, 0, st>>>(a);
+        k_bunpack<SPH_DENSITY, true, true><<<g, 64, 0, st>>>(a);
     } else if (write) {
-        if (loop == SPH_DENSITY) k_bunpack<SPH_DENSITY, true><<<g, 128, 0, st>>>(a);
-        else if (loop == SPH_GRADIENT) k_bunpack<SPH_GRADIENT, true><<<g, 128, 0, st>>>(a);
-        else k_bunpack<SPH_FORCE, true><<<g, 128, 0, st>>>(a);
+        if (loop == SPH_DENSITY) k_bunpack<SPH_DENSITY, true><<<g, 64, 0, st>>>(a);
+        else if (loop == SPH_GRADIENT) k_bunpack<SPH_GRADIENT, true><<<g, 64, 0, st>>>(a);
+        else k_bunpack<SPH_FORCE, true><<<g, 64, 0, st>>>(a);
     } else {
-        if (loop == SPH_DENSITY) k_bunpack<SPH_DENSITY><<<g, 128, 0, st>>>(a);
-        else if (loop == SPH_GRADIENT) k_bunpack<SPH_GRADIENT><<<g, 128, 0, st>>>(a);
-        else k_bunpack<SPH_FORCE><<<g, 128, 0, st>>>(a);
+        if (loop == SPH_DENSITY) k_bunpack<SPH_DENSITY><<<g, 64, 0, st>>>(a);
+        else if (loop == SPH_GRADIENT) k_bunpack<SPH_GRADIENT><<<g, 64, 0, st>>>(a);
+        else k_bunpack<SPH_FORCE><<<g, 64, 0, st>>>(a);
     }
     return launch_check("batch unpack");
 }

@@ -175,14 +175,15 @@ __global__ void __launch_bounds__(128) k_bpack(BPackArgs a) {
     float ctr[3];
     for (int d = 0; d < 3; ++d) {
         float lo = red[d][0], hi = red[3 + d][0];
-        for (int w = 1; w < 4; ++w) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
             lo = fminf(lo, red[d][w]);
             hi = fmaxf(hi, red[3 + d][w]);
         }
         ctr[d] = 0.5f * (lo + hi);
     }
     if (threadIdx.x == 0) {
-        const float hm = fmaxf(fmaxf(hred[0], hred[1]), fmaxf(hred[2], hred[3]));
+        float hm = hred[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) hm = fmaxf(hm, hred[w]);
         reinterpret_cast<float *>(a.buf + BL::cellh(a.S))[blockIdx.x] = hm;
     }
     // octant key of particle k (0 when the cell keeps store order)
