@@ -102,7 +102,10 @@ def chain(x, m, u, f: dict, pairs, box=(1.0, 1.0, 1.0), active_bin: int = 0,
     div = Sdiv / rho
     rot = Srot / rho[:, None]
     omega = 1 + H / (3 * rho) * rho_dh
-    fgh = 1 / omega
+    # no neighbour inside the support: Omega is exactly 0 and f_gradh = 1
+    lone = torch.zeros(n, dtype=dt).index_add(0, I, dens) == 0
+    fgh = torch.where(lone, torch.ones_like(omega), 1 / torch.where(lone, torch.ones_like(omega),
+                                                                   omega))
     P = (gamma - 1) * rho * u
     c = torch.sqrt(gamma * (gamma - 1) * u)
     R2 = (rot * rot).sum(dim=1)

@@ -157,7 +157,9 @@ int64_t oracle_density(int64_t n, const double *x, const float *v,
 /* Ghost after density (the linear update of Sec. 2.1).                      */
 /*   rho += m_i W(0, H_i); rho_dh += m_i dW/dH(0, H_i); wcount += its self   */
 /*   term; div v = raw / rho; curl v = raw / rho;                            */
-/*   Omega = 1 + H/(3 rho) d rho/dH;  f_gradh = 1/Omega;                     */
+/*   Omega = 1 + H/(3 rho) d rho/dH;  f_gradh = 1/Omega, except for a       */
+/*   particle with no neighbour inside its support (raw wcount sum 0), whose */
+/*   Omega is exactly 0: f_gradh = 1 (no grad-h correction).                 */
 /*   P = (gamma - 1) rho u;  c = sqrt(gamma (gamma - 1) u);                  */
 /*   Balsara B = |div v| / (|div v| + |curl v| + eps c / h).                 */
 /* out[12 k + ...] = rho, rho_dh, wcount, wcount_dh, div_v, rot_v[3],        */
@@ -181,7 +183,7 @@ void oracle_ghost(int64_t nsel, const int64_t *sel, const float *m,
         double div = s[4] / rho;
         double rot[3] = {s[5] / rho, s[6] / rho, s[7] / rho};
         double omega = 1.0 + Hi / (3.0 * rho) * rho_dh;
-        double fgh = 1.0 / omega;
+        double fgh = s[2] == 0.0 ? 1.0 : 1.0 / omega;
         double ui = (double)u[i];
         double pres = (P->gamma - 1.0) * rho * ui;
         double cs = sqrt(P->gamma * (P->gamma - 1.0) * ui);

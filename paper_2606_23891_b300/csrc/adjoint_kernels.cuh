@@ -29,7 +29,7 @@ constexpr int kAdjRec = 6;   // float4 records per slot
 // store fields read by the adjoint (indices into AdjArgs::f; rot_v takes 3)
 enum AdjField {
     A_X0, A_X1, A_X2, A_V0, A_V1, A_V2, A_M, A_H, A_U, A_RHO, A_FGH, A_BAL, A_AV, A_AD,
-    A_CS, A_PRES, A_TB, A_RHODH, A_DIV, A_ROT0, A_NUM = A_ROT0 + 3
+    A_CS, A_PRES, A_TB, A_RHODH, A_DIV, A_ROT0, A_WCOUNT = A_ROT0 + 3, A_NUM
 };
 
 struct AdjArgs {
@@ -357,7 +357,13 @@ __global__ void k_adj_ghost(AdjArgs a) {
         for (int d = 0; d < 3; ++d) grot[d] = R > 0.f ? gRn * rt[d] / R : 0.f;
         const float gSdiv = gdiv / rho;
         grho -= gdiv * div / rho + (grot[0] * rt[0] + grot[1] * rt[1] + grot[2] * rt[2]) / rho;
-        const float gOm = -g1.z * f * f;
+        // a particle with no neighbour in its support took f = 1 (Omega = 0):
+        // f is then constant.  It is recognised by f == 1 together with a
+        // neighbour count equal to the self term, which no other particle
+        // reaches (an edge neighbour that leaves the count unchanged in
+        // float makes Omega tiny and f far from 1).
+        const bool lone = f == 1.f && ld<float>(a.f[A_WCOUNT], p) == 32.f / 3.f;
+        const float gOm = lone ? 0.f : -g1.z * f * f;
         const float grhodh = gOm * H / (3.f * rho);
         grho -= gOm * H * rho_dh / (3.f * rho * rho);
         const float Hi = 1.f / H;

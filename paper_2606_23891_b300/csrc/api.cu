@@ -1374,6 +1374,10 @@ int sph_batch_list_build(sph_store s, sph_batch b, void *dev_buf_in, void *dev_l
     const int64_t NI = (int64_t)b->items.size();
     if ((int64_t)list_bytes < ListLayout::fixed(NI) + 512)
         return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
+    // the header is reset here too, so a plan without bundles leaves it valid
+    if (int rc = cuda_check(cudaMemsetAsync(dev_list, 0, sizeof(ListHdr), (cudaStream_t)stream),
+                            "reset list header"))
+        return rc;
     for (int k = 0; k < (int)b->bundles.size(); ++k) {
         if (int rc = sph_batch_pack(s, b, SPH_DENSITY, k, dev_buf_in, p, stream)) return rc;
         if (int rc = sph_batch_list_build_bundle(s, b, k, dev_buf_in, dev_list, list_bytes, p,
@@ -1483,6 +1487,9 @@ int sph_batch_offload_step_list(sph_store s, sph_batch b, void *dev_buf_in, void
         return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
     if ((int64_t)list_bytes < ListLayout::fixed((int64_t)b->items.size()) + 512)
         return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
+    if (int rc = cuda_check(cudaMemsetAsync(dev_list, 0, sizeof(ListHdr), (cudaStream_t)stream),
+                            "reset list header"))
+        return rc;
     for (int k = 0; k < (int)b->bundles.size(); ++k) {
         if (int rc = sph_batch_pack_list(s, b, SPH_DENSITY, k, dev_buf_in, p, stream)) return rc;
         if (int rc = sph_batch_list_build_bundle(s, b, k, dev_buf_in, dev_list, list_bytes, p,
@@ -1557,7 +1564,7 @@ int sph_batch_adjoint(sph_store s, sph_batch b, void *dev_buf_in, const void *de
                                  {F_MASS, 0}, {F_H, 0}, {F_U, 0}, {F_RHO, 0}, {F_FGRADH, 0},
                                  {F_BALS, 0}, {F_AVISC, 0}, {F_ADIFF, 0}, {F_CS, 0},
                                  {F_PRES, 0}, {F_TBIN, 0}, {F_RHODH, 0}, {F_DIVV, 0},
-                                 {F_ROTV, 0}, {F_ROTV, 1}, {F_ROTV, 2}};
+                                 {F_ROTV, 0}, {F_ROTV, 1}, {F_ROTV, 2}, {F_WCOUNT, 0}};
     for (int r = 0; r < A_NUM; ++r) a.f[r] = at(s, roles[r][0], roles[r][1]);
     a.abar = dev_abar;
     a.ebar = dev_ebar;

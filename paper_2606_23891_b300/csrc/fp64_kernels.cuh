@@ -255,7 +255,8 @@ __global__ void k_ghost64(GhostArgs a, long long n, double kernel_gamma, double 
         const double H = kernel_gamma * h;
         const double rho = (double)ld<float>(a.f[3], p) + m * norm / (H * H * H);
         const double rho_dh = (double)ld<float>(a.f[4], p) - 3.0 * m * norm / (H * H * H * H);
-        const double wcount = (double)ld<float>(a.f[5], p) + 32.0 / 3.0;
+        const double wsum = ld<float>(a.f[5], p);
+        const double wcount = wsum + 32.0 / 3.0;
         const double div = ld<float>(a.f[6], p) / rho;
         const double r0 = ld<float>(a.f[7], p) / rho, r1 = ld<float>(a.f[8], p) / rho,
                      r2 = ld<float>(a.f[9], p) / rho;
@@ -270,7 +271,7 @@ __global__ void k_ghost64(GhostArgs a, long long n, double kernel_gamma, double 
         st<float>(a.f[7], p, (float)r0);
         st<float>(a.f[8], p, (float)r1);
         st<float>(a.f[9], p, (float)r2);
-        st<float>(a.f[10], p, (float)(1.0 / omega));
+        st<float>(a.f[10], p, wsum == 0.0 ? 1.f : (float)(1.0 / omega));   // no neighbour: Omega = 0
         st<float>(a.f[11], p, (float)((gamma - 1.0) * rho * u));
         st<float>(a.f[12], p, (float)cs);
         st<float>(a.f[13], p, (float)bal);

@@ -221,7 +221,8 @@ int host_ghost(sph_store s, float kernel_gamma, float gamma, float balsara_eps, 
         const float Hinv3 = Hinv * Hinv * Hinv;
         const float rho = hld<float>(f[3], p) + m * norm * Hinv3;
         const float rho_dh = hld<float>(f[4], p) - 3.f * m * norm * Hinv3 * Hinv;
-        const float wcount = hld<float>(f[5], p) + 32.f / 3.f;
+        const float wsum = hld<float>(f[5], p);
+        const float wcount = wsum + 32.f / 3.f;
         const float rinv = 1.f / rho;
         const float div = hld<float>(f[6], p) * rinv;
         const float r0 = hld<float>(f[7], p) * rinv, r1 = hld<float>(f[8], p) * rinv,
@@ -239,7 +240,7 @@ int host_ghost(sph_store s, float kernel_gamma, float gamma, float balsara_eps, 
         hst<float>(f[7], p, r0);
         hst<float>(f[8], p, r1);
         hst<float>(f[9], p, r2);
-        hst<float>(f[10], p, 1.f / omega);
+        hst<float>(f[10], p, wsum == 0.f ? 1.f : 1.f / omega);   // no neighbour: Omega = 0
         hst<float>(f[11], p, pres);
         hst<float>(f[12], p, cs);
         hst<float>(f[13], p, bal);

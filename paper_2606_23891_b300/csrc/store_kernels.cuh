@@ -101,7 +101,8 @@ struct GhostArgs {
 // The ghost's arithmetic for one particle, from its raw density sums s[8]
 // (rho, rho_dh, wcount, wcount_dh, div_v, rot_v) and m, h, u; g[11] receives
 // rho, rho_dh, wcount, div_v, rot_v (3), f_gradh, pressure, soundspeed,
-// balsara.
+// balsara.  A particle with no neighbour inside its support (raw wcount sum
+// 0) has Omega = 0 exactly and takes f_gradh = 1.
 __device__ __forceinline__ void ghost_point(const float *s, float m, float h, float u,
                                             float kernel_gamma, float gamma, float balsara_eps,
                                             float *g) {
@@ -129,7 +130,7 @@ __device__ __forceinline__ void ghost_point(const float *s, float m, float h, fl
     g[4] = r0;
     g[5] = r1;
     g[6] = r2;
-    g[7] = 1.f / omega;
+    g[7] = s[2] == 0.f ? 1.f : 1.f / omega;
     g[8] = pres;
     g[9] = cs;
     g[10] = bal;

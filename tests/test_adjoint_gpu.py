@@ -141,3 +141,18 @@ def test_gresho_64_adjoint_against_central_differences():
     assert norm_err(gpx, fdx) <= 1e-4
     assert norm_err(gpm, fdm) <= 1e-4
     assert norm_err(gpu_, fdu) <= 1e-4
+
+
+def test_adjoint_with_a_particle_without_neighbours():
+    """One particle's support holds no other particle (f_gradh = 1, a
+    constant), while its neighbours' wider supports still reach it: the GPU
+    adjoint keeps f out of that particle's gradient like the oracle."""
+    f = system(n_side=12, seed=7, alpha_diff=0.2)
+    f["h"][100] = 0.002
+    ref_loss, rx, rm, ru = adjoint.gradient(f)
+    L, gx, gm, gu, off = gpu_grad(f)
+    assert off.export(("f_gradh",))["f_gradh"][100] == 1.0
+    assert abs(L - ref_loss) <= 1e-5 * ref_loss
+    assert norm_err(gx, rx) <= 1e-4
+    assert norm_err(gm, rm) <= 1e-4
+    assert norm_err(gu, ru) <= 1e-4

@@ -98,3 +98,46 @@ def test_gradient_equals_central_differences(alpha_diff):
                 (L(m0, hi) - L(m0, lo)) / (2 * eps)
             assert abs(fd - g[p]) <= 1e-5 * max(abs(g[p]), 1e-30) + 1e-8 * np.abs(g).max(), \
                 (name, p, fd, g[p])
+
+
+def lone_and_wide(seed=6):
+    """Two particles: A with no other particle inside its own support, and B
+    whose wider support reaches A."""
+    f = system(n_side=6, seed=seed)
+    g = {k: v[:2].copy() for k, v in f.items()}
+    g["x"][0] = [0.5, 0.5, 0.5]
+    g["x"][1] = [0.52, 0.5, 0.5]
+    g["h"][0] = 0.004           # H_A = 0.0073 < 0.02
+    g["h"][1] = 0.02            # H_B = 0.0365 > 0.02
+    g["time_bin"][:] = 0
+    return g
+
+
+def test_a_particle_without_neighbours_takes_f_gradh_one():
+    """Omega = 1 + H/(3 rho) drho/dH is exactly 0 for a particle whose
+    support holds no other particle (rho and drho/dH are its self terms), so
+    f_gradh = 1/Omega is undefined; the reading is f_gradh = 1.  Its force
+    comes only from the wider support of B, equal and opposite in m a."""
+    f = lone_and_wide()
+    ref = oracle.chain(f, oracle.params())
+    H0 = oracle.KERNEL_GAMMA * float(f["h"][0])
+    m0 = float(f["mass"][0])
+    assert ref["f_gradh"][0] == 1.0
+    assert ref["rho"][0] == pytest.approx(m0 * 8.0 / np.pi / H0 ** 3, rel=1e-12)
+    assert ref["div_v"][0] == 0.0
+    assert np.isfinite(ref["f_gradh"]).all() and ref["f_gradh"][1] != 1.0
+    pa = float(f["mass"][0]) * ref["a"][0]
+    pb = float(f["mass"][1]) * ref["a"][1]
+    assert np.abs(pa).max() > 0.0
+    np.testing.assert_allclose(pa, -pb, rtol=1e-10)
+    # the autograd restatement agrees, value and gradient finite
+    x = torch.tensor(np.asarray(f["x"], np.float64), requires_grad=True)
+    m = torch.tensor(np.asarray(f["mass"], np.float64))
+    u = torch.tensor(np.asarray(f["u"], np.float64))
+    H = oracle.KERNEL_GAMMA * np.asarray(f["h"], np.float64)
+    got = adjoint.chain(x, m, u, f, adjoint.pair_list(f["x"], H))
+    for k in ("rho", "f_gradh", "a", "u_dt"):
+        np.testing.assert_allclose(got[k].detach().numpy(), ref[k], rtol=1e-10,
+                                   atol=1e-12 * np.abs(ref[k]).max(), err_msg=k)
+    got["loss"].backward()
+    assert torch.isfinite(x.grad).all()
