@@ -86,3 +86,53 @@ def test_unpack_writes_the_marked_variables(loop):
     oracle.unpack(loop, g, perm, cs, ci, cj, 0, t1, lanes.view(np.uint8))
     for name, _, _, marks in table1():
         assert (not np.array_equal(g[name], f[name])) == marks[2 * loop + 1], (name, loop)
+
+
+# ------------------------------------------------------------ layouts --
+# The paper's layout rules (Sec. 3, "Particle Memory Layouts"), checked on
+# the oracle's layout descriptors with Table 1's marks: pack-gradient puts
+# every variable the gradient pack uses into one struct, pack-force every
+# variable the force pack uses; the *-type variants split each struct so that
+# every substruct holds one data type; AoS is one struct, SoA one array per
+# component.
+def groups_of(layout):
+    names = oracle.FIELD_NAMES
+    return [{names[fid] for fid, _, _ in members} for _, members in oracle.layout_groups(layout)]
+
+
+def marked(col):
+    return {name for name, _, _, m in table1() if m[col]}
+
+
+@pytest.mark.parametrize("layout, col", [("pack_grad", 2), ("pack_force", 4)])
+def test_kernel_driven_layouts_keep_their_pack_together(layout, col):
+    gs = groups_of(oracle.LAYOUTS.index(layout))
+    want = marked(col)
+    home = [g for g in gs if want & g]
+    assert len(home) == 1 and want <= home[0], (layout, want, gs)
+    others = {name for name, _, _, _ in table1()} - want
+    assert not (others & home[0]), (layout, others & home[0])
+
+
+@pytest.mark.parametrize("layout", ["pack_grad_type", "pack_force_type", "pack_shared_type"])
+def test_type_split_layouts_hold_one_type_per_struct(layout):
+    for g in groups_of(oracle.LAYOUTS.index(layout)):
+        types = {np.dtype(ics.FIELD_DTYPES[name][0]) for name in g if name in ics.FIELD_DTYPES}
+        assert len(types) <= 1, (layout, g)
+
+
+@pytest.mark.parametrize("base, split", [("pack_grad", "pack_grad_type"),
+                                         ("pack_force", "pack_force_type"),
+                                         ("pack_shared", "pack_shared_type")])
+def test_type_split_refines_its_baseline(base, split):
+    """Each type-split struct lies inside one struct of its baseline."""
+    gb = groups_of(oracle.LAYOUTS.index(base))
+    for g in groups_of(oracle.LAYOUTS.index(split)):
+        assert any(g <= b for b in gb), (split, g)
+
+
+def test_aos_is_one_struct_and_soa_one_array_per_component():
+    aos = oracle.layout_groups(oracle.LAYOUTS.index("aos"))
+    assert len(aos) == 1
+    soa = oracle.layout_groups(oracle.LAYOUTS.index("soa"))
+    assert all(len(members) == 1 for _, members in soa)
