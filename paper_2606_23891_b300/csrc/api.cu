@@ -23,6 +23,8 @@
 #include "adjoint_kernels.cuh"
 #include "host_batch.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace sph {
 
 static thread_local char g_msg[512] = "";
@@ -86,6 +88,25 @@ static int check_params(const sph_params *p) {
         return fail(SPH_EINVAL, "params: kernel_gamma > 0 and gamma > 1 required");
     return SPH_OK;
 }
+
+// Named host ranges around each stage ("sph/pack/density", ...) for
+// timeline profilers; a push and a pop with no tool attached.
+struct StageRange {
+    explicit StageRange(const char *name) { nvtxRangePushA(name); }
+    ~StageRange() { nvtxRangePop(); }
+    StageRange(const StageRange &) = delete;
+    StageRange &operator=(const StageRange &) = delete;
+};
+static const char *stage_name(int stage, int loop) {
+    static const char *names[5][3] = {
+        {"sph/pack/density", "sph/pack/gradient", "sph/pack/force"},
+        {"sph/interact/density", "sph/interact/gradient", "sph/interact/force"},
+        {"sph/unpack/density", "sph/unpack/gradient", "sph/unpack/force"},
+        {"sph/list_build", "sph/list_build", "sph/list_build"},
+        {"sph/adjoint", "sph/adjoint", "sph/adjoint"}};
+    return names[stage][loop >= 0 && loop < 3 ? loop : 0];
+}
+enum { ST_PACK, ST_INTERACT, ST_UNPACK, ST_LIST, ST_ADJOINT };
 
 // Host-side fault injection (tests of the error paths; no device fault):
 // the armed site fails on its countdown-th use, once.
@@ -530,6 +551,7 @@ int sph_init(sph_store s, int loop, const sph_params *p, void *stream) {
 }
 
 int sph_pack(sph_store s, sph_tasks t, int loop, int bundle, void *dev_buf_in, void *stream) {
+    StageRange range_(stage_name(ST_PACK, loop));
     if (int rc = check_store(s)) return rc;
     if (int rc = check_tasks(t, bundle)) return rc;
     if (int rc = check_loop(loop)) return rc;
@@ -557,6 +579,7 @@ int sph_pack(sph_store s, sph_tasks t, int loop, int bundle, void *dev_buf_in, v
 
 static int interact(sph_tasks t, int loop, int bundle, const void *in, void *out,
                     const sph_params *p, unsigned long long *count, void *stream) {
+    StageRange range_(stage_name(ST_INTERACT, loop));
     if (int rc = check_tasks(t, bundle)) return rc;
     if (int rc = check_params(p)) return rc;
     if (!in || !aligned256(in))
@@ -618,6 +641,7 @@ int sph_count_pairs(sph_tasks t, int loop, int bundle, const void *dev_buf_in,
 
 int sph_unpack(sph_store s, sph_tasks t, int loop, int bundle, const void *dev_buf_out,
                void *stream) {
+    StageRange range_(stage_name(ST_UNPACK, loop));
     if (int rc = check_store(s)) return rc;
     if (int rc = check_tasks(t, bundle)) return rc;
     if (int rc = check_loop(loop)) return rc;
@@ -1048,6 +1072,7 @@ int sph_batch_pack_list(sph_store s, sph_batch b, int loop, int bundle, void *de
 
 static int batch_pack(sph_store s, sph_batch b, int loop, int bundle, void *dev_buf_in,
                       const sph_params *p, void *stream, bool compact) {
+    StageRange range_(stage_name(ST_PACK, loop));
     if (int rc = check_store(s)) return rc;
     if (int rc = check_batch(b, bundle)) return rc;
     if (int rc = check_loop(loop)) return rc;
@@ -1118,6 +1143,7 @@ static BInteractArgs interact_args(sph_batch b, int bundle, const void *dev_buf_
 
 int sph_batch_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in,
                        void *dev_buf_out, const sph_params *p, void *stream) {
+    StageRange range_(stage_name(ST_INTERACT, loop));
     if (int rc = check_batch(b, bundle)) return rc;
     if (int rc = check_loop(loop)) return rc;
     if (int rc = check_params(p)) return rc;
@@ -1138,6 +1164,7 @@ int sph_batch_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in
 static int batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const void *dev_buf_out,
                         const void *dev_buf_in, bool write, bool ghost, const sph_params *p,
                         void *stream) {
+    StageRange range_(stage_name(ST_UNPACK, loop));
     if (int rc = check_store(s)) return rc;
     if (int rc = check_batch(b, bundle)) return rc;
     if (int rc = check_loop(loop)) return rc;
@@ -1390,6 +1417,7 @@ int sph_batch_list_build(sph_store s, sph_batch b, void *dev_buf_in, void *dev_l
 int sph_batch_list_build_bundle(sph_store s, sph_batch b, int bundle, const void *dev_buf_in,
                                 void *dev_list, size_t list_bytes, const sph_params *p,
                                 void *stream) {
+    StageRange range_(stage_name(ST_LIST, 0));
     if (int rc = check_store(s)) return rc;
     if (int rc = check_batch(b, bundle)) return rc;
     if (int rc = check_params(p)) return rc;
@@ -1428,6 +1456,7 @@ int sph_batch_list_status(const void *dev_list, int64_t *chunks_needed, int *ove
 int sph_batch_list_interact(sph_batch b, int loop, int bundle, const void *dev_buf_in,
                             void *dev_buf_out, const void *dev_list, size_t list_bytes,
                             const sph_params *p, void *stream) {
+    StageRange range_(stage_name(ST_INTERACT, loop));
     if (int rc = check_batch(b, bundle)) return rc;
     if (int rc = check_loop(loop)) return rc;
     if (int rc = check_params(p)) return rc;
@@ -1522,6 +1551,7 @@ int sph_batch_adjoint(sph_store s, sph_batch b, void *dev_buf_in, const void *de
                       const int64_t *dev_store_perm, const float *dev_abar,
                       const float *dev_ebar, double *dev_gx, float *dev_gm, float *dev_gu,
                       const sph_params *p, void *stream) {
+    StageRange range_(stage_name(ST_ADJOINT, 0));
     if (int rc = check_store(s)) return rc;
     if (!b) return fail(SPH_EINVAL, "NULL batch handle");
     if (int rc = check_params(p)) return rc;
