@@ -55,7 +55,7 @@ NCU_TRAFFIC = {
     # from one ncu capture, valid while the kernel's source file is unchanged
     ("plain", "kernel", 2): {"bytes_per_unit": 92.1, "src": "e4b699e728bdf76e",
                              "file": "physics_kernels.cuh"},
-    ("list", "list", 0): {"bytes_per_unit": 493.1, "src": "67b5c99eb0ab3fb9",
+    ("list", "list", 0): {"bytes_per_unit": 492.8, "src": "f67e8fb660a57d8c",
                           "file": "list_kernels.cuh"},
 }
 # bytes per particle of the batched pack records (nf float4 + index lanes)

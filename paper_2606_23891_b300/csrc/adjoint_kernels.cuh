@@ -257,7 +257,8 @@ __global__ void __launch_bounds__(128, 4) k_adj_pairs(AdjArgs a) {
         auto next_ent = [&]() -> uint32_t {
             uint32_t e = 0u;
             if (kl < cnt)
-                e = __ldg(&a.L.entries[(long long)chunk * kLChunk + (kl % kLPer) * 32 + lane]);
+                e = __ldg(&a.L.entries[checked(chunk, (long long)a.L.pool) * kLChunk +
+                                       (kl % kLPer) * 32 + lane]);
             ++kl;
             if (kl % kLPer == 0 && kl < maxc) chunk = a.L.next[chunk];
             return e;
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(128, 4) k_adj_pairs(AdjArgs a) {
         if (un) {
 #pragma unroll
             for (int f = 0; f < kAdjRec; ++f)
-                nxt[f] = __ldg(&a.rec[kAdjRec * (long long)(e & 0x7fffffffu) + f]);
+                nxt[f] = __ldg(&a.rec[kAdjRec * checked(e & 0x7fffffffu, a.S) + f]);
         }
         e = next_ent();
 #pragma unroll 1
@@ -282,7 +283,7 @@ __global__ void __launch_bounds__(128, 4) k_adj_pairs(AdjArgs a) {
             if (un) {
 #pragma unroll
                 for (int f = 0; f < kAdjRec; ++f)
-                    nxt[f] = __ldg(&a.rec[kAdjRec * (long long)(e & 0x7fffffffu) + f]);
+                    nxt[f] = __ldg(&a.rec[kAdjRec * checked(e & 0x7fffffffu, a.S) + f]);
             }
             en = e;
             e = next_ent();
@@ -310,7 +311,8 @@ __global__ void __launch_bounds__(128, 4) k_adj_pairs(AdjArgs a) {
                     gx += gd[0]; gy += gd[1]; gz += gd[2];
                 }
                 if (r2 < oth[0].w * oth[0].w) {  // r < H_j: own in the partner's sums
-                    const float4 oS = __ldg(&a.sg[2 * js]), oR = __ldg(&a.sg[2 * js + 1]);
+                    const float4 oS = __ldg(&a.sg[2 * checked(js, a.S)]),
+                                 oR = __ldg(&a.sg[2 * checked(js, a.S) + 1]);
                     gm += density_back(oth, oS, oR, own, -dx, -dy, -dz, r2, gd);
                     gx -= gd[0]; gy -= gd[1]; gz -= gd[2];
                 }

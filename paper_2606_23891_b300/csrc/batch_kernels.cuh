@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(128) k_bpack(BPackArgs a) {
         float4 r[BL::nf];
         float hf;
         make_record<LOOP, COMPACT>(a, p, r, hf);
-        const long long sl = (long long)C.slot + pos;
+        const long long sl = checked((long long)C.slot + pos, a.S);
         for (int f = 0; f < nf; ++f)
             reinterpret_cast<float4 *>(a.buf + BL::rec(f, a.S))[sl] = r[f];
         reinterpret_cast<int32_t *>(a.buf + BL::perm(a.S))[sl] = (int32_t)p;
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(128) k_bunpack(BUnpackArgs a) {
     const BCellDev C = a.cells[a.targets[blockIdx.x].cell];
     const long long r16 = (a.S * 16 + 255) / 256 * 256;
     for (int k = threadIdx.x; k < C.n; k += blockDim.x) {
-        const long long sl = (long long)C.slot + k;
+        const long long sl = checked((long long)C.slot + k, a.S);
         const long long p = a.perm[sl];
         auto base = [&](const CompPtr &d) { return WRITE ? 0.f : ld<float>(d, p); };
         if constexpr (LOOP == SPH_DENSITY) {

@@ -10,10 +10,27 @@ namespace sph {
 constexpr float kPi = 3.14159265358979323846f;
 constexpr float kNorm = 8.0f / kPi;  // cubic spline normalisation for support H
 
-// Latched kernel error word, read back by sph_sync (bit 0: bounds, bit 1: a
-// bounded wait ran out).
+// Latched kernel error word, read back by sph_sync (bit 0: an index out of
+// bounds, bit 1: a bounded wait ran out, bit 2: the neighbour-list pool ran
+// out).
 // All device code is compiled as one translation unit (api.cu).
 __device__ unsigned int g_error_word = 0;
+
+// Index check of the checked build (-DSPH_CHECK, libsph_check.so): an index
+// outside [0, bound) latches bit 0 of the error word (SPH_EBOUNDS at
+// sph_sync) and is replaced by 0, so the access stays inside the buffer.
+// The default build compiles the check away.
+__device__ __forceinline__ long long checked(long long i, long long bound) {
+#ifdef SPH_CHECK
+    if (i < 0 || i >= bound) {
+        atomicOr(&g_error_word, 1u);
+        return 0;
+    }
+#else
+    (void)bound;
+#endif
+    return i;
+}
 
 template <typename T>
 __device__ __forceinline__ T ld(const CompPtr &c, long long p) {

@@ -104,8 +104,8 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
         const long long slot = (long long)C.slot + i;
         float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0;
         if (valid) {
-            o0 = rec0[slot];
-            o1 = rec1[slot];
+            o0 = rec0[checked(slot, a.S)];
+            o1 = rec1[checked(slot, a.S)];
         }
         const float Hi = o0.w;
         const float H2i = Hi * Hi;
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
                     const int k = 32 * w + lane;
                     bool in = false;
                     if (k < jn) {
-                        const long long js = (long long)Cn.slot + j0 + k;
+                        const long long js = checked((long long)Cn.slot + j0 + k, a.S);
                         float4 r0 = rec0[js], r1 = rec1[js];
                         if (code != kSelf) {
                             add2(r0.x, r1.x, sh[0], sl[0]);
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
                         if (!(dens || r2 < fmaxf(H2i, p1.w))) continue;
                         if (!lost) {
                             const uint32_t js = (uint32_t)(Cn.slot + j0 + j);
-                            L.entries[(long long)chain[count / kLPer] * kLChunk +
+                            L.entries[checked(chain[count / kLPer], (long long)L.pool) * kLChunk +
                                       (count % kLPer) * 32 + lane] = js | (dens ? 0x80000000u : 0u);
                         }
                         ++count;
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
         bool active = false;
         if (valid) {
 #pragma unroll
-            for (int f = 0; f < nf; ++f) own[f] = rec[f][slot];
+            for (int f = 0; f < nf; ++f) own[f] = rec[f][checked(slot, a.S)];
             if constexpr (LOOP == SPH_DENSITY) acc.init(own, a.delta);
             else acc.init(own, a.delta, a.pa);
             active = LOOP != SPH_FORCE ||
@@ -393,7 +393,8 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
         auto next_ent = [&]() -> uint32_t {
             uint32_t e = 0u;
             if (kl < cnt)
-                e = __ldg(&L.entries[(long long)chunk * kLChunk + (kl % kLPer) * 32 + lane]);
+                e = __ldg(&L.entries[checked(chunk, (long long)L.pool) * kLChunk +
+                                     (kl % kLPer) * 32 + lane]);
             ++kl;
             if (kl % kLPer == 0 && kl < maxc) chunk = L.next[chunk];
             return e;
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
         };
         auto gather = [&](float4 *o, uint32_t e) {
 #pragma unroll
-            for (int f = 0; f < nf; ++f) o[f] = __ldg(&rec[f][e & 0x7fffffffu]);
+            for (int f = 0; f < nf; ++f) o[f] = __ldg(&rec[f][checked(e & 0x7fffffffu, a.S)]);
         };
         auto pair = [&](float4 *oth) {
             // periodic image: the hi-part separation exceeds half the box

@@ -12,7 +12,10 @@ import ctypes as C
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsph.so")
+# SPH_CHECKED_BUILD=1 selects the index-checked build (python -m
+# paper_2606_23891_b300.build --check), for tests of the kernels' bounds.
+LIB_PATH = os.path.join(_HERE, "libsph_check.so" if os.environ.get("SPH_CHECKED_BUILD") == "1"
+                        else "libsph.so")
 
 SPH_AOS, SPH_AOS_RANDOM, SPH_SAOS_PACK_GRAD, SPH_SAOS_PACK_FORCE, \
     SPH_SAOS_PACK_SHARED, SPH_SAOS_PACK_GRAD_TYPE, SPH_SAOS_PACK_FORCE_TYPE, \
@@ -87,8 +90,9 @@ def lib() -> C.CDLL:
     if _lib is not None:
         return _lib
     if not os.path.exists(LIB_PATH):
-        raise ImportError("libsph.so is not built; run "
-                          "`python -m paper_2606_23891_b300.build`")
+        raise ImportError("%s is not built; run `python -m paper_2606_23891_b300.build%s`"
+                          % (os.path.basename(LIB_PATH),
+                             " --check" if LIB_PATH.endswith("_check.so") else ""))
     L = C.CDLL(LIB_PATH)
     p, i, i64, u64, sz = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_size_t
     sig = {
