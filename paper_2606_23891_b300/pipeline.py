@@ -350,12 +350,21 @@ class Offload:
     def list_step(self) -> None:
         """Lists, then density -> ghost -> gradient -> force over them, in one
         library call (the density pack serves the list build too).  The first
-        call sizes the list pool with a separate build."""
+        call sizes the list pool with a separate build.  Later steps only
+        enqueue: if moved particles need more list entries than the pool
+        holds, the step's loops skip all pairs and the next sph_sync raises
+        SPH_ENOMEM; resize() then regrows the pool for the next step."""
         if getattr(self, "blist", None) is None:
             self.list_build()
         sph.sph_batch_offload_step_list(self.store, self.bplan, self.bbuf_in.data_ptr(),
                                         self.bbuf_out.data_ptr(), self.blist.data_ptr(),
                                         self.blist_bytes, self.params, self.stream)
+
+    def resize(self) -> None:
+        """Size the list pool again for the current positions (one
+        synchronous build and status read)."""
+        self.blist = None
+        self.list_build()
 
     def close_batch(self) -> None:
         self.f64_in = self.f64_out = None

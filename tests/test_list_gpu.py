@@ -276,3 +276,30 @@ def test_one_call_step_rejects_misuse_before_any_work():
                                    off.bbuf_in.data_ptr(), off.params, stream=st)
     sph.sph_sync(st)
     assert np.array_equal(off.store_bytes(), before)
+
+
+def test_list_pool_regrows_after_the_supports_grow():
+    """Supports grown by 20% need about 1.7x the list entries: the enqueued
+    step reports SPH_ENOMEM at sph_sync, resize() regrows the pool, and the
+    next step equals a fresh offload of the same inputs."""
+    f = ragged(12, 80)
+    off = Offload(f, layout=6)
+    off.batch()
+    off.list_step()
+    sph.sph_sync(off.stream)
+    g = {k: v.copy() for k, v in f.items()}
+    g["h"] = (f["h"] * 1.2).astype(np.float32)
+    off.import_fields(g, ("h",))
+    off.list_step()
+    with pytest.raises(sph.SphError) as e:
+        sph.sph_sync(off.stream)
+    assert e.value.status == 2
+    off.resize()
+    off.list_step()
+    got = off.export()
+    ref = Offload(g, layout=6)
+    ref.batch()
+    ref.list_step()
+    want = ref.export()
+    for k in want:
+        np.testing.assert_array_equal(got[k], want[k], err_msg=k)
