@@ -59,7 +59,10 @@ NCU_TRAFFIC = {
                           "file": "list_kernels.cuh"},
 }
 # bytes per particle of the batched pack records (nf float4 + index lanes)
-BATCH_REC = (3 * 16 + 4, 4 * 16 + 4, 5 * 16 + 9)
+# (the density pack also writes the list loop's two fixed-point lanes; the
+# list pipeline's gradient and force packs write compact records)
+BATCH_REC = (5 * 16 + 4, 4 * 16 + 4, 5 * 16 + 9)
+LIST_REC = (5 * 16 + 4, 3 * 16 + 4, 4 * 16 + 9)
 CSRC = os.path.join(ROOT, "paper_2606_23891_b300", "csrc")
 
 
@@ -821,7 +824,8 @@ def run_ours(args, ws, rank, local):
                 pack_b = slots * 2 * VIEW_IN[l]
                 unpack_b = slots * VIEW_OUT[l] + n * 2 * VIEW_OUT[l]
             else:  # each particle packed once; one result per particle
-                pack_b = bslots * (VIEW_IN[l] + BATCH_REC[l])
+                rec = LIST_REC if pipeline == "list" else BATCH_REC
+                pack_b = bslots * (VIEW_IN[l] + rec[l])
                 unpack_b = n * VIEW_OUT[l] + n * 2 * VIEW_OUT[l]
             loops[LOOP_NAMES[l]] = {
                 "pack_ms": pk, "kernel_ms": kr, "unpack_ms": up,
@@ -941,7 +945,8 @@ def run_ours(args, ws, rank, local):
             bpl = (slots * 2 * VIEW_IN[loop] if stage == "pack"
                    else slots * VIEW_OUT[loop] + n * 2 * VIEW_OUT[loop]) / per_step
         else:
-            bpl = (bslots * (VIEW_IN[loop] + BATCH_REC[loop]) if stage == "pack"
+            rec = LIST_REC if args.head_pipeline == "list" else BATCH_REC
+            bpl = (bslots * (VIEW_IN[loop] + rec[loop]) if stage == "pack"
                    else n * 3 * VIEW_OUT[loop]) / per_step
         achieved = bpl / (dur * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6400.0)

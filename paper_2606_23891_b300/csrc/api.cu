@@ -1085,6 +1085,7 @@ static int batch_pack(sph_store s, sph_batch b, int loop, int bundle, void *dev_
     a.cells = b->d_cells + bb.cell0;
     a.buf = (char *)dev_buf_in;
     a.S = bb.slots;
+    for (int d = 0; d < 3; ++d) a.fx_scale[d] = 4294967296.0 / b->box[d];
     const int roles[R_NUM][2] = {{F_X, 0}, {F_X, 1}, {F_X, 2}, {F_V, 0}, {F_V, 1},
                                  {F_V, 2}, {F_MASS, 0}, {F_H, 0}, {F_U, 0}, {F_RHO, 0},
                                  {F_FGRADH, 0}, {F_BALS, 0}, {F_AVISC, 0}, {F_ADIFF, 0},
@@ -1131,6 +1132,7 @@ static BInteractArgs interact_args(sph_batch b, int bundle, const void *dev_buf_
         a.shift_hi[d] = (float)b->box[d];
         a.shift_lo[d] = (float)(b->box[d] - (double)a.shift_hi[d]);
         a.half[d] = (float)(0.5 * b->box[d]);
+        a.fx_unit[d] = (float)(b->box[d] / 4294967296.0);
     }
     a.active_bin = p->active_bin;
     a.pa.beta = a.beta;

@@ -25,14 +25,18 @@ constexpr int kBTile = 128;   // j records staged per tile (4 mask words)
 constexpr int kBSortMax = 2048;  // cells larger than this keep store order
 
 // Lanes of a batched pack buffer of S slots and C cells: nf record lanes
-// (float4), the store index of each slot (int32), the activity byte (force),
-// h f / rho (force, for dh/dt), then the per-cell support maximum (float).
+// (float4), for the density loop two more lanes holding its fixed-point
+// gather record (fx), the store index of each slot (int32), the activity
+// byte (force), h f / rho (force, for dh/dt), then the per-cell support
+// maximum (float).
 template <int LOOP>
 struct BLayout {
     static constexpr int nf = NF<LOOP>::value;
+    static constexpr int nlanes = LOOP == SPH_DENSITY ? nf + 2 : nf;
     static __host__ __device__ int64_t r256(int64_t b) { return (b + 255) / 256 * 256; }
     static __host__ __device__ int64_t rec(int f, int64_t S) { return r256(S * 16) * f; }
-    static __host__ __device__ int64_t perm(int64_t S) { return rec(nf, S); }
+    static __host__ __device__ int64_t fx(int k, int64_t S) { return rec(nf + k, S); }
+    static __host__ __device__ int64_t perm(int64_t S) { return rec(nlanes, S); }
     static __host__ __device__ int64_t tb(int64_t S) { return perm(S) + r256(S * 4); }
     static __host__ __device__ int64_t hf(int64_t S) { return tb(S) + r256(S); }
     static __host__ __device__ int64_t cellh(int64_t S) { return hf(S) + r256(S * 4); }
@@ -50,6 +54,7 @@ struct BPackArgs {
     const BCellDev *cells;
     char *buf;
     long long S;
+    double fx_scale[3];   // 2^32 / box edge: fixed-point position units
     CompPtr src[R_NUM];
     float kernel_gamma, gamma, delta;
 };
@@ -75,8 +80,20 @@ struct StoreSrc {
 
 // Compact records of the neighbour-list loops, which gather whole j records
 // per pair (fewer float4 lanes gathered; c and P are recomputed from u, rho):
-//   gradient: [0] hi H  [1] lo m/rho  [2] v u
+//   gradient: [0] X m/rho  [1] v u  [2] H (own particle only, not gathered)
 //   force:    [0] hi 1/H  [1] lo m  [2] v u  [3] rho  A = f P / rho^2  alpha_visc B  alpha_diff
+// The density pack adds the density loop's gather record in its fx lanes:
+//   [fx0] X m  [fx1] v 0
+// X is the position in 32-bit fixed point (x / box 2^32, modulo 2^32, the
+// bits stored in the float slots): the difference of two such words, read as
+// a signed integer, is the minimum-image separation in units of box / 2^32,
+// exact before its conversion to float, so the periodic image comes for free.
+__device__ __forceinline__ float fixed_coord(double x, double scale) {
+    return __uint_as_float((unsigned int)(unsigned long long)__double2ll_rn(x * scale));
+}
+__device__ __forceinline__ float fixed_sep(float xi, float xj, float unit) {
+    return (float)(int)(__float_as_uint(xi) - __float_as_uint(xj)) * unit;
+}
 template <int LOOP>
 struct NFC {
     static constexpr int value = LOOP == SPH_DENSITY ? 3 : (LOOP == SPH_GRADIENT ? 3 : 4);
@@ -96,12 +113,15 @@ __device__ __forceinline__ void make_record(const BPackArgs &a, long long p, flo
     const float H = a.kernel_gamma * h;
     if (LOOP == SPH_DENSITY) u = 0.f;
     if (COMPACT && LOOP != SPH_DENSITY) {
-        r[1] = make_float4(lx, ly, lz, LOOP == SPH_GRADIENT ? vm.w / rho : vm.w);
-        r[2] = make_float4(vm.x, vm.y, vm.z, u);
         hf = 0.f;
         if (LOOP == SPH_GRADIENT) {
-            r[0] = make_float4(hx, hy, hz, H);
+            r[0] = make_float4(fixed_coord(x[0], a.fx_scale[0]), fixed_coord(x[1], a.fx_scale[1]),
+                               fixed_coord(x[2], a.fx_scale[2]), vm.w / rho);
+            r[1] = make_float4(vm.x, vm.y, vm.z, u);
+            r[2] = make_float4(H, 0.f, 0.f, 0.f);
         } else {
+            r[1] = make_float4(lx, ly, lz, vm.w);
+            r[2] = make_float4(vm.x, vm.y, vm.z, u);
             const float P = (a.gamma - 1.f) * rho * u;
             r[0] = make_float4(hx, hy, hz, 1.f / H);
             r[3] = make_float4(rho, fgh * P / (rho * rho), av * bal, ad);
@@ -245,6 +265,12 @@ __global__ void __launch_bounds__(128) k_bpack(BPackArgs a) {
         for (int f = 0; f < nf; ++f)
             reinterpret_cast<float4 *>(a.buf + BL::rec(f, a.S))[sl] = r[f];
         reinterpret_cast<int32_t *>(a.buf + BL::perm(a.S))[sl] = (int32_t)p;
+        if (LOOP == SPH_DENSITY) {
+            float X[3];
+            for (int d = 0; d < 3; ++d) X[d] = fixed_coord(ld<double>(a.src[R_X0 + d], p), a.fx_scale[d]);
+            reinterpret_cast<float4 *>(a.buf + BL::fx(0, a.S))[sl] = make_float4(X[0], X[1], X[2], r[1].w);
+            reinterpret_cast<float4 *>(a.buf + BL::fx(1, a.S))[sl] = make_float4(r[2].x, r[2].y, r[2].z, 0.f);
+        }
         if (LOOP == SPH_FORCE) {
             reinterpret_cast<int8_t *>(a.buf + BL::tb(a.S))[sl] = ld<int8_t>(a.src[R_TB], p);
             reinterpret_cast<float *>(a.buf + BL::hf(a.S))[sl] = hf;
@@ -265,6 +291,7 @@ struct BInteractArgs {
     float kernel_gamma, gamma, beta, delta;
     float shift_hi[3], shift_lo[3];   // box edge as a two-float value
     float half[3];                    // half the box edge (image choice of the list loops)
+    float fx_unit[3];                 // box edge / 2^32: one fixed-point position unit
     int active_bin;
     PhysArgs pa;  // parameters the pair bodies read (beta)
 };

@@ -18,9 +18,13 @@
 //           places in the pool vary, so results are reproducible.
 // k_bloop   persistent warps over the items again: each lane walks its list,
 //           gathers the j records of the loop's view from the bundle buffer
-//           (read-only path, the list loads running ahead), applies the periodic image shift (decided from
-//           the hi-part separation: supports are below half the box, so the
-//           image is unique) as an exact two-float add, and runs the pair body.
+//           (read-only path, the list loads running ahead) and runs the pair
+//           body.  Density and gradient gather two lanes per pair and take the
+//           separation from 32-bit fixed-point positions, whose integer
+//           difference is the minimum image; the force loop gathers its
+//           two-float record and applies the periodic image shift (decided
+//           from the hi-part separation: supports are below half the box, so
+//           the image is unique) as an exact two-float add.
 //           Lanes' lists differ in length by the neighbour-count scatter only.
 //
 // When the pool runs out, the build marks the list header and the error word
@@ -275,7 +279,9 @@ struct AccL<SPH_GRADIENT> {
     __device__ __forceinline__ void body(const float4 *own, const float4 *oth, float dx,
                                          float dy, float dz, float r2, const PhysArgs &a) {
         const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-        const float q = r2 * rinv * Hinv;
+        // clamped: the list was decided on two-float separations, this
+        // fixed-point one may round a support-edge pair to just past q = 1
+        const float q = fminf(r2 * rinv * Hinv, 1.f);
         float w, dw;
         spline(q, w, dw);
         const float wdot = ((own[2].x - oth[2].x) * dx + (own[2].y - oth[2].y) * dy +
@@ -360,6 +366,14 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
     const float4 *rec[nf];
 #pragma unroll
     for (int f = 0; f < nf; ++f) rec[f] = reinterpret_cast<const float4 *>(a.in + BL::rec(f, a.S));
+    // the two gathered lanes of the density and gradient loops: a fixed-point
+    // position with one scalar, and v with u (see the compact records)
+    const float4 *g0 = LOOP == SPH_DENSITY
+                           ? reinterpret_cast<const float4 *>(a.in + BLayout<SPH_DENSITY>::fx(0, a.S))
+                           : rec[0];
+    const float4 *g1 = LOOP == SPH_DENSITY
+                           ? reinterpret_cast<const float4 *>(a.in + BLayout<SPH_DENSITY>::fx(1, a.S))
+                           : rec[1 % nf];
     const bool broken = L.hdr->overflow != 0u;
     for (;;) {
         int it = 0;
@@ -373,11 +387,27 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
         const bool valid = i < C.n;
         const long long slot = (long long)C.slot + i;
         float4 own[nf];
+        float ox = 0.f, oy = 0.f, oz = 0.f;  // own fixed-point position (density, gradient)
         AccL<LOOP> acc;
         bool active = false;
         if (valid) {
 #pragma unroll
             for (int f = 0; f < nf; ++f) own[f] = rec[f][checked(slot, a.S)];
+            if constexpr (LOOP == SPH_GRADIENT) {
+                // to the record form the pair body reads: [0].w H, [1].w m/rho, [2] v u
+                const float4 r0 = own[0], r1 = own[1], r2 = own[2];
+                ox = r0.x;
+                oy = r0.y;
+                oz = r0.z;
+                own[0] = make_float4(0.f, 0.f, 0.f, r2.x);
+                own[1] = make_float4(0.f, 0.f, 0.f, r0.w);
+                own[2] = r1;
+            } else if constexpr (LOOP == SPH_DENSITY) {
+                const float4 X = g0[checked(slot, a.S)];
+                ox = X.x;
+                oy = X.y;
+                oz = X.z;
+            }
             if constexpr (LOOP == SPH_DENSITY) acc.init(own, a.delta);
             else acc.init(own, a.delta, a.pa);
             active = LOOP != SPH_FORCE ||
@@ -447,15 +477,26 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
                 if (u) pair(oth);
             }
         } else {
+            // density and gradient: two gathered lanes per pair; the
+            // separation from the fixed-point positions (minimum image by the
+            // integer wrap-around)
             uint32_t e = next_ent();
 #pragma unroll 1
             for (int k = 0; k < maxc; ++k) {
                 const uint32_t cur = e;
                 e = next_ent();
                 if (!uses(cur, k)) continue;
+                const long long js = checked(cur & 0x7fffffffu, a.S);
+                const float4 j0 = __ldg(&g0[js]), j1 = __ldg(&g1[js]);
+                const float dx = fixed_sep(ox, j0.x, a.fx_unit[0]);
+                const float dy = fixed_sep(oy, j0.y, a.fx_unit[1]);
+                const float dz = fixed_sep(oz, j0.z, a.fx_unit[2]);
                 float4 oth[nf];
-                gather(oth, cur);
-                pair(oth);
+                oth[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+                oth[1] = make_float4(0.f, 0.f, 0.f, j0.w);
+                oth[2] = j1;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                acc.body(own, oth, dx, dy, dz, r2, a.pa);
             }
         }
         if (valid) {

@@ -116,7 +116,9 @@ struct Acc<SPH_DENSITY> {
                                          float dy, float dz, float r2, const PhysArgs &) {
         const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
         const float r = r2 * rinv;
-        const float q = r * Hinv;
+        // clamped at the support edge: the list loop's fixed-point separation
+        // may round a pair the list admitted (r < H) to just past q = 1
+        const float q = fminf(r * Hinv, 1.f);
         float w, dw;
         spline(q, w, dw);
         const float mj = oth[1].w;

@@ -1,6 +1,6 @@
 """Neighbour-list variant of the batched cycle: the same results as the tile
-kernels (to the rounding order of r^2) and as the oracle, on the grid and
-the tree plans; pool sizing and its overflow report."""
+kernels (to the rounding of the separations) and as the oracle, on the grid
+and the tree plans; pool sizing and its overflow report."""
 import numpy as np
 import pytest
 
@@ -25,6 +25,10 @@ def test_list_pass_matches_the_oracle(case, threads):
 
 @pytest.mark.parametrize("mtc", [0, 37])
 def test_list_agrees_with_the_tile_kernels(mtc):
+    """The list loops of density and gradient take separations from 32-bit
+    fixed-point positions (one unit = box / 2^32, then one float rounding),
+    the tile kernels from two-float ones: the results agree to a few 1e-7 of
+    each field's rms, up to about 1e-6 in the cancelling sum of div v."""
     f = ragged(24, 8)
     off = Offload(f, layout=6)
     off.batch(max_target_cells=mtc)
@@ -33,7 +37,7 @@ def test_list_agrees_with_the_tile_kernels(mtc):
     off.list_step()
     b = off.export()
     for k in a:
-        assert rms_err(b[k], a[k]) <= 1e-6, k
+        assert rms_err(b[k], a[k]) <= 5e-6, k
 
 
 def test_list_on_the_tree_plan_and_inactive_particles():
