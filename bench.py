@@ -55,7 +55,7 @@ NCU_TRAFFIC = {
     # from one ncu capture, valid while the kernel's source file is unchanged
     ("plain", "kernel", 2): {"bytes_per_unit": 92.1, "src": "e4b699e728bdf76e",
                              "file": "physics_kernels.cuh"},
-    ("list", "list", 0): {"bytes_per_unit": 492.8, "src": "f67e8fb660a57d8c",
+    ("list", "list", 0): {"bytes_per_unit": 493.2, "src": "772f1f75265704a8",
                           "file": "list_kernels.cuh"},
 }
 # bytes per particle of the batched pack records (nf float4 + index lanes)
