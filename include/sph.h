@@ -461,6 +461,11 @@ int sph_tree_plan(int64_t n, const double *host_x, const float *host_h,
 /* info[0] plan kind (0 grid, 1 tree), [1] cells or leaves with particles,
  * [2] largest cell / leaf population, [3] neighbour entries (all cells). */
 int sph_batch_plan_info(sph_batch b, int64_t info[4]);
+/* 1 when the plan's list build decides pairs on 32-bit fixed-point
+ * separations (every cell or leaf extent plus the largest support is below
+ * half the box, so minimum images are unambiguous), 0 when it uses two-float
+ * separations with the entries' periodic shifts; -SPH_EINVAL for NULL. */
+int sph_batch_list_fixed(sph_batch b);
 /* Pair interactions of `loop` over the plan, decided in FP64 as the loops
  * define them (density and gradient: r < H_i; force: r < max(H_i, H_j),
  * active i only), added to *dev_count (device uint64).  Uses dev_buf_in of

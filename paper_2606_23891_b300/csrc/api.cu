@@ -258,13 +258,22 @@ int dispatch_bloop(sph_batch b, const BInteractArgs &a, const ListView &L, long 
     return dispatch_bloop_w<LOOP, kLLoopWarpsGrid>(b->threads, a, L, item0, st);
 }
 
-inline int dispatch_blist(int threads, const BInteractArgs &a, const ListView &L, long long item0,
-                          cudaStream_t st) {
+template <bool FIXED>
+inline int dispatch_blist_p(int threads, const BInteractArgs &a, const ListView &L,
+                            long long item0, cudaStream_t st) {
     if (threads == 64)
-        return launch_persistent(k_blist<64>, 64, a.nitems, st, "list build", a, L, item0);
+        return launch_persistent(k_blist<64, FIXED>, 64, a.nitems, st, "list build", a, L, item0);
     if (threads == 256)
-        return launch_persistent(k_blist<256>, 256, a.nitems, st, "list build", a, L, item0);
-    return launch_persistent(k_blist<128>, 128, a.nitems, st, "list build", a, L, item0);
+        return launch_persistent(k_blist<256, FIXED>, 256, a.nitems, st, "list build", a, L,
+                                 item0);
+    return launch_persistent(k_blist<128, FIXED>, 128, a.nitems, st, "list build", a, L, item0);
+}
+
+// The list build takes the fixed-point path where the plan allows it.
+inline int dispatch_blist(sph_batch b, const BInteractArgs &a, const ListView &L,
+                          long long item0, cudaStream_t st) {
+    if (b->fixed_build) return dispatch_blist_p<true>(b->threads, a, L, item0, st);
+    return dispatch_blist_p<false>(b->threads, a, L, item0, st);
 }
 
 template <int LOOP>
@@ -1021,6 +1030,11 @@ int sph_tree_plan(int64_t n, const double *host_x, const float *host_h,
     }
 }
 
+int sph_batch_list_fixed(sph_batch b) {
+    if (!b) return -fail(SPH_EINVAL, "NULL batch handle");
+    return b->fixed_build ? 1 : 0;
+}
+
 int sph_batch_plan_info(sph_batch b, int64_t info[4]) {
     if (!b || !info) return fail(SPH_EINVAL, "NULL argument");
     info[0] = b->kind;
@@ -1441,7 +1455,7 @@ int sph_batch_list_build_bundle(sph_store s, sph_batch b, int bundle, const void
     if (int rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st),
                             "reset work queue"))
         return rc;
-    return dispatch_blist(b->threads, a, L, bb.item0, st);
+    return dispatch_blist(b, a, L, bb.item0, st);
 }
 
 int sph_batch_list_status(const void *dev_list, int64_t *chunks_needed, int *overflow) {

@@ -157,6 +157,9 @@ int build_batch(const sph_tasks_s *T, const sph_batch_params *bp, sph_batch_s *B
     B->n = T->n;
     B->kind = 0;
     for (int d = 0; d < 3; ++d) B->box[d] = T->box[d];
+    // cells are at least the largest support, so extent + support <= 2 cells:
+    // below half the box when every dimension has 5 or more cells
+    B->fixed_build = nc[0] >= 5 && nc[1] >= 5 && nc[2] >= 5;
 
     // cells with particles, in grid index order
     GlobalPlan G;
@@ -439,6 +442,34 @@ int build_batch_tree(int64_t n, const double *x, const float *h, const sph_tree_
     B->n = n;
     B->kind = 1;
     for (int d = 0; d < 3; ++d) B->box[d] = tp->box[d];
+    // largest leaf extent (per dimension) and support, for the list build's
+    // fixed-point path
+    double e0 = 0.0, e1 = 0.0, e2 = 0.0;
+    float Hmax = 0.f;
+    const float kg = (float)tp->kernel_gamma;
+#pragma omp parallel for reduction(max : Hmax)
+    for (int64_t i = 0; i < n; ++i) Hmax = std::max(Hmax, kg * h[i]);
+    const int64_t nleaf = (int64_t)G.cnt.size();
+#pragma omp parallel for schedule(dynamic, 256) reduction(max : e0, e1, e2)
+    for (int64_t l = 0; l < nleaf; ++l) {
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t k = G.p0[(size_t)l]; k < G.p0[(size_t)l] + G.cnt[(size_t)l]; ++k) {
+            const int64_t i = perm_out[k];
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], x[3 * i + d]);
+                hi[d] = std::max(hi[d], x[3 * i + d]);
+            }
+        }
+        if (G.cnt[(size_t)l] > 0) {
+            e0 = std::max(e0, hi[0] - lo[0]);
+            e1 = std::max(e1, hi[1] - lo[1]);
+            e2 = std::max(e2, hi[2] - lo[2]);
+        }
+    }
+    const double ext[3] = {e0, e1, e2};
+    B->fixed_build = true;
+    for (int d = 0; d < 3; ++d)
+        B->fixed_build = B->fixed_build && ext[d] + (double)Hmax + 1e-6 * tp->box[d] < 0.5 * tp->box[d];
     return assemble(G, bp, B);
 }
 

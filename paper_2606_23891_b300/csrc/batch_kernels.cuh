@@ -82,8 +82,9 @@ struct StoreSrc {
 // per pair (fewer float4 lanes gathered; c and P are recomputed from u, rho):
 //   gradient: [0] X m/rho  [1] v u  [2] H (own particle only, not gathered)
 //   force:    [0] hi 1/H  [1] lo m  [2] v u  [3] rho  A = f P / rho^2  alpha_visc B  alpha_diff
-// The density pack adds the density loop's gather record in its fx lanes:
-//   [fx0] X m  [fx1] v 0
+// The density pack adds the density loop's gather record in its fx lanes
+// (fx0 alone also serves the fixed-point list build):
+//   [fx0] X H  [fx1] v m
 // X is the position in 32-bit fixed point (x / box 2^32, modulo 2^32, the
 // bits stored in the float slots): the difference of two such words, read as
 // a signed integer, is the minimum-image separation in units of box / 2^32,
@@ -268,8 +269,8 @@ __global__ void __launch_bounds__(128) k_bpack(BPackArgs a) {
         if (LOOP == SPH_DENSITY) {
             float X[3];
             for (int d = 0; d < 3; ++d) X[d] = fixed_coord(ld<double>(a.src[R_X0 + d], p), a.fx_scale[d]);
-            reinterpret_cast<float4 *>(a.buf + BL::fx(0, a.S))[sl] = make_float4(X[0], X[1], X[2], r[1].w);
-            reinterpret_cast<float4 *>(a.buf + BL::fx(1, a.S))[sl] = make_float4(r[2].x, r[2].y, r[2].z, 0.f);
+            reinterpret_cast<float4 *>(a.buf + BL::fx(0, a.S))[sl] = make_float4(X[0], X[1], X[2], r[0].w);
+            reinterpret_cast<float4 *>(a.buf + BL::fx(1, a.S))[sl] = make_float4(r[2].x, r[2].y, r[2].z, r[1].w);
         }
         if (LOOP == SPH_FORCE) {
             reinterpret_cast<int8_t *>(a.buf + BL::tb(a.S))[sl] = ld<int8_t>(a.src[R_TB], p);

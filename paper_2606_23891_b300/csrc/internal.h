@@ -153,6 +153,9 @@ struct sph_batch_s {
     std::vector<BNbrDev> nbrs;
     int64_t max_slots = 0, max_targets = 0;
     int kind = 0;                 // 0: uniform cell grid, 1: adaptive octree leaves
+    // the list build may use fixed-point separations: every cell or leaf
+    // extent plus the largest support stays below half the box
+    bool fixed_build = false;
     int64_t plan_cells = 0, plan_max_cell = 0, plan_nbrs = 0;
     BCellDev *d_cells = nullptr;
     BTargetDev *d_targets = nullptr;

@@ -81,7 +81,16 @@ struct ListLayout {
 };
 
 // ---------------------------------------------------------------- build --
-template <int T>
+// FIXED: positions from the density pack's fixed-point lane (X, H).  The
+// prefilter and the box cull use floats relative to the item's first
+// particle (the difference of fixed-point words is the minimum image, so no
+// shift is applied) and the exact decisions use the fixed-point differences
+// themselves.  Chosen by the plan when every cell or leaf extent plus the
+// largest support stays below half the box: then the image nearest the
+// item's first particle is the image nearest each of its particles for every
+// pair that can interact, and no cell enters a target's entries twice.
+// Otherwise the two-float path: hi/lo records, shifts by the entry codes.
+template <int T, bool FIXED>
 __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView L, long long item0) {
     using BL = BLayout<SPH_DENSITY>;
     constexpr int kWarps = T / 32;
@@ -107,7 +116,17 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
         const bool valid = i < C.n;
         const long long slot = (long long)C.slot + i;
         float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0;
-        if (valid) {
+        const float4 *fxs = reinterpret_cast<const float4 *>(a.in + BL::fx(0, a.S));
+        unsigned int rx = 0u, ry = 0u, rz = 0u;   // FIXED: the item's reference position
+        if constexpr (FIXED) {
+            if (valid) o1 = fxs[checked(slot, a.S)];   // (X, H) of this particle
+            rx = __shfl_sync(0xffffffffu, __float_as_uint(o1.x), 0);
+            ry = __shfl_sync(0xffffffffu, __float_as_uint(o1.y), 0);
+            rz = __shfl_sync(0xffffffffu, __float_as_uint(o1.z), 0);
+            o0 = make_float4(fixed_sep(o1.x, __uint_as_float(rx), a.fx_unit[0]),
+                             fixed_sep(o1.y, __uint_as_float(ry), a.fx_unit[1]),
+                             fixed_sep(o1.z, __uint_as_float(rz), a.fx_unit[2]), o1.w);
+        } else if (valid) {
             o0 = rec0[checked(slot, a.S)];
             o1 = rec1[checked(slot, a.S)];
         }
@@ -162,11 +181,21 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
                     bool in = false;
                     if (k < jn) {
                         const long long js = checked((long long)Cn.slot + j0 + k, a.S);
-                        float4 r0 = rec0[js], r1 = rec1[js];
-                        if (code != kSelf) {
-                            add2(r0.x, r1.x, sh[0], sl[0]);
-                            add2(r0.y, r1.y, sh[1], sl[1]);
-                            add2(r0.z, r1.z, sh[2], sl[2]);
+                        float4 r0, r1;
+                        if constexpr (FIXED) {
+                            r1 = fxs[js];   // (X, H): the exact pass reads X back
+                            r0 = make_float4(fixed_sep(r1.x, __uint_as_float(rx), a.fx_unit[0]),
+                                             fixed_sep(r1.y, __uint_as_float(ry), a.fx_unit[1]),
+                                             fixed_sep(r1.z, __uint_as_float(rz), a.fx_unit[2]),
+                                             r1.w);
+                        } else {
+                            r0 = rec0[js];
+                            r1 = rec1[js];
+                            if (code != kSelf) {
+                                add2(r0.x, r1.x, sh[0], sl[0]);
+                                add2(r0.y, r1.y, sh[1], sl[1]);
+                                add2(r0.z, r1.z, sh[2], sl[2]);
+                            }
                         }
                         const float Hj = r0.w, Hjp = Hj + a.delta;
                         r1.w = Hj * Hj;
@@ -236,9 +265,16 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
                         const int j = 32 * w + (__ffs(m) - 1);
                         m &= m - 1;
                         const float4 p0 = sm[0][j], p1 = sm[1][j];
-                        const float dx = (o0.x - p0.x) + (o1.x - p1.x);
-                        const float dy = (o0.y - p0.y) + (o1.y - p1.y);
-                        const float dz = (o0.z - p0.z) + (o1.z - p1.z);
+                        float dx, dy, dz;
+                        if constexpr (FIXED) {
+                            dx = fixed_sep(o1.x, p1.x, a.fx_unit[0]);
+                            dy = fixed_sep(o1.y, p1.y, a.fx_unit[1]);
+                            dz = fixed_sep(o1.z, p1.z, a.fx_unit[2]);
+                        } else {
+                            dx = (o0.x - p0.x) + (o1.x - p1.x);
+                            dy = (o0.y - p0.y) + (o1.y - p1.y);
+                            dz = (o0.z - p0.z) + (o1.z - p1.z);
+                        }
                         const float r2 = dx * dx + dy * dy + dz * dz;
                         const bool dens = r2 < H2i;
                         if (!(dens || r2 < fmaxf(H2i, p1.w))) continue;
@@ -367,7 +403,7 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
 #pragma unroll
     for (int f = 0; f < nf; ++f) rec[f] = reinterpret_cast<const float4 *>(a.in + BL::rec(f, a.S));
     // the two gathered lanes of the density and gradient loops: a fixed-point
-    // position with one scalar, and v with u (see the compact records)
+    // position with one scalar, and v with one scalar (see the records)
     const float4 *g0 = LOOP == SPH_DENSITY
                            ? reinterpret_cast<const float4 *>(a.in + BLayout<SPH_DENSITY>::fx(0, a.S))
                            : rec[0];
@@ -493,7 +529,8 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
                 const float dz = fixed_sep(oz, j0.z, a.fx_unit[2]);
                 float4 oth[nf];
                 oth[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-                oth[1] = make_float4(0.f, 0.f, 0.f, j0.w);
+                // m_j (density: fx1.w) or m_j / rho_j (gradient: record 0 .w)
+                oth[1] = make_float4(0.f, 0.f, 0.f, LOOP == SPH_DENSITY ? j1.w : j0.w);
                 oth[2] = j1;
                 const float r2 = dx * dx + dy * dy + dz * dz;
                 acc.body(own, oth, dx, dy, dz, r2, a.pa);

@@ -141,6 +141,7 @@ def lib() -> C.CDLL:
         "sph_batch_list_bytes": (sz, [p, i64]),
         "sph_batch_list_build": (i, [p, p, p, p, sz, p, p]),
         "sph_batch_list_build_bundle": (i, [p, p, i, p, p, sz, p, p]),
+        "sph_batch_list_fixed": (i, [p]),
         "sph_batch_list_status": (i, [p, p, p]),
         "sph_batch_offload_loop_list": (i, [p, p, i, p, p, p, sz, p, p]),
         "sph_batch_offload_step_list": (i, [p, p, p, p, p, sz, p, p]),
@@ -429,6 +430,13 @@ def sph_batch_list_build_bundle(s, b, bundle: int, dev_in: int, dev_list: int,
                                 list_bytes: int, p: Params, stream: int = 0):
     _ok(lib().sph_batch_list_build_bundle(s, b, bundle, dev_in, dev_list, list_bytes,
                                           C.byref(p), stream))
+
+
+def sph_batch_list_fixed(b) -> bool:
+    r = lib().sph_batch_list_fixed(b)
+    if r < 0:
+        _ok(-r)
+    return r == 1
 
 
 def sph_batch_list_status(dev_list: int):

@@ -31,6 +31,7 @@ def keep(tag, off):
                             "v_sig")).items():
         out[tag + "/" + k] = v
 cases = [("grid", ragged(12, 71), {}, 0), ("grid3", ragged(12, 72), {}, 37),
+         ("grid8", ragged(24, 73), {}, 0),
          ("tree", ics.lognormal(n_side=24, seed=31), {"plan": "tree"}, 101)]
 for tag, f, kw, mtc in cases:
     off = Offload(f, layout="pack_force_type", **kw)

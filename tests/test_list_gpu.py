@@ -307,3 +307,17 @@ def test_list_pool_regrows_after_the_supports_grow():
     want = ref.export()
     for k in want:
         np.testing.assert_array_equal(got[k], want[k], err_msg=k)
+
+
+def test_list_build_path_follows_the_plan_geometry():
+    """Four cells per dimension leave too little room for unambiguous images
+    relative to an item's first particle, so the build keeps two-float
+    separations; eight cells allow the fixed-point path.  Both match the
+    oracle."""
+    cases = [(ragged(12, 90), False), (ragged(24, 91), True)]
+    for f, fixed in cases:
+        off = Offload(f, layout=6)
+        off.batch()
+        assert sph.sph_batch_list_fixed(off.bplan) == fixed
+        off.list_step()
+        check_physics(f, off.export())
