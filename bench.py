@@ -55,7 +55,7 @@ NCU_TRAFFIC = {
     # from one ncu capture, valid while the kernel's source file is unchanged
     ("plain", "kernel", 2): {"bytes_per_unit": 92.1, "src": "e4b699e728bdf76e",
                              "file": "physics_kernels.cuh"},
-    ("list", "list", 0): {"bytes_per_unit": 493.2, "src": "772f1f75265704a8",
+    ("list", "list", 0): {"bytes_per_unit": 442.7, "src": "1a89b69ceeca8ec8",
                           "file": "list_kernels.cuh"},
 }
 # bytes per particle of the batched pack records (nf float4 + index lanes)
