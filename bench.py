@@ -55,14 +55,15 @@ NCU_TRAFFIC = {
     # from one ncu capture, valid while the kernel's source file is unchanged
     ("plain", "kernel", 2): {"bytes_per_unit": 92.1, "src": "e4b699e728bdf76e",
                              "file": "physics_kernels.cuh"},
-    ("list", "list", 0): {"bytes_per_unit": 442.7, "src": "1a89b69ceeca8ec8",
+    ("list", "list", 0): {"bytes_per_unit": 442.7, "src": "38dbb0532f6e1d63",
                           "file": "list_kernels.cuh"},
 }
 # bytes per particle of the batched pack records (nf float4 + index lanes)
 # (the density pack also writes the list loop's two fixed-point lanes; the
-# list pipeline's gradient and force packs write compact records)
+# list pipeline's packs write compact records, for density on plans with the
+# fixed-point list build only those two lanes, as at Gresho256)
 BATCH_REC = (5 * 16 + 4, 4 * 16 + 4, 5 * 16 + 9)
-LIST_REC = (5 * 16 + 4, 3 * 16 + 4, 4 * 16 + 9)
+LIST_REC = (2 * 16 + 4, 3 * 16 + 4, 4 * 16 + 9)
 CSRC = os.path.join(ROOT, "paper_2606_23891_b300", "csrc")
 
 

@@ -1115,7 +1115,11 @@ static int batch_pack(sph_store s, sph_batch b, int loop, int bundle, void *dev_
     const unsigned g = (unsigned)bb.ncells;
     // one CTA per cell; 64 threads suit cells of a few dozen particles
     // (measured against 128: faster on the uniform and the clustered sets)
-    if (loop == SPH_DENSITY) k_bpack<SPH_DENSITY><<<g, 64, 0, st>>>(a);
+    // the list loops' density pack writes only the fixed-point lanes where the
+    // list build reads nothing else (plans on the fixed-point path)
+    if (loop == SPH_DENSITY && compact && b->fixed_build)
+        k_bpack<SPH_DENSITY, true><<<g, 64, 0, st>>>(a);
+    else if (loop == SPH_DENSITY) k_bpack<SPH_DENSITY><<<g, 64, 0, st>>>(a);
     else if (loop == SPH_GRADIENT && compact) k_bpack<SPH_GRADIENT, true><<<g, 64, 0, st>>>(a);
     else if (loop == SPH_GRADIENT) k_bpack<SPH_GRADIENT><<<g, 64, 0, st>>>(a);
     else if (compact) k_bpack<SPH_FORCE, true><<<g, 64, 0, st>>>(a);

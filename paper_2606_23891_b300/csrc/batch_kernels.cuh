@@ -79,7 +79,8 @@ struct StoreSrc {
 };
 
 // Compact records of the neighbour-list loops, which gather whole j records
-// per pair (fewer float4 lanes gathered; c and P are recomputed from u, rho):
+// per pair (fewer float4 lanes gathered; c and P are recomputed from u, rho;
+// the compact density pack writes only its two fixed-point lanes):
 //   gradient: [0] X m/rho  [1] v u  [2] H (own particle only, not gathered)
 //   force:    [0] hi 1/H  [1] lo m  [2] v u  [3] rho  A = f P / rho^2  alpha_visc B  alpha_diff
 // The density pack adds the density loop's gather record in its fx lanes
@@ -96,8 +97,8 @@ __device__ __forceinline__ float fixed_sep(float xi, float xj, float unit) {
     return (float)(int)(__float_as_uint(xi) - __float_as_uint(xj)) * unit;
 }
 template <int LOOP>
-struct NFC {
-    static constexpr int value = LOOP == SPH_DENSITY ? 3 : (LOOP == SPH_GRADIENT ? 3 : 4);
+struct NFC {   // density: none besides the fixed-point lanes
+    static constexpr int value = LOOP == SPH_DENSITY ? 0 : (LOOP == SPH_GRADIENT ? 3 : 4);
 };
 
 template <int LOOP, bool COMPACT = false>

@@ -397,7 +397,11 @@ template <int LOOP, int T, int WARPS>
 __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
     k_bloop(BInteractArgs a, ListView L, long long item0) {
     using BL = BLayout<LOOP>;
-    constexpr int nf = NFC<LOOP>::value;     // compact records (k_bpack<LOOP, true>)
+    // compact records (k_bpack<LOOP, true>); the density loop reads only its
+    // fixed-point lanes and lays them out as the three-lane record its pair
+    // body reads
+    constexpr int nr = NFC<LOOP>::value;
+    constexpr int nf = nr > 0 ? nr : 3;
     const int lane = threadIdx.x & 31;
     const float4 *rec[nf];
 #pragma unroll
@@ -428,7 +432,7 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
         bool active = false;
         if (valid) {
 #pragma unroll
-            for (int f = 0; f < nf; ++f) own[f] = rec[f][checked(slot, a.S)];
+            for (int f = 0; f < nr; ++f) own[f] = rec[f][checked(slot, a.S)];
             if constexpr (LOOP == SPH_GRADIENT) {
                 // to the record form the pair body reads: [0].w H, [1].w m/rho, [2] v u
                 const float4 r0 = own[0], r1 = own[1], r2 = own[2];
@@ -439,10 +443,14 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
                 own[1] = make_float4(0.f, 0.f, 0.f, r0.w);
                 own[2] = r1;
             } else if constexpr (LOOP == SPH_DENSITY) {
-                const float4 X = g0[checked(slot, a.S)];
+                // [0].w H, [2] v: the fields the density body reads of its own
+                const float4 X = g0[checked(slot, a.S)], V = g1[checked(slot, a.S)];
                 ox = X.x;
                 oy = X.y;
                 oz = X.z;
+                own[0] = make_float4(0.f, 0.f, 0.f, X.w);
+                own[1] = make_float4(0.f, 0.f, 0.f, V.w);
+                own[2] = make_float4(V.x, V.y, V.z, 0.f);
             }
             if constexpr (LOOP == SPH_DENSITY) acc.init(own, a.delta);
             else acc.init(own, a.delta, a.pa);
