@@ -55,7 +55,7 @@ NCU_TRAFFIC = {
     # from one ncu capture, valid while the kernel's source file is unchanged
     ("plain", "kernel", 2): {"bytes_per_unit": 92.1, "src": "e4b699e728bdf76e",
                              "file": "physics_kernels.cuh"},
-    ("list", "list", 0): {"bytes_per_unit": 442.7, "src": "38dbb0532f6e1d63",
+    ("list", "list", 0): {"bytes_per_unit": 433.4, "src": "7e6555dfb8bf883e",
                           "file": "list_kernels.cuh"},
 }
 # bytes per particle of the batched pack records (nf float4 + index lanes)

@@ -7,10 +7,9 @@
 //
 // k_blist   persistent warps over the same work items: stage neighbour tiles,
 //           cull by the warp box, prefilter on hi-only separations, take the
-//           exact two-float decision of both loop criteria (r < H_i for
-//           density and gradient, r < max(H_i, H_j) for force) and append
-//           each accepted j's bundle slot to the lane's list, bit 31 set when
-//           r < H_i.  Lists are stored in chunks of 64 entries per lane for
+//           exact decision of both loop criteria (r < H_i for density and
+//           gradient, r < max(H_i, H_j) for force) and append each accepted
+//           j's bundle slot to the lane's list, bit 31 set when r < H_i.  Lists are stored in chunks of 64 entries per lane for
 //           the 32 lanes of an item (lane-interleaved, so the loops read them
 //           coalesced); chunks come from a pool through an atomic counter
 //           and are chained per item.  The content and order of each list
@@ -84,8 +83,10 @@ struct ListLayout {
 // FIXED: positions from the density pack's fixed-point lane (X, H).  The
 // prefilter and the box cull use floats relative to the item's first
 // particle (the difference of fixed-point words is the minimum image, so no
-// shift is applied) and the exact decisions use the fixed-point differences
-// themselves.  Chosen by the plan when every cell or leaf extent plus the
+// shift is applied).  The decisions are those of the fixed-point differences
+// themselves: a hit whose relative-float separation lies a margin inside H_i
+// meets both criteria there too and is accepted from the prefilter; only the
+// others are tested on the fixed-point words.  Chosen by the plan when every cell or leaf extent plus the
 // largest support stays below half the box: then the image nearest the
 // item's first particle is the image nearest each of its particles for every
 // pair that can interact, and no cell enters a target's entries twice.
@@ -134,6 +135,11 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
         const float H2i = Hi * Hi;
         const float Hpre = Hi + a.delta;
         const float Hpre2 = Hpre * Hpre;
+        // FIXED: below (H_i - delta)^2 on the relative floats a pair is inside
+        // H_i on the fixed-point separation too (their difference is a few
+        // 1e-7 of the box, delta is 4e-6 of it), so it meets both criteria
+        const float Hs = fmaxf(Hi - a.delta, 0.f);
+        const float Hs2 = Hs * Hs;
         float bmn[3], bmx[3], hw;
         bmn[0] = valid ? o0.x : INFINITY; bmx[0] = valid ? o0.x : -INFINITY;
         bmn[1] = valid ? o0.y : INFINITY; bmx[1] = valid ? o0.y : -INFINITY;
@@ -210,12 +216,13 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
                     cw[w] = __ballot_sync(0xffffffffu, in);
                 }
                 __syncwarp();
-                // pass 1: hi-only prefilter under the wider (force) criterion
-                unsigned int hm[kWTile / 32];
+                // pass 1: hi-only prefilter under the wider (force) criterion;
+                // FIXED: also the hits certainly inside H_i
+                unsigned int hm[kWTile / 32], sure[kWTile / 32];
                 int nh = 0;
 #pragma unroll
                 for (int w = 0; w < kWTile / 32; ++w) {
-                    unsigned int m = cw[w], h = 0;
+                    unsigned int m = cw[w], h = 0, su = 0;
                     while (m) {     // two candidates per iteration (the second may repeat the first)
                         const int b = __ffs(m) - 1;
                         m &= m - 1;
@@ -226,12 +233,35 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
                         const float ex = o0.x - pk.x, ey = o0.y - pk.y, ez = o0.z - pk.z;
                         const float r2 = dx * dx + dy * dy + dz * dz;
                         const float s2 = ex * ex + ey * ey + ez * ez;
-                        h |= (r2 < fmaxf(Hpre2, pj.w) ? (1u << b) : 0u) |
-                             (s2 < fmaxf(Hpre2, pk.w) ? (1u << b2) : 0u);
+                        const unsigned int bj = 1u << b, bk = 1u << b2;
+                        h |= (r2 < fmaxf(Hpre2, pj.w) ? bj : 0u) | (s2 < fmaxf(Hpre2, pk.w) ? bk : 0u);
+                        if constexpr (FIXED) su |= (r2 < Hs2 ? bj : 0u) | (s2 < Hs2 ? bk : 0u);
                     }
                     if (self && (i - j0) >= 32 * w && (i - j0) < 32 * w + 32)
                         h &= ~(1u << (i - j0 - 32 * w));
                     hm[w] = valid ? h : 0u;
+                    sure[w] = su & hm[w];
+                }
+                // FIXED: the exact decisions on the other hits (dm: r < H_i);
+                // hm keeps the accepted ones, in slot order
+                unsigned int dm[kWTile / 32];
+#pragma unroll
+                for (int w = 0; w < kWTile / 32; ++w) {
+                    dm[w] = sure[w];
+                    if constexpr (FIXED) {
+                        unsigned int m = hm[w] & ~sure[w];
+                        while (m) {
+                            const int b = __ffs(m) - 1;
+                            m &= m - 1;
+                            const float4 p1 = sm[1][32 * w + b];
+                            const float dx = fixed_sep(o1.x, p1.x, a.fx_unit[0]);
+                            const float dy = fixed_sep(o1.y, p1.y, a.fx_unit[1]);
+                            const float dz = fixed_sep(o1.z, p1.z, a.fx_unit[2]);
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 < H2i) dm[w] |= 1u << b;
+                            else if (!(r2 < fmaxf(H2i, p1.w))) hm[w] &= ~(1u << b);
+                        }
+                    }
                     nh += __popc(hm[w]);
                 }
                 // room for up to nh more entries in every lane's chain; once
@@ -257,33 +287,44 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
                     if (c == kLNone) lost = true;
                     ++nch;
                 }
-                // exact decisions on the hits, appended in slot order
+                if constexpr (FIXED) {
+                    // the accepted hits, appended in slot order
+#pragma unroll
+                    for (int w = 0; w < kWTile / 32; ++w) {
+                        unsigned int m = hm[w];
+                        while (m) {
+                            const int b = __ffs(m) - 1;
+                            m &= m - 1;
+                            if (!lost) {
+                                const uint32_t js = (uint32_t)(Cn.slot + j0 + 32 * w + b);
+                                L.entries[checked(chain[count / kLPer], (long long)L.pool) * kLChunk +
+                                          (count % kLPer) * 32 + lane] = js | ((dm[w] >> b) & 1u) << 31;
+                            }
+                            ++count;
+                        }
+                    }
+                } else {
+                    // exact two-float decisions on the hits, appended in slot order
 #pragma unroll 1
-                for (int w = 0; w < kWTile / 32; ++w) {
-                    unsigned int m = hm[w];
-                    while (m) {
-                        const int j = 32 * w + (__ffs(m) - 1);
-                        m &= m - 1;
-                        const float4 p0 = sm[0][j], p1 = sm[1][j];
-                        float dx, dy, dz;
-                        if constexpr (FIXED) {
-                            dx = fixed_sep(o1.x, p1.x, a.fx_unit[0]);
-                            dy = fixed_sep(o1.y, p1.y, a.fx_unit[1]);
-                            dz = fixed_sep(o1.z, p1.z, a.fx_unit[2]);
-                        } else {
-                            dx = (o0.x - p0.x) + (o1.x - p1.x);
-                            dy = (o0.y - p0.y) + (o1.y - p1.y);
-                            dz = (o0.z - p0.z) + (o1.z - p1.z);
+                    for (int w = 0; w < kWTile / 32; ++w) {
+                        unsigned int m = hm[w];
+                        while (m) {
+                            const int j = 32 * w + (__ffs(m) - 1);
+                            m &= m - 1;
+                            const float4 p0 = sm[0][j], p1 = sm[1][j];
+                            const float dx = (o0.x - p0.x) + (o1.x - p1.x);
+                            const float dy = (o0.y - p0.y) + (o1.y - p1.y);
+                            const float dz = (o0.z - p0.z) + (o1.z - p1.z);
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            const bool dens = r2 < H2i;
+                            if (!(dens || r2 < fmaxf(H2i, p1.w))) continue;
+                            if (!lost) {
+                                const uint32_t js = (uint32_t)(Cn.slot + j0 + j);
+                                L.entries[checked(chain[count / kLPer], (long long)L.pool) * kLChunk +
+                                          (count % kLPer) * 32 + lane] = js | (dens ? 0x80000000u : 0u);
+                            }
+                            ++count;
                         }
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        const bool dens = r2 < H2i;
-                        if (!(dens || r2 < fmaxf(H2i, p1.w))) continue;
-                        if (!lost) {
-                            const uint32_t js = (uint32_t)(Cn.slot + j0 + j);
-                            L.entries[checked(chain[count / kLPer], (long long)L.pool) * kLChunk +
-                                      (count % kLPer) * 32 + lane] = js | (dens ? 0x80000000u : 0u);
-                        }
-                        ++count;
                     }
                 }
             }
