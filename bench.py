@@ -180,11 +180,11 @@ def precision_study(off, f, sel, ref, steps, mixed_step):
     import torch
     import oracle
     from oracle import compare
-    H = oracle.KERNEL_GAMMA * np.asarray(f["h"][sel], np.float64)
+    sc = oracle.dh_scales(f, oracle.params(), sel)
     res = {"sample": int(len(sel))}
     mixed_step()
     got = off.export()
-    e = compare.errors({k: v[sel] for k, v in got.items()}, ref, H)
+    e = compare.errors({k: v[sel] for k, v in got.items()}, ref, sc)
     res["mixed"] = {"per_loop": compare.per_loop(e), "fields": e}
     off.fp64_step()                                   # warm-up (allocates buffers)
     torch.cuda.synchronize()
@@ -197,7 +197,7 @@ def precision_study(off, f, sel, ref, steps, mixed_step):
     torch.cuda.synchronize()
     res["fp64_ms_per_step"] = e0.elapsed_time(e1) / steps
     got = off.export()
-    e = compare.errors({k: v[sel] for k, v in got.items()}, ref, H)
+    e = compare.errors({k: v[sel] for k, v in got.items()}, ref, sc)
     res["fp64"] = {"per_loop": compare.per_loop(e), "fields": e}
     res["metrics"] = ("relative error for rho, wcount, f_gradh, pressure, soundspeed, "
                       "v_sig; err / (3 rho / H) and err / max(|x|, 3 wcount / H) for the "

@@ -11,16 +11,27 @@ Parity status of each function (what pins it is in the tests):
                          counts, sinusoidal div/curl fields)
   gradient               pinned (closed form v_sig = 2c, sinusoidal Laplacian)
   force                  pinned (momentum and energy conservation, lattice
-                         symmetry, dh/dt = (h/3) f div v identity)
+                         symmetry, dh/dt = (h/3) f div v identity; magnitudes:
+                         pressure force = -grad of the thermal energy by
+                         central differences of the density sum, adiabatic
+                         du/dt and dh/dt from the density's rate along the
+                         flow, the continuum pressure gradient of a
+                         sinusoidal u, viscous heating >= 0 and zero in
+                         receding flow, a two-particle viscosity closed form)
+  dh_scales              tolerance scales, not results (bounded below by the
+                         sums they scale, equal to them when no term cancels)
   grid / tasks / bundles pinned (library KD-tree pair coverage)
   pack / unpack          pinned (minimum-image positions, bincount sums)
   store layouts          pinned (ctypes struct offsets, paper's 160 B record)
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
+import shutil
 import subprocess
+import tempfile
 
 import numpy as np
 
@@ -68,49 +79,90 @@ class Fields(C.Structure):
 _lib = None
 
 
+def _bind(L):
+    d, i64, p = C.c_double, C.c_int64, C.c_void_p
+    for name in ("oracle_w", "oracle_dw"):
+        getattr(L, name).restype = d
+        getattr(L, name).argtypes = [d]
+    for name in ("oracle_W", "oracle_dWdr", "oracle_dWdH"):
+        getattr(L, name).restype = d
+        getattr(L, name).argtypes = [d, d]
+    L.oracle_density.restype = i64
+    L.oracle_density.argtypes = [i64, p, p, p, p, p, i64, p, p]
+    L.oracle_dh_scales.restype = None
+    L.oracle_dh_scales.argtypes = [i64, p, p, p, p, i64, p, p]
+    L.oracle_ghost.restype = None
+    L.oracle_ghost.argtypes = [i64, p, p, p, p, p, p, p]
+    L.oracle_gradient.restype = i64
+    L.oracle_gradient.argtypes = [i64, p, p, p, p, p, p, p, i64, p, p]
+    L.oracle_force.restype = i64
+    L.oracle_force.argtypes = [i64] + [p] * 13 + [p, i64, p, p]
+    L.oracle_grid.restype = C.c_int
+    L.oracle_grid.argtypes = [i64, p, p, p, d, p, p, p, p]
+    L.oracle_tasks.restype = i64
+    L.oracle_tasks.argtypes = [p, p, p, p, p]
+    L.oracle_bundles.restype = i64
+    L.oracle_bundles.argtypes = [i64, p, p, p, i64, p]
+    L.oracle_buffer_bytes.restype = i64
+    L.oracle_buffer_bytes.argtypes = [C.c_int, C.c_int, i64]
+    L.oracle_pack.restype = C.c_int
+    L.oracle_pack.argtypes = [C.c_int, p, p, p, p, p, p, i64, i64, p, p]
+    L.oracle_unpack.restype = C.c_int
+    L.oracle_unpack.argtypes = [C.c_int, p, i64, p, p, p, p, i64, i64, p]
+    L.oracle_splitmix64.restype = C.c_uint64
+    L.oracle_splitmix64.argtypes = [p]
+    L.oracle_layout_group.restype = C.c_int
+    L.oracle_layout_group.argtypes = [C.c_int, C.c_uint64, C.c_int, p, p, p, p]
+    L.oracle_layout_ngroups.restype = C.c_int
+    L.oracle_layout_ngroups.argtypes = [C.c_int, C.c_uint64]
+    L.oracle_store_bytes.restype = i64
+    L.oracle_store_bytes.argtypes = [C.c_int, C.c_uint64, i64]
+    L.oracle_store_encode.restype = C.c_int
+    L.oracle_store_encode.argtypes = [C.c_int, C.c_uint64, i64, p, p, p]
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
-        L = C.CDLL(build())
-        d, i64, p = C.c_double, C.c_int64, C.c_void_p
-        for name in ("oracle_w", "oracle_dw"):
-            getattr(L, name).restype = d
-            getattr(L, name).argtypes = [d]
-        for name in ("oracle_W", "oracle_dWdr", "oracle_dWdH"):
-            getattr(L, name).restype = d
-            getattr(L, name).argtypes = [d, d]
-        L.oracle_density.restype = i64
-        L.oracle_density.argtypes = [i64, p, p, p, p, p, i64, p, p]
-        L.oracle_ghost.restype = None
-        L.oracle_ghost.argtypes = [i64, p, p, p, p, p, p, p]
-        L.oracle_gradient.restype = i64
-        L.oracle_gradient.argtypes = [i64, p, p, p, p, p, p, p, i64, p, p]
-        L.oracle_force.restype = i64
-        L.oracle_force.argtypes = [i64] + [p] * 13 + [p, i64, p, p]
-        L.oracle_grid.restype = C.c_int
-        L.oracle_grid.argtypes = [i64, p, p, p, d, p, p, p, p]
-        L.oracle_tasks.restype = i64
-        L.oracle_tasks.argtypes = [p, p, p, p, p]
-        L.oracle_bundles.restype = i64
-        L.oracle_bundles.argtypes = [i64, p, p, p, i64, p]
-        L.oracle_buffer_bytes.restype = i64
-        L.oracle_buffer_bytes.argtypes = [C.c_int, C.c_int, i64]
-        L.oracle_pack.restype = C.c_int
-        L.oracle_pack.argtypes = [C.c_int, p, p, p, p, p, p, i64, i64, p, p]
-        L.oracle_unpack.restype = C.c_int
-        L.oracle_unpack.argtypes = [C.c_int, p, i64, p, p, p, p, i64, i64, p]
-        L.oracle_splitmix64.restype = C.c_uint64
-        L.oracle_splitmix64.argtypes = [p]
-        L.oracle_layout_group.restype = C.c_int
-        L.oracle_layout_group.argtypes = [C.c_int, C.c_uint64, C.c_int, p, p, p, p]
-        L.oracle_layout_ngroups.restype = C.c_int
-        L.oracle_layout_ngroups.argtypes = [C.c_int, C.c_uint64]
-        L.oracle_store_bytes.restype = i64
-        L.oracle_store_bytes.argtypes = [C.c_int, C.c_uint64, i64]
-        L.oracle_store_encode.restype = C.c_int
-        L.oracle_store_encode.argtypes = [C.c_int, C.c_uint64, i64, p, p, p]
-        _lib = L
+        _lib = _bind(C.CDLL(build()))
     return _lib
+
+
+def build_variant(edits) -> str:
+    """Compile a copy of the oracle with text edits applied and return the
+    library's path.  Tests use it to plant a mistake in the oracle (on the
+    CPU) and show that a pin catches it; each ``(old, new)`` edit must match
+    the source exactly once."""
+    with open(_SRC) as fh:
+        src = fh.read()
+    for old, new in edits:
+        if src.count(old) != 1:
+            raise ValueError("edit does not match exactly once: %r" % old)
+        src = src.replace(old, new)
+    d = tempfile.mkdtemp(prefix="oracle_variant_")
+    path = os.path.join(d, "sph_oracle_variant.c")
+    with open(path, "w") as fh:
+        fh.write(src)
+    so = os.path.join(d, "liboracle_variant.so")
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           "-o", so, path, "-lm"])
+    return so
+
+
+@contextlib.contextmanager
+def variant(edits):
+    """Run the oracle's functions on an edited copy for the duration of the
+    block (see build_variant); the real oracle is restored afterwards."""
+    global _lib
+    saved = lib()
+    so = build_variant(edits)
+    try:
+        _lib = _bind(C.CDLL(so))
+        yield
+    finally:
+        _lib = saved
+        shutil.rmtree(os.path.dirname(so), ignore_errors=True)
 
 
 def _p(a):
@@ -162,6 +214,19 @@ def density(f: dict, P: Params, sel=None):
     pairs = lib().oracle_density(n, _p(x), _p(v), _p(m), _p(h), C.byref(P),
                                  ns, _p(s), _p(out))
     return out, pairs
+
+
+def dh_scales(f: dict, P: Params, sel=None):
+    """Conditioning scales of the cancelling h-derivative sums for the
+    selected particles: (rho_dh scale, wcount_dh scale), each the sum of its
+    terms' magnitudes with the self term included (tolerance scales only)."""
+    n = f["x"].shape[0]
+    s, ns = _sel(sel, n)
+    x = _c(f["x"], np.float64)
+    m, h = _c(f["mass"], np.float32), _c(f["h"], np.float32)
+    out = np.zeros((ns, 2), np.float64)
+    lib().oracle_dh_scales(n, _p(x), _p(m), _p(h), C.byref(P), ns, _p(s), _p(out))
+    return out[:, 0], out[:, 1]
 
 
 def ghost(f: dict, P: Params, dens, sel=None):

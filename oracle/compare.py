@@ -2,8 +2,9 @@
 
 One number per output field, each on the scale the parity bars use:
 relative error for the positive sums (rho, wcount, f_gradh, pressure,
-soundspeed, the two signal velocities), the natural scales 3 rho / H and
-max(|wcount_dh|, 3 wcount / H) for the cancelling h-derivatives, max error
+soundspeed, the two signal velocities), the conditioning scales of the
+cancelling h-derivative sums (the sum of their terms' magnitudes, self term
+included: oracle.dh_scales) for rho_dh and wcount_dh, max error
 over the field's rms for the signed vector-like sums (div v, curl v,
 Laplacian of u, a, du/dt, dh/dt), and the absolute error of the Balsara
 switch (a number in [0, 1]).
@@ -26,19 +27,18 @@ def _rel(a, b):
     return np.where(d == 0.0, 0.0, d / np.maximum(np.abs(b), 1e-300))
 
 
-def errors(got: dict, ref: dict, H) -> dict:
+def errors(got: dict, ref: dict, scales) -> dict:
     """Per-field error of ``got`` (arrays indexed like ``ref``) against the
-    oracle's ``ref``; ``H`` is the kernel support of the same particles."""
+    oracle's ``ref``; ``scales`` = oracle.dh_scales of the same particles."""
     g = {k: np.asarray(got[k], np.float64) for k in LOOP_OF}
     r = {k: np.asarray(ref[k], np.float64) for k in LOOP_OF}
-    H = np.asarray(H, np.float64)
+    s_rho, s_w = (np.asarray(s, np.float64) for s in scales)
     out = {}
     for k in RELATIVE:
         out[k] = float(np.max(_rel(g[k], r[k]), initial=0.0))
-    out["rho_dh"] = float(np.max(np.abs(g["rho_dh"] - r["rho_dh"]) / (3 * r["rho"] / H),
-                                 initial=0.0))
-    sc = np.maximum(np.abs(r["wcount_dh"]), 3 * r["wcount"] / H)
-    out["wcount_dh"] = float(np.max(np.abs(g["wcount_dh"] - r["wcount_dh"]) / sc, initial=0.0))
+    out["rho_dh"] = float(np.max(np.abs(g["rho_dh"] - r["rho_dh"]) / s_rho, initial=0.0))
+    out["wcount_dh"] = float(np.max(np.abs(g["wcount_dh"] - r["wcount_dh"]) / s_w,
+                                    initial=0.0))
     for k in RMS:
         s = np.sqrt(np.mean(r[k] * r[k])) if r[k].size else 0.0
         e = float(np.max(np.abs(g[k] - r[k]), initial=0.0))
@@ -54,3 +54,16 @@ def per_loop(err: dict) -> dict:
         loop = LOOP_OF[k]
         res[loop] = max(res.get(loop, 0.0), v)
     return res
+
+
+def relative_distribution(got, ref, scale) -> dict:
+    """Percentiles of |got - ref| / |ref| and of |got - ref| / scale (for a
+    cancelling sum the first is large where the value is near 0)."""
+    g, r = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    d = np.abs(g - r)
+    rel = np.where(d == 0.0, 0.0, d / np.maximum(np.abs(r), 1e-300))
+    cond = d / np.asarray(scale, np.float64)
+    q = (50, 90, 99, 100)
+    return {"rel_to_value": {"p%d" % p: float(np.percentile(rel, p)) for p in q},
+            "rel_to_scale": {"p%d" % p: float(np.percentile(cond, p)) for p in q},
+            "value_over_scale_median": float(np.median(np.abs(r) / np.asarray(scale)))}

@@ -154,6 +154,45 @@ int64_t oracle_density(int64_t n, const double *x, const float *v,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Conditioning scales of the two h-derivative sums of the density loop.     */
+/* Their terms change sign at q = 1/2 and largely cancel, so the value says  */
+/* nothing about the rounding a sum of them can carry; the sum of the terms' */
+/* magnitudes (self term included) does.  These are tolerance scales for    */
+/* comparisons, not results of the method.                                  */
+/*   out[2 k + 0] = m_i |dW/dH(0, H_i)| + sum m_j |dW/dH(r, H_i)|            */
+/*   out[2 k + 1] = the same for the wcount_dh terms                         */
+/*                  (4 pi / 3) |3 H^2 W + H^3 dW/dH|                         */
+/* over j != i with r_ij < H_i.                                              */
+/* ------------------------------------------------------------------------ */
+void oracle_dh_scales(int64_t n, const double *x, const float *m, const float *h,
+                      const oracle_params *P, int64_t nsel, const int64_t *sel,
+                      double *out)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t k = 0; k < nsel; ++k) {
+        int64_t i = sel ? sel[k] : k;
+        double Hi = P->kernel_gamma * (double)h[i];
+        double H2 = Hi * Hi * (1.0 + P->support_eps);
+        double c = 4.0 * ORACLE_PI / 3.0;
+        double s_rho = (double)m[i] * fabs(oracle_dWdH(0.0, Hi));
+        double s_w = c * fabs(3.0 * Hi * Hi * oracle_W(0.0, Hi) +
+                              Hi * Hi * Hi * oracle_dWdH(0.0, Hi));
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3];
+            min_image(&x[3 * i], &x[3 * j], P->box, d);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(r2 < H2)) continue;
+            double r = sqrt(r2);
+            s_rho += (double)m[j] * fabs(oracle_dWdH(r, Hi));
+            s_w += c * fabs(3.0 * Hi * Hi * oracle_W(r, Hi) + Hi * Hi * Hi * oracle_dWdH(r, Hi));
+        }
+        out[2 * k + 0] = s_rho;
+        out[2 * k + 1] = s_w;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Ghost after density (the linear update of Sec. 2.1).                      */
 /*   rho += m_i W(0, H_i); rho_dh += m_i dW/dH(0, H_i); wcount += its self   */
 /*   term; div v = raw / rho; curl v = raw / rho;                            */

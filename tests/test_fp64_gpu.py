@@ -51,13 +51,13 @@ def test_fp64_pass_matches_the_oracle(case, mtc):
     off.fp64_step()
     got64 = off.export()
     ref = oracle.chain(f, oracle.params())
-    H = oracle.KERNEL_GAMMA * np.asarray(f["h"], np.float64)
-    e64 = compare.errors(got64, ref, H)
+    sc = oracle.dh_scales(f, oracle.params())
+    e64 = compare.errors(got64, ref, sc)
     fp64_bars(e64)
     check_physics(f, got64)
     # the mixed path on the same plan: never closer on the positive sums
     off.batch_step()
-    e32 = compare.errors(off.export(), ref, H)
+    e32 = compare.errors(off.export(), ref, sc)
     for k in ("rho", "wcount", "pressure"):
         assert e64[k] <= max(e32[k], 2.5e-7), (k, e64[k], e32[k])
 
@@ -90,8 +90,8 @@ def test_fp64_inactive_particles_and_large_cells():
     assert np.all(got["v_sig"][inactive] == 7.0)
     sel = np.nonzero(~inactive)[0]
     ref = oracle.chain(f, oracle.params(active_bin=2), sel)
-    H = oracle.KERNEL_GAMMA * np.asarray(f["h"][sel], np.float64)
-    fp64_bars(compare.errors({k: v[sel] for k, v in got.items()}, ref, H))
+    sc = oracle.dh_scales(f, oracle.params(active_bin=2), sel)
+    fp64_bars(compare.errors({k: v[sel] for k, v in got.items()}, ref, sc))
 
 
 def test_fp64_steps_are_reproducible():

@@ -622,3 +622,28 @@ def test_store_encoding_reads_back_through_numpy(layout):
             np.testing.assert_array_equal(got.reshape(arr.shape), arr)
         base += (n * rec + 255) // 256 * 256
     assert base == len(img)
+
+
+# ------------------------------------------------- h-derivative scales ---
+def test_dh_scales_bound_the_h_derivative_sums():
+    """The conditioning scales (sums of the terms' magnitudes) bound the
+    h-derivative sums and equal them when no term changes sign: the wcount_dh
+    terms never do (d/dH (H^3 W) = -(sigma/H) q w'(q) >= 0), and the rho_dh
+    terms do not for neighbours inside H/2 (3 w + q w' > 0 there)."""
+    f = _random_box(400, seed=71)
+    P = oracle.params()
+    out = oracle.chain(f, P)
+    s_rho, s_w = oracle.dh_scales(f, P)
+    assert np.all(np.abs(out["rho_dh"]) <= s_rho * (1 + 1e-12))
+    # the terms cancel for most particles of a random set
+    assert np.median(s_rho / np.abs(out["rho_dh"])) > 1.1
+    np.testing.assert_allclose(s_w, np.abs(out["wcount_dh"]), rtol=1e-10)
+    g = ics.empty_fields(2)
+    g["x"][:] = [[0.5, 0.5, 0.5], [0.52, 0.5, 0.5]]
+    g["mass"][:] = 0.25
+    g["h"][:] = 0.05                          # H = 0.091 > 2 x 0.02
+    g["u"][:] = 1.0
+    two = oracle.chain(g, P)
+    s2, w2 = oracle.dh_scales(g, P)
+    np.testing.assert_allclose(s2, np.abs(two["rho_dh"]), rtol=1e-13)
+    np.testing.assert_allclose(w2, np.abs(two["wcount_dh"]), rtol=1e-13)

@@ -172,15 +172,14 @@ def check_physics(f, got, sel=None, box=(1.0, 1.0, 1.0), active_bin=0, bands=Fal
     P = oracle.params(box=box, active_bin=active_bin)
     ref = oracle.chain(f, P, sel)
     g = {k: (v if sel is None else v[sel]) for k, v in got.items()}
-    H = oracle.KERNEL_GAMMA * np.asarray(f["h"] if sel is None else f["h"][sel], np.float64)
     for k in ("rho", "wcount", "f_gradh", "pressure", "soundspeed"):
         assert np.max(rel(g[k], ref[k])) <= 1e-5, k
-    # h-derivatives against their natural scales 3 rho / H and 3 wcount / H
-    # (equal to |value| for ordinary particles; they guard the cases where
-    # the sum cancels or its only terms sit at the support edge)
-    assert np.max(np.abs(g["rho_dh"] - ref["rho_dh"]) / (3 * ref["rho"] / H)) <= 1e-5
-    sc = np.maximum(np.abs(ref["wcount_dh"]), 3 * ref["wcount"] / H)
-    assert np.max(np.abs(g["wcount_dh"] - ref["wcount_dh"]) / sc) <= 1e-5
+    # h-derivatives: their terms change sign inside the support and cancel,
+    # so the bar is relative to the sum of the terms' magnitudes (self term
+    # included), the scale that bounds the rounding of such a sum
+    s_rho, s_w = oracle.dh_scales(f, P, sel)
+    assert np.max(np.abs(g["rho_dh"] - ref["rho_dh"]) / s_rho) <= 1e-5
+    assert np.max(np.abs(g["wcount_dh"] - ref["wcount_dh"]) / s_w) <= 1e-5
     lo = hi = None
     for k in ("v_sig_grad", "v_sig"):
         if np.max(rel(g[k], ref[k])) <= 1e-5 and not bands:

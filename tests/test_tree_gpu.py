@@ -83,8 +83,8 @@ def test_tree_plan_fp64_path_and_inactive_particles():
     assert np.all(got["a"][inactive] == 7.0)
     sel = np.nonzero(~inactive)[0]
     ref = oracle.chain(f, oracle.params(active_bin=2), sel)
-    H = oracle.KERNEL_GAMMA * np.asarray(f["h"][sel], np.float64)
-    fp64_bars(compare.errors({k: v[sel] for k, v in got.items()}, ref, H))
+    sc = oracle.dh_scales(f, oracle.params(active_bin=2), sel)
+    fp64_bars(compare.errors({k: v[sel] for k, v in got.items()}, ref, sc))
 
 
 def test_tree_plan_graph_replay_is_bit_identical():
