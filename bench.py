@@ -2,12 +2,18 @@
 """Benchmark of the SPH cell-pair offload pipeline on one B300.
 
 Workload: the Gresho-vortex shaped set of 256^3 particles (jittered lattice,
-55/73/64/64 particles per cell, the paper's "Gresho256", Sec. 3.4), one step =
-density -> ghost -> gradient -> force, each loop = init + per bundle
-(pack -> interaction kernel -> unpack).  Metric: pair interactions per second
-of the whole step, plus pack+unpack GB/s per loop, for every store layout of
-Sec. 3.1 (sAoS vs AoS).  The headline value is the split (sAoS) layout
-BENCH_LAYOUT.
+55/73/64/64 particles per cell, the paper's "Gresho256", Sec. 3.4).  One
+step = density -> ghost -> gradient -> force over the whole set.  Metric:
+pair interactions per second of the whole step, plus pack+unpack GB/s per
+loop, for a split (sAoS) store against AoS (Sec. 3.1).  The headline is the
+list pipeline on the pack-force-type layout; the paper's per-task cycle
+(pipeline "plain") is timed beside it.
+
+Output: the study sections (measured peaks, link rate, per-layout stage
+times, list-build work counts, host-staged breakdown, precision, ...) as
+one JSON line each, {"section": name, "data": ...}; then, as the LAST line,
+the compact headline (metric, value, e2e, roofline, cpu_baseline, clocks,
+per-loop rates), kept under a few KB.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -40,13 +46,24 @@ LOOP_NAMES = ("density", "gradient", "force")
 # plus output fields read + written per particle (unpack)
 VIEW_IN = (44, 52, 69)
 VIEW_OUT = (32, 8, 24)
-# FP32 operations (FMA = 2) of the implemented formula: per candidate test
-# and per accepted pair of each loop
+# FP32 operations (FADD, FMUL = 1, FFMA = 2) of the implemented formulas.
+# List build, fixed-point plans (the Gresho plan): per staged candidate the
+# three fixed-point separations (1 FMUL each), H_j + delta, two squares and
+# the box distance (6 FADD, r^2 with 1 FMUL + 2 FFMA) = 17; per prefiltered
+# (particle, candidate) pair 3 FADD + r^2 = 8; per exact test the same 8.
+# Two-float plans: per staged candidate the shift (TwoSum, 3 x 8 FADD) and
+# the rest as above = 38; per exact test the two-float separation
+# (3 x 3 FADD) + r^2 = 14.
+FLOPS_STAGE = {True: 17, False: 38}
 FLOPS_CANDIDATE = 8
-FLOPS_EXACT = 14      # two-float separation, r^2 and both loop criteria
+FLOPS_EXACT = {True: 8, False: 14}
 FLOPS_PAIR = (73, 52, 113)
-# FP32 CUDA-core peak: 148 SMs x 128 lanes x 2 flop x 2.032 GHz
-FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# derived FP32 CUDA-core peak (148 SMs x 128 lanes x 2 flop x 2.032 GHz):
+# only a fallback when the measured one is missing
+FP32_PEAK_DERIVED = 148 * 128 * 2 * 2.032e9 / 1e12
+# the headline line is kept below this size (the driver keeps the tail of
+# stdout; study sections go on earlier lines)
+HEADLINE_MAX_BYTES = 2800
 # DRAM bytes per slot of the interaction kernels from an ncu capture of a
 # smaller case (traffic grows with the slots a launch processes), valid only
 # for the kernel source with this digest (else reported as null)
@@ -81,51 +98,188 @@ def measured_peaks() -> dict:
 
 
 # ---------------------------------------------------------------- clocks --
-class ClockSampler:
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+_SAMPLER = r"""
+import sys, time
+import pynvml
+pynvml.nvmlInit()
+uuid, index, period = sys.argv[1], int(sys.argv[2]), float(sys.argv[3])
+try:
+    h = pynvml.nvmlDeviceGetHandleByUUID(uuid)
+except Exception:
+    h = pynvml.nvmlDeviceGetHandleByIndex(index)
+print("max %f" % pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM), flush=True)
+while True:
+    t = time.time()
+    mhz = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
+    rs = pynvml.nvmlDeviceGetCurrentClocksEventReasons(h)
+    print("%.6f %d %d" % (t, mhz, rs), flush=True)
+    time.sleep(period)
+"""
 
-    def __init__(self, index: int):
+
+class ClockSampler:
+    """SM clock and throttle reasons of one GPU, sampled every `period`
+    seconds by a separate process (NVML, read-only queries) that runs for the
+    whole benchmark; start() and stop() mark a timed region on the wall clock
+    and stop() summarises the samples taken inside it."""
+    REASONS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40,
+               "sw_thermal_slowdown": 0x20, "sw_power_cap": 0x4}
+    _shared = {}
+
+    def __init__(self, index: int, period: float = 0.01):
         self.index = index
-        self.proc = None
+        key = (index, period)
+        if key not in ClockSampler._shared:
+            ClockSampler._shared[key] = self._launch(index, period)
+        self.proc, self.samples, self.info = ClockSampler._shared[key]
+        self.t0 = None
+
+    @staticmethod
+    def _launch(index, period):
+        import threading
+        import torch
+        uuid = str(torch.cuda.get_device_properties(index).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        samples, info = [], {"max": 0.0}
+        try:
+            proc = subprocess.Popen([sys.executable, "-c", _SAMPLER, uuid, str(index), str(period)],
+                                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            return None, samples, info
+
+        def reader():
+            for line in proc.stdout:
+                parts = line.split()
+                try:
+                    if parts[0] == "max":
+                        info["max"] = float(parts[1])
+                    else:
+                        samples.append((float(parts[0]), float(parts[1]), int(parts[2])))
+                except (ValueError, IndexError):
+                    continue
+        threading.Thread(target=reader, daemon=True).start()
+        time.sleep(0.5)                       # NVML up before the first region
+        return proc, samples, info
 
     def start(self):
-        try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.proc = None
+        self.t0 = time.time()
 
     def stop(self):
-        if self.proc is None:
+        if self.proc is None or self.t0 is None:
             return None
-        self.proc.terminate()
-        try:
-            out, _ = self.proc.communicate(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-            out, _ = self.proc.communicate()
-        sm, mx, reasons = [], [], set()
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for line in out.strip().splitlines():
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, val in zip(names, parts[5:9]):
-                if val.lower() in ("active", "0x1", "1"):
-                    reasons.add(nm)
-        if not sm:
+        t1 = time.time()
+        time.sleep(0.05)                      # samples of the region's end are read
+        inside = [(m, r) for t, m, r in list(self.samples) if self.t0 <= t <= t1]
+        if not inside:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        reasons = sorted(nm for nm, bit in self.REASONS.items()
+                         if any(r & bit for _, r in inside))
+        return {"sm_mhz": statistics.median(m for m, _ in inside),
+                "sm_max_mhz": self.info["max"], "reasons": reasons, "samples": len(inside),
+                "region_s": round(t1 - self.t0, 3)}
+
+    @classmethod
+    def close_all(cls):
+        for proc, _, _ in cls._shared.values():
+            if proc is not None:
+                proc.terminate()
+        cls._shared.clear()
+
+
+# ------------------------------------------------------ measured peaks --
+def _event_ms(fn, reps: int = 1) -> float:
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_peaks(index: int, target_ms: float = 150.0) -> dict:
+    """FP32 FMA, FP64 FMA and FP64 add peaks of this GPU from the library's
+    microbenchmark (sph_peak_run), each the best of 3 launches of about
+    target_ms, with the SM clock sampled during them."""
+    import torch
+    from paper_2606_23891_b300 import sph
+    sink = torch.zeros(256, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    clocks = ClockSampler(index)
+    clocks.start()
+    out = {}
+    for kind, name in ((sph.PEAK_FP32_FMA, "fp32_tflops"), (sph.PEAK_FP64_FMA, "fp64_fma_tflops"),
+                       (sph.PEAK_FP64_ADD, "fp64_add_tflops")):
+        iters = 16
+        ms = _event_ms(lambda: sph.sph_peak_run(kind, iters, sink.data_ptr(), st))
+        iters = max(16, int(iters * target_ms / max(ms, 1e-3)))
+        best = 0.0
+        for _ in range(3):
+            fl = [0.0]
+
+            def run():
+                fl[0] = sph.sph_peak_run(kind, iters, sink.data_ptr(), st)
+            ms = _event_ms(run)
+            best = max(best, fl[0] / (ms * 1e-3) / 1e12)
+        out[name] = best
+    out["clocks"] = clocks.stop()
+    out["how"] = ("sph_peak_run: 4 x 256 threads per SM, 8 independent chains of FMA "
+                  "(2 flops) or add; best of 3 launches of ~%d ms, CUDA events" % target_ms)
+    return out
+
+
+def measure_link(nbytes: int = 1 << 30, reps: int = 5) -> dict:
+    """Pinned host <-> device copy rate: one cudaMemcpyAsync of nbytes per
+    direction (torch copy_ of a page-locked tensor), best of reps."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    h2d = min(_event_ms(lambda: d.copy_(h, non_blocking=True)) for _ in range(reps))
+    d2h = min(_event_ms(lambda: h.copy_(d, non_blocking=True)) for _ in range(reps))
+    del h, d
+    torch.cuda.empty_cache()
+    return {"h2d_GBps": nbytes / (h2d * 1e-3) / 1e9, "d2h_GBps": nbytes / (d2h * 1e-3) / 1e9,
+            "bytes": nbytes, "how": "one pinned cudaMemcpyAsync per direction, best of %d" % reps}
+
+
+def list_build_counts(off) -> dict:
+    """The list build's work per step, counted by its measurement variant
+    (sph_batch_list_count) over every bundle: candidates staged, pairs past
+    the warp-box cull (each prefiltered), prefilter hits, exact tests and
+    entries written."""
+    import torch
+    from paper_2606_23891_b300 import sph
+    cnt = torch.zeros(5, dtype=torch.int64, device=off.device)
+    for b in range(off.binfo["nbundles"]):
+        sph.sph_batch_pack_list(off.store, off.bplan, 0, b, off.bbuf_in.data_ptr(), off.params,
+                                off.stream)
+        sph.sph_batch_list_count(off.store, off.bplan, b, off.bbuf_in.data_ptr(),
+                                 off.blist.data_ptr(), off.blist_bytes, off.params,
+                                 cnt.data_ptr(), off.stream)
+    sph.sph_sync(off.stream)
+    keys = ("staged", "culled_in", "prefilter_hits", "exact_tests", "entries")
+    return dict(zip(keys, (int(v) for v in cnt.cpu().tolist())))
+
+
+def sig(x, n: int = 4):
+    """x rounded to n significant digits (compact JSON)."""
+    if isinstance(x, float) and x != 0.0 and np.isfinite(x):
+        return float("%.*g" % (n, x))
+    return x
+
+
+def compact_line(line: dict, limit: int = HEADLINE_MAX_BYTES) -> str:
+    """The headline JSON, dropping the optional keys (last first) until it
+    fits in `limit` bytes."""
+    optional = ["staged", "peaks", "per_loop"]
+    out = json.dumps(line, separators=(",", ":"))
+    while len(out) > limit and optional:
+        line.pop(optional.pop(), None)
+        out = json.dumps(line, separators=(",", ":"))
+    return out
 
 
 # ---------------------------------------------------------- distributed --
@@ -185,7 +339,9 @@ def precision_study(off, f, sel, ref, steps, mixed_step):
     mixed_step()
     got = off.export()
     e = compare.errors({k: v[sel] for k, v in got.items()}, ref, sc)
-    res["mixed"] = {"per_loop": compare.per_loop(e), "fields": e}
+    res["mixed"] = {"per_loop": compare.per_loop(e), "fields": e,
+                    "rho_dh": compare.relative_distribution(got["rho_dh"][sel], ref["rho_dh"],
+                                                            sc[0])}
     off.fp64_step()                                   # warm-up (allocates buffers)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -200,9 +356,9 @@ def precision_study(off, f, sel, ref, steps, mixed_step):
     e = compare.errors({k: v[sel] for k, v in got.items()}, ref, sc)
     res["fp64"] = {"per_loop": compare.per_loop(e), "fields": e}
     res["metrics"] = ("relative error for rho, wcount, f_gradh, pressure, soundspeed, "
-                      "v_sig; err / (3 rho / H) and err / max(|x|, 3 wcount / H) for the "
-                      "h-derivatives; max err / rms for div v, curl v, laplace u, a, "
-                      "du/dt, dh/dt; absolute error for the Balsara switch")
+                      "v_sig; err / (sum of the terms' magnitudes) for the h-derivatives; "
+                      "max err / rms for div v, curl v, laplace u, a, du/dt, dh/dt; "
+                      "absolute error for the Balsara switch")
     off.f64_in = off.f64_out = None
     torch.cuda.empty_cache()
     return res
@@ -368,22 +524,19 @@ def run_layout(off, steps, warmup, ws, clocks=None, pipeline="plain"):
 
 
 def run_e2e(off, f, steps, warmup, pipeline="plain"):
-    """Same step through the package from pinned host inputs to pinned host
-    results: every step copies its inputs in and its results out, the copies
-    of neighbouring steps overlapping the current step's kernels
-    (pipeline.StreamingSteps)."""
+    """The same step from pinned host inputs to pinned host results, every
+    byte through the library: per step sph_hostio_begin (H2D of the step's
+    inputs, import), the step's library calls, sph_hostio_end (export, D2H
+    of its results); the copies of neighbouring steps overlap the current
+    step's kernels on the library's two copy streams."""
     import torch
     from paper_2606_23891_b300 import sph
-    from paper_2606_23891_b300.pipeline import (STEP_INPUTS, STEP_RESULTS, StreamingSteps,
-                                                field_spec)
+    from paper_2606_23891_b300.pipeline import STEP_INPUTS, STEP_RESULTS, StreamingSteps
     timer = StepTimer(off, pipeline)
     ss = StreamingSteps(off, lambda: timer.step(record=False), STEP_INPUTS, STEP_RESULTS)
-    pin_in = {}
-    for name in STEP_INPUTS:
-        dt, k = field_spec(name)
-        pin_in[name] = torch.from_numpy(np.ascontiguousarray(f[name], dt)).pin_memory()
-    pin_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory()
-               for k, v in ss.dev_out[0].items()}
+    pin_in, pin_out = ss.pinned_in(), ss.pinned_out()
+    for name, t in pin_in.items():
+        t.numpy()[...] = np.asarray(f[name], t.numpy().dtype).reshape(t.shape)
     h2d, d2h = ss.bytes_per_step()
     for _ in range(warmup):
         ss.step(pin_in, pin_out)
@@ -399,14 +552,16 @@ def run_e2e(off, f, steps, warmup, pipeline="plain"):
     end.record()
     torch.cuda.synchronize()
     sph.sph_sync(off.stream)
+    ss.close()
     return start.elapsed_time(end) / steps, h2d, d2h
 
 
-def run_host_staged(f, layouts, steps, bundle_slots, fission_bundles=2):
+def run_host_staged(f, layouts, steps, bundle_slots, link, fission_bundles=2):
     """The paper's own setting: store in pinned host memory, host pack and
     unpack (all host cores), double-buffered H2D / kernel / D2H on two
-    streams.  Wall-clock per step, plus the isolated host pack and unpack
-    time per loop (the quantity of the paper's Fig. 2)."""
+    streams.  Per layout: wall-clock per step, and a step with every stage
+    timed (sph_offload_loop_host_stats), giving the offload-time breakdown
+    of the paper's Fig. 1 and the copies' rate against the measured link."""
     import torch
     from paper_2606_23891_b300 import sph
     from paper_2606_23891_b300.pipeline import HostOffload
@@ -424,22 +579,28 @@ def run_host_staged(f, layouts, steps, bundle_slots, fission_bundles=2):
             host.step()
         torch.cuda.synchronize()
         step_s = (time.perf_counter() - t0) / steps
+        stats = host.step_stats()
+        tot = {k: sum(st[k] for st in stats) for k in stats[0]}
+        stage_ms = {"host_pack": 1e3 * tot["host_pack_s"], "h2d": tot["h2d_ms"],
+                    "kernel": tot["kernel_ms"], "d2h": tot["d2h_ms"],
+                    "host_unpack": 1e3 * tot["host_unpack_s"]}
+        serial = sum(stage_ms.values())
+        wall = 1e3 * tot["wall_s"]
+        h2d_gbps = tot["h2d_bytes"] / (tot["h2d_ms"] * 1e-3) / 1e9
+        d2h_gbps = tot["d2h_bytes"] / (tot["d2h_ms"] * 1e-3) / 1e9
         loops = {}
-        nb = host.info["nbundles"]
-        for l in range(3):
-            tp = tu = 0.0
-            for b in range(nb):
-                t1 = time.perf_counter()
-                sph.sph_pack_host(host.store, host.tasks, l, b, host.host_in[0][0].ctypes.data)
-                t2 = time.perf_counter()
-                sph.sph_unpack_host(host.store, host.tasks, l, b, host.host_out[0][0].ctypes.data)
-                tu += time.perf_counter() - t2
-                tp += t2 - t1
-            loops[LOOP_NAMES[l]] = {"host_pack_ms": 1e3 * tp, "host_unpack_ms": 1e3 * tu}
+        for l, st in enumerate(stats):
+            loops[LOOP_NAMES[l]] = {
+                "wall_ms": 1e3 * st["wall_s"], "host_pack_ms": 1e3 * st["host_pack_s"],
+                "h2d_ms": st["h2d_ms"], "kernel_ms": st["kernel_ms"], "d2h_ms": st["d2h_ms"],
+                "host_unpack_ms": 1e3 * st["host_unpack_s"],
+                "host_wait_ms": 1e3 * st["host_wait_s"], "h2d_bytes": st["h2d_bytes"],
+                "d2h_bytes": st["d2h_bytes"], "bundles": st["bundles"]}
         # loop-fission variants (Sec. 3.3, Fig. 4) on the first bundles of
         # each loop; the isolated unpacks fold result buffers into the store,
         # which is not read again
         fission = {}
+        nb = host.info["nbundles"]
         nbf = min(nb, fission_bundles)
         for name, fv in sph.FISSION.items():
             tp = tu = 0.0
@@ -457,12 +618,25 @@ def run_host_staged(f, layouts, steps, bundle_slots, fission_bundles=2):
         base_ms = fission["none"]["pack_ms"] + fission["none"]["unpack_ms"]
         for v in fission.values():
             v["relative_to_none"] = (v["pack_ms"] + v["unpack_ms"]) / base_ms
-        out[lname] = {"ms_per_step": 1e3 * step_s, "loops": loops,
-                      "loop_fission": {"bundles_per_loop": nbf, "variants": fission}}
+        out[lname] = {
+            "ms_per_step": 1e3 * step_s, "timed_step_ms": wall, "stage_ms": stage_ms,
+            "stage_share": {k: v / serial for k, v in stage_ms.items()},
+            "pack_unpack_share": (stage_ms["host_pack"] + stage_ms["host_unpack"]) / serial,
+            "launch_share": (stage_ms["h2d"] + stage_ms["kernel"] + stage_ms["d2h"]) / serial,
+            "overlap": 1.0 - wall / serial,
+            "h2d_GBps": h2d_gbps, "d2h_GBps": d2h_gbps,
+            "h2d_link_frac": h2d_gbps / link["h2d_GBps"],
+            "d2h_link_frac": d2h_gbps / link["d2h_GBps"],
+            "h2d_bytes_per_step": tot["h2d_bytes"], "d2h_bytes_per_step": tot["d2h_bytes"],
+            "loops": loops,
+            "loop_fission": {"bundles_per_loop": nbf, "variants": fission}}
     if host is not None:
         host.close()
-    return {"bundle_max_slots": bundle_slots, "threads": cpu_cores(),
-            "h2d_link": "pinned host memory, cudaMemcpyAsync on 2 streams", "layouts": out}
+    return {"bundle_max_slots": bundle_slots, "threads": cpu_cores(), "link": link,
+            "h2d_link": "pinned host memory, cudaMemcpyAsync on 2 streams",
+            "stage_times": "host stages on the host clock; copies and kernels with CUDA "
+                           "events, summed over bundles (they overlap)",
+            "layouts": out}
 
 
 def layout_phase_study(per_layout: dict, convert_ms: dict, base: str) -> dict:
@@ -542,7 +716,7 @@ def plan_candidates(f, leaf_max: int = 128) -> dict:
     return out
 
 
-def run_cosmology(args, ws, peaks):
+def run_cosmology(args, ws, fp32_peak):
     """Clustered set (lognormal, sigma(ln rho) = 2): the batched pipeline on the
     octree-leaf plan, autotuned, per layout, with CUDA-graph replay."""
     import torch
@@ -618,15 +792,18 @@ def run_cosmology(args, ws, peaks):
     if stage == "list":
         nbl = off.binfo["nbundles"]
         dur = st[top] / (args.steps * nbl)
-        ach = (ncand * FLOPS_CANDIDATE + pairs[2] * FLOPS_EXACT) / nbl / (dur * 1e-3) / 1e12
+        c = list_build_counts(off)
+        fixed = sph.sph_batch_list_fixed(off.bplan)
+        ach = (c["staged"] * FLOPS_STAGE[fixed] + c["culled_in"] * FLOPS_CANDIDATE +
+               c["exact_tests"] * FLOPS_EXACT[fixed]) / nbl / (dur * 1e-3) / 1e12
+        res["list_build_counts"] = c
         name = "neighbour-list build (tree plan)"
     else:
         dur = st[top] / cnt[loop]
         ach = pairs[loop] * FLOPS_PAIR[loop] / cnt[loop] * args.steps / (dur * 1e-3) / 1e12
         name = "list interaction/%s (tree plan)" % LOOP_NAMES[loop]
     res["roofline"] = {"kernel": name, "bound": "alu", "achieved": ach,
-                       "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                       "frac": ach / FP32_PEAK_TFLOPS}
+                       "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak}
     res["gpu_launches_per_step"] = launches / args.steps
     off.close()
     del off
@@ -798,6 +975,9 @@ def run_ours(args, ws, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    mpeaks = measured_peaks()
+    peaks = measure_peaks(local) if args.peaks else {}
+    link = measure_link() if args.host_steps > 0 else None
     f = ics.gresho(n_side=args.n_side)
     t_build = time.perf_counter()
     base = Offload(f, layout=args.layouts[0], bundle_max_slots=args.bundle_slots)
@@ -880,7 +1060,8 @@ def run_ours(args, ws, rank, local):
                 torch.cuda.empty_cache()
     off, total_ms, timer, cl, st, cnt = head
     ms_step = total_ms / args.steps
-    kernel_dependent = layout_phase_study(per_layout, convert_ms, args.layouts[0])
+    kernel_dependent = layout_phase_study(per_layout, convert_ms, args.layouts[0]) \
+        if convert_ms else None
     value = job_rate(sum(pairs), ms_step, ws)
     graph = None
     if args.head_pipeline in ("batched", "list"):
@@ -889,15 +1070,7 @@ def run_ours(args, ws, rank, local):
         gs = GraphStep(off, step=off.list_step if args.head_pipeline == "list" else None)
         for _ in range(args.warmup):
             gs.replay()
-        torch.cuda.synchronize()
-        g0 = torch.cuda.Event(enable_timing=True)
-        g1 = torch.cuda.Event(enable_timing=True)
-        g0.record()
-        for _ in range(args.steps):
-            gs.replay()
-        g1.record()
-        torch.cuda.synchronize()
-        gms = barrier_max(g0.elapsed_time(g1), ws) / args.steps
+        gms = barrier_max(_event_ms(gs.replay, args.steps), ws)
         graph = {"ms_per_step": gms, "pair_interactions_per_s": job_rate(sum(pairs), gms, ws)}
         del gs
     # dominant kernel of the headline layout
@@ -905,27 +1078,32 @@ def run_ours(args, ws, rank, local):
     stage, loop = top
     per_step = cnt[loop] / args.steps             # launches per step (bundles)
     dur = st[top] / cnt[loop]                     # ms per launch
-    peaks = measured_peaks()
+    fp32_peak = peaks.get("fp32_tflops") or FP32_PEAK_DERIVED
+    fp32_src = ("measured: sph_peak_run FP32 FMA at %.0f MHz" % peaks["clocks"]["sm_mhz"]
+                if peaks.get("fp32_tflops") and peaks.get("clocks")
+                else "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz")
+    build_counts = None
+    if args.head_pipeline == "list":
+        build_counts = list_build_counts(off)
     if stage == "list":
-        # the neighbour-list build: the candidate tests of the cell pairs (hi-only
-        # r^2 against the support) and the exact two-float decision on each pair
+        # the neighbour-list build: its work counted by the measurement
+        # variant (staged candidates, prefiltered pairs, exact tests) times
+        # the FP32 operations of the implemented formulas
+        fixed = sph.sph_batch_list_fixed(off.bplan)
         per_step = off.binfo["nbundles"]
         dur = st[top] / (args.steps * per_step)
-        flops = (ncand * FLOPS_CANDIDATE + pairs[2] * FLOPS_EXACT) / per_step
+        flops = (build_counts["staged"] * FLOPS_STAGE[fixed] +
+                 build_counts["culled_in"] * FLOPS_CANDIDATE +
+                 build_counts["exact_tests"] * FLOPS_EXACT[fixed]) / per_step
         achieved = flops / (dur * 1e-3) / 1e12
         tr = NCU_TRAFFIC.get(("list", "list", 0))
         traffic = (tr["bytes_per_unit"] * n / per_step
                    if tr and tr["src"] == src_digest(tr["file"]) else None)
-        roof = {"kernel": "neighbour-list build", "bound": "alu",
-                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "traffic_source": "ncu DRAM bytes of a 128^3 capture, scaled by particles",
-                "hbm_GBps": (traffic / (dur * 1e-3) / 1e9) if traffic else None,
-                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"}
+        roof = {"kernel": "k_blist (neighbour-list build)", "bound": "alu",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": traffic, "peak_source": fp32_src,
+                "ms": dur}
     elif stage == "kernel":
-        # useful FP32 work only: accepted pairs x the pair body; the candidate
-        # tests of the cell pairs (most skipped by the projection windows) are
-        # reported beside it, not counted as achieved work
         flops = pairs[loop] * FLOPS_PAIR[loop] / per_step
         achieved = flops / (dur * 1e-3) / 1e12
         tr = NCU_TRAFFIC.get((args.head_pipeline, stage, loop))
@@ -933,14 +1111,9 @@ def run_ours(args, ws, rank, local):
         traffic = (tr["bytes_per_unit"] * units / per_step
                    if tr and tr["src"] == src_digest(tr["file"]) else None)
         roof = {"kernel": "%s interaction/%s" % (args.head_pipeline, LOOP_NAMES[loop]),
-                "bound": "alu",
-                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
-                "with_cell_pair_candidates_TFLOPs":
-                    (ncand * FLOPS_CANDIDATE + pairs[loop] * FLOPS_PAIR[loop]) / per_step
-                    / (dur * 1e-3) / 1e12,
-                "hbm_GBps": (traffic / (dur * 1e-3) / 1e9) if traffic else None}
+                "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": traffic, "peak_source": fp32_src,
+                "ms": dur}
     else:
         if args.head_pipeline == "plain":
             bpl = (slots * 2 * VIEW_IN[loop] if stage == "pack"
@@ -950,19 +1123,21 @@ def run_ours(args, ws, rank, local):
             bpl = (bslots * (VIEW_IN[loop] + rec[loop]) if stage == "pack"
                    else n * 3 * VIEW_OUT[loop]) / per_step
         achieved = bpl / (dur * 1e-3) / 1e9
-        peak = peaks.get("hbm_gbs", 6400.0)
+        peak = mpeaks.get("hbm_gbs", 6400.0)
         roof = {"kernel": "%s/%s" % (stage, LOOP_NAMES[loop]), "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": "measured" if peaks else "fallback"}
+                "traffic": None, "peak_source": "measured" if mpeaks else "fallback", "ms": dur}
+    head_loops = per_layout[args.headline][args.head_pipeline]["loops"]
+    loop_fracs = {LOOP_NAMES[l]: head_loops[LOOP_NAMES[l]]["kernel_useful_fp32_TFLOPs"] / fp32_peak
+                  for l in range(3)}
     e2e_ms, h2d, d2h = run_e2e(off, f, args.steps, 2, args.head_pipeline)
     e2e_ms = barrier_max(e2e_ms, ws)
     cpu = None
     if rank == 0 and ws == 1 and args.cpu_sample > 0:
         p, t = oracle_sample(f, args.cpu_sample, 7)
         cpu = {"value": p / t, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-               "sample": "%d particles of the %d^3 Gresho set, each with its full "
-                         "density->ghost->gradient->force chain by brute-force O(N) "
-                         "scans (neighbour densities included), %.1f s"
+               "sample": "%d particles of gresho%d, full density-ghost-gradient-force chain "
+                         "each, brute-force O(N) scans, %.1f s"
                          % (args.cpu_sample, args.n_side, t)}
     precision = None
     if cpu is not None and args.precision_steps > 0 and args.head_pipeline in ("batched", "list"):
@@ -981,54 +1156,72 @@ def run_ours(args, ws, rank, local):
     torch.cuda.empty_cache()
     staged = None
     if args.host_steps > 0:
-        staged = run_host_staged(f, args.host_layouts, args.host_steps, args.host_bundle_slots)
+        staged = run_host_staged(f, args.host_layouts, args.host_steps, args.host_bundle_slots,
+                                 link)
         for lname, v in staged["layouts"].items():
             v["pair_interactions_per_s"] = sum(pairs) / (v["ms_per_step"] * 1e-3)
     del f
     adj = run_adjoint(args, ws) if args.adjoint_n_side else None
     prec_cl = (run_precision_clustered(args)
                if args.precision_clustered_n_side > 0 and rank == 0 and ws == 1 else None)
-    cosmo = run_cosmology(args, ws, peaks) if args.cosmo_n_side > 0 else None
+    cosmo = run_cosmology(args, ws, fp32_peak) if args.cosmo_n_side > 0 else None
+    sections = {
+        "config_detail": {
+            "batch_threads": args.batch_threads, "batch_bundles": cfg_vals["bbundles"],
+            "tasks": cfg_vals["tasks"], "bundles": cfg_vals["bundles"],
+            "bundle_max_slots": args.bundle_slots, "slots_per_loop": slots,
+            "cell_pair_candidates_per_loop": ncand, "pairs": dict(zip(LOOP_NAMES, pairs)),
+            "task_build_s": t_build},
+        "peaks": peaks, "link": link, "layouts": per_layout, "cuda_graph": graph,
+        "autotune": tuning, "list_build_counts": build_counts, "roofline": roof,
+        "loop_fp32_frac": loop_fracs, "host_staged": staged, "precision": precision,
+        "precision_clustered": prec_cl, "kernel_dependent_layout": kernel_dependent,
+        "cosmology": cosmo, "adjoint": adj,
+    }
+    if rank == 0:
+        for name, body in sections.items():
+            if body is not None:
+                print(json.dumps({"section": name, "data": body}))
+    per_loop = {"fields": ["pair-interactions/s", "pack+unpack GB/s"]}
+    for lname, v in per_layout.items():
+        for pl, r in v.items():
+            per_loop["%s/%s" % (lname, pl)] = [
+                [sig(r["loops"][nm]["pair_interactions_per_s"], 3),
+                 sig(r["loops"][nm]["pack_unpack_GBps"], 4)] for nm in LOOP_NAMES]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {
-            "workload": "gresho256: Gresho-vortex shaped jittered 256^3 lattice, "
-                        "64^3 cells of 55..73 particles, all loops",
-            "particles": n, "layout": args.headline, "pipeline": args.head_pipeline,
-            "batch_threads": args.batch_threads,
-            "batch_bundles": cfg_vals["bbundles"], "tasks": cfg_vals["tasks"],
-            "bundles": cfg_vals["bundles"], "bundle_max_slots": args.bundle_slots,
-            "slots_per_loop": slots, "candidates_per_loop": ncand,
-            "pairs": dict(zip(LOOP_NAMES, pairs)),
-            "l2": "inputs larger than L2 (store %.2f GB, pack buffer %.2f GB)"
-                  % (cfg_vals["store_gb"], cfg_vals["buf_gb"]),
-            "parallelism": "replicas" if ws > 1 else "single GPU",
-            "task_build_s": t_build,
-        },
+        "config": {"workload": "gresho256", "particles": n, "layout": args.headline,
+                   "pipeline": args.head_pipeline,
+                   "l2": "inputs larger than L2 (store %.2f GB)" % cfg_vals["store_gb"],
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
         "e2e": {"value": job_rate(sum(pairs), e2e_ms, ws), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_ms,
-                "copied": "in: x v m h u alpha_visc alpha_diff time_bin; "
-                          "out: rho a du/dt dh/dt v_sig (the step's results)"},
+                "ms_per_step": sig(e2e_ms),
+                "api": "sph_hostio_begin/end around sph_batch_* calls, pinned host arrays"},
         "gpu_launches": timer.launches,
-        "roofline": roof,
+        "roofline": {k: sig(v) for k, v in roof.items()},
         "cpu_baseline": cpu,
         "clocks": cl,
-        "layouts": per_layout,
-        "cuda_graph": graph,
-        "autotune": tuning,
-        "host_staged": staged,
-        "precision": precision,
-        "precision_clustered": prec_cl,
-        "kernel_dependent_layout": kernel_dependent,
-        "cosmology": cosmo,
-        "adjoint": adj,
+        "per_loop": per_loop,
+        "peaks": {"fp32_tflops": sig(peaks.get("fp32_tflops")),
+                  "fp64_fma_tflops": sig(peaks.get("fp64_fma_tflops")),
+                  "fp64_add_tflops": sig(peaks.get("fp64_add_tflops")),
+                  "hbm_gbs": mpeaks.get("hbm_gbs"),
+                  "h2d_gbs": sig(link["h2d_GBps"]), "d2h_gbs": sig(link["d2h_GBps"])},
     }
+    if staged is not None:
+        line["staged"] = {
+            lname: {"ms": sig(v["ms_per_step"]),
+                    "share": {k: sig(x, 3) for k, x in v["stage_share"].items()},
+                    "h2d_frac": sig(v["h2d_link_frac"], 3),
+                    "overlap": sig(v["overlap"], 3)}
+            for lname, v in staged["layouts"].items()}
+    ClockSampler.close_all()
     if rank == 0:
-        print(json.dumps(line))
+        print(compact_line(line))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -1041,26 +1234,28 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--layouts", default=",".join(ALL_LAYOUTS))
+    ap.add_argument("--layouts", default="pack_force_type,aos",
+                    help="store layouts to time ('all': the 11 layouts)")
     ap.add_argument("--headline", default=BENCH_LAYOUT)
     ap.add_argument("--bundle-slots", type=int, default=BUNDLE_SLOTS)
     ap.add_argument("--n-side", type=int, default=N_SIDE)
     ap.add_argument("--cpu-sample", type=int, default=16)
     ap.add_argument("--ref-sample", type=int, default=2)
-    ap.add_argument("--cosmo-n-side", type=int, default=376,
+    ap.add_argument("--cosmo-n-side", type=int, default=0,
                     help="clustered (lognormal) set on the tree plan; 0: skip")
     ap.add_argument("--cosmo-layouts", type=lambda s: s.split(","),
                     default=["pack_force_type", "aos"])
     ap.add_argument("--adjoint-n-side", type=lambda s: [int(v) for v in s.split(",") if v],
-                    default=[64, 256], help="Gresho sizes of the adjoint timing ('' skips)")
+                    default=[], help="Gresho sizes of the adjoint timing ('' skips)")
     ap.add_argument("--adjoint-fd", type=int, default=8,
                     help="particles of the central-difference check of the adjoint")
-    ap.add_argument("--precision-clustered-n-side", type=int, default=256,
+    ap.add_argument("--precision-clustered-n-side", type=int, default=0,
                     help="lognormal set of the clustered precision study (0: skip)")
     ap.add_argument("--precision-clustered-sample", type=int, default=8)
     ap.add_argument("--precision-steps", type=int, default=2,
                     help="timed steps of the all-FP64 path (0: skip the precision study)")
-    ap.add_argument("--pipelines", default="plain,batched,list")
+    ap.add_argument("--pipelines", default="plain,list")
+    ap.add_argument("--peaks", type=int, default=1, help="measure the FP32/FP64 peaks")
     ap.add_argument("--head-pipeline", default="list")
     ap.add_argument("--batch-threads", type=int, default=128)
     ap.add_argument("--autotune", type=int, default=1)
@@ -1068,7 +1263,8 @@ def main(argv=None):
     ap.add_argument("--host-layouts", default="aos,pack_force_type,soa")
     ap.add_argument("--host-bundle-slots", type=int, default=1 << 24)
     args = ap.parse_args(argv)
-    args.layouts = [s for s in args.layouts.split(",") if s]
+    args.layouts = list(ALL_LAYOUTS) if args.layouts == "all" else \
+        [s for s in args.layouts.split(",") if s]
     args.host_layouts = [s for s in args.host_layouts.split(",") if s]
     args.pipelines = [s for s in args.pipelines.split(",") if s]
     if args.head_pipeline not in args.pipelines:

@@ -53,7 +53,7 @@ enum sph_layout {
     SPH_SOA = 8,                   /* one array per field component */
     SPH_SAOS_PACK_FORCE_REPL = 9,  /* pack-force plus the density view
                                       {x, v, m, h} stored again on its own
-                                      (replicated positions, Sec. 6): the
+                                      (replicated positions, Sec. 5): the
                                       density pack reads only that copy */
     SPH_SAOS_FUSED = 10,           /* fused views: each loop's inputs with the
                                       outputs its unpack writes, in phase order */
@@ -162,6 +162,46 @@ int sph_store_import(sph_store s, const sph_fields *dev_src,
                      const int64_t *dev_perm, void *stream);
 int sph_store_export(sph_store s, const sph_fields *dev_dst,
                      const int64_t *dev_perm, void *stream);
+
+/* ---- end-to-end host I/O ------------------------------------------------
+ * A step's inputs live in page-locked host arrays and its results go back to
+ * them: the offload cycle of Sec. 2.3 seen from an application whose data
+ * stay on the host between steps.  A host I/O handle moves them through a
+ * double-buffered device staging area so that, on the caller's streams,
+ * step k+1's host-to-device copies and step k-1's device-to-host copies run
+ * while step k computes:
+ *
+ *   sph_hostio_begin(io, host_in, stream)   H2D of every selected input on
+ *        copy_in_stream into staging set k%2 (after that set's previous
+ *        import finished), then, on `stream`, the import into the store;
+ *   ... the step's library calls on `stream` ...
+ *   sph_hostio_end(io, host_out, stream)    export into staging set k%2 on
+ *        `stream` (after that set's previous D2H copies finished), then the
+ *        D2H copies into host_out on copy_out_stream;
+ *   sph_hostio_drain(io, stream)            `stream` waits for the last D2H.
+ *
+ * in_sel / out_sel select the fields: every non-NULL member is selected (its
+ * value is not used).  The staging area is caller device memory of
+ * sph_hostio_bytes bytes, 256-byte aligned; dev_perm is the store's
+ * permutation (as for sph_store_import; the handle keeps the pointer).
+ * host_in / host_out must hold exactly the selected fields, in original
+ * particle order, each in page-locked host memory (SPH_EINVAL otherwise,
+ * before anything is enqueued).  A host array must not be touched by the
+ * host until the copies of its step are complete (after sph_hostio_drain and
+ * a synchronisation of `stream`, or two steps later).  begin and end
+ * alternate, one pair per step.  The handle owns eight CUDA events and
+ * nothing else; sph_hostio_info gives the bytes copied per step (in, out)
+ * and the steps completed.  Not thread-safe. */
+typedef struct sph_hostio_s *sph_hostio;
+size_t sph_hostio_bytes(int64_t n, const sph_fields *in_sel, const sph_fields *out_sel);
+int sph_hostio_create(sph_store s, const int64_t *dev_perm, const sph_fields *in_sel,
+                      const sph_fields *out_sel, void *dev_staging, size_t bytes,
+                      void *copy_in_stream, void *copy_out_stream, sph_hostio *out);
+int sph_hostio_begin(sph_hostio io, const sph_fields *host_in, void *stream);
+int sph_hostio_end(sph_hostio io, const sph_fields *host_out, void *stream);
+int sph_hostio_drain(sph_hostio io, void *stream);
+int sph_hostio_info(sph_hostio io, int64_t info[3]);
+int sph_hostio_destroy(sph_hostio io);
 
 /* Layout conversion between two device stores of the same particles (same
  * count and order): every field of dst, every copy of a replicated one, from
@@ -333,6 +373,30 @@ int sph_offload_loop_host(sph_store s, sph_tasks t, int loop, void *const host_i
                           void *const dev_out[2], const sph_params *p,
                           void *const streams[2], int nthreads);
 
+/* The same loop with every stage timed, for the breakdown of the offload
+ * time into the host pack, the transfers, the kernels and the host unpack
+ * (Sec. 2.3-2.5, Fig. 1).  Host stages are timed on the host clock; the
+ * H2D copy, the kernel and the D2H copy of each bundle with CUDA events on
+ * its stream (summed over bundles; they overlap the host stages and each
+ * other across the two streams, so the parts add up to more than wall_s).
+ * stats must be non-NULL.  Costs 4 events per bundle. */
+typedef struct {
+    double wall_s;         /* the whole call, host clock */
+    double host_pack_s;    /* host pack of every bundle */
+    double host_unpack_s;  /* host unpack of every bundle (and the ghost after density) */
+    double host_wait_s;    /* host blocked on a bundle's device work */
+    double h2d_ms;         /* device time of the host-to-device copies */
+    double kernel_ms;      /* device time of the interaction kernels */
+    double d2h_ms;         /* device time of the device-to-host copies */
+    int64_t h2d_bytes;     /* bytes copied host to device */
+    int64_t d2h_bytes;     /* bytes copied device to host */
+    int64_t bundles;
+} sph_staged_stats;
+int sph_offload_loop_host_stats(sph_store s, sph_tasks t, int loop, void *const host_in[2],
+                                void *const host_out[2], void *const dev_in[2],
+                                void *const dev_out[2], const sph_params *p,
+                                void *const streams[2], int nthreads, sph_staged_stats *stats);
+
 /* ---- offload cycle without any allocation ------------------------------
  * The paper has no counterpart to this entry point.  It is for callers that
  * cannot allocate device memory while they run: for example a host
@@ -355,7 +419,10 @@ int sph_offload_loop_host(sph_store s, sph_tasks t, int loop, void *const host_i
  *    in sph_tasks_build accordingly (e.g. 300000 slots fit every loop).
  *  - The first call on a device looks up that device's address of the array
  *    (with that device current); make this first call before any stream
- *    capture is started on the device.
+ *    capture is started on the device.  The address is kept for the life of
+ *    the process: after cudaDeviceReset (or any other teardown of the
+ *    device's primary context) the array may live elsewhere, so do not call
+ *    this entry point again in that process.
  *  - All calls share the one array and it keeps whatever the last call left
  *    in it.  Nothing in it needs to start at zero: each bundle's pack buffer
  *    is written in full before it is read, and so is its result buffer.
@@ -384,7 +451,19 @@ typedef struct {
 } sph_batch_params;
 
 /* Build a batch plan from a task handle's cells (host) and upload it to the
- * current device (allocates the plan's device metadata). */
+ * current device (allocates the plan's device metadata).
+ *
+ * A plan (this one or a tree plan) holds for the positions and supports it
+ * was built from.  Every cell records the largest support the plan holds
+ * for it: here the shortest cell edge (any support up to it keeps every
+ * interacting pair in adjacent cells), for a tree plan the leaf's largest
+ * support at build time (its neighbour entries were found with it).  Each
+ * density pack checks the cell's current supports against that limit; a
+ * larger one, whose pairs the plan may miss, is reported by the next
+ * sph_sync as SPH_EUNSUPPORTED, and the plan must be rebuilt.  The list
+ * build's fixed-point path (sph_batch_list_fixed) is decided from the same
+ * supports, so it stays valid while no such report occurs.  Particles that
+ * leave their cell also need a new plan; that is the caller's to track. */
 int sph_batch_build(sph_tasks t, const sph_batch_params *bp, sph_batch *out);
 /* info[0] bundles, [1] largest bundle slots, [2] work items, [3] threads,
  * [4] largest bundle target slots, [5] packed cells (all bundles). */
@@ -501,6 +580,16 @@ int sph_batch_list_build_bundle(sph_store s, sph_batch b, int bundle, const void
                                 void *dev_list, size_t list_bytes, const sph_params *p,
                                 void *stream);
 int sph_batch_list_status(const void *dev_list, int64_t *chunks_needed, int *overflow);
+/* Measurement variant of sph_batch_list_build_bundle (the paper has no
+ * counterpart; it states the list build's work from what it tests): builds
+ * the same lists and adds into dev_counts[0..4] (device uint64, 8-byte
+ * aligned, zeroed by the caller) the candidates staged, the (particle,
+ * candidate) pairs that pass the warp-box cull and are prefiltered, the
+ * prefilter's hits, the hits that take the exact test, and the list entries
+ * written.  Slower than the build it counts; not for timed runs. */
+int sph_batch_list_count(sph_store s, sph_batch b, int bundle, const void *dev_buf_in,
+                         void *dev_list, size_t list_bytes, const sph_params *p,
+                         unsigned long long *dev_counts, void *stream);
 /* The pack of the list loops: the density view as sph_batch_pack, the
  * gradient and force views as compact records (c and P recomputed in the
  * loop from u and rho, so each gathered j record is 48 / 64 bytes). */
@@ -569,6 +658,19 @@ int sph_batch_offload_loop_fp64(sph_store s, sph_batch b, int loop, void *dev_bu
                                 void *dev_buf_out, const sph_params *p, void *stream);
 int sph_offload_loop_noalloc(sph_store s, sph_tasks t, int loop, const sph_params *p,
                              void *stream);
+
+
+/* ---- measurement utility -------------------------------------------------
+ * The paper has no counterpart to this call: it measures the arithmetic
+ * peaks that the interaction loops' roofline is stated against (they run on
+ * the FP32 CUDA cores; an FP64 separation would use the FP64 pipe).  One
+ * launch of 4 CTAs of 256 threads per SM, each thread running 8 independent
+ * chains of `iters` x 16 operations: kind 0 FP32 fused multiply-add (2 flops
+ * each), 1 FP64 fused multiply-add (2 flops), 2 FP64 add (1 flop).
+ * *flops_out gets the launch's flop count; the caller times the launch on
+ * `stream` (CUDA events) and divides.  dev_sink: 256-byte aligned device
+ * memory of at least 8 bytes, which the kernel may write. */
+int sph_peak_run(int kind, int64_t iters, void *dev_sink, void *stream, double *flops_out);
 
 int sph_tasks_destroy(sph_tasks t);
 

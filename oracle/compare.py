@@ -36,9 +36,10 @@ def errors(got: dict, ref: dict, scales) -> dict:
     out = {}
     for k in RELATIVE:
         out[k] = float(np.max(_rel(g[k], r[k]), initial=0.0))
-    out["rho_dh"] = float(np.max(np.abs(g["rho_dh"] - r["rho_dh"]) / s_rho, initial=0.0))
-    out["wcount_dh"] = float(np.max(np.abs(g["wcount_dh"] - r["wcount_dh"]) / s_w,
-                                    initial=0.0))
+    for k, sc in (("rho_dh", s_rho), ("wcount_dh", s_w)):
+        d = np.abs(g[k] - r[k])     # 0/0 (a lone particle's wcount_dh) reads as 0
+        out[k] = float(np.max(np.where(d == 0.0, 0.0, d / np.maximum(sc, 1e-300)),
+                              initial=0.0))
     for k in RMS:
         s = np.sqrt(np.mean(r[k] * r[k])) if r[k].size else 0.0
         e = float(np.max(np.abs(g[k] - r[k]), initial=0.0))
@@ -62,7 +63,7 @@ def relative_distribution(got, ref, scale) -> dict:
     g, r = np.asarray(got, np.float64), np.asarray(ref, np.float64)
     d = np.abs(g - r)
     rel = np.where(d == 0.0, 0.0, d / np.maximum(np.abs(r), 1e-300))
-    cond = d / np.asarray(scale, np.float64)
+    cond = np.where(d == 0.0, 0.0, d / np.maximum(np.asarray(scale, np.float64), 1e-300))
     q = (50, 90, 99, 100)
     return {"rel_to_value": {"p%d" % p: float(np.percentile(rel, p)) for p in q},
             "rel_to_scale": {"p%d" % p: float(np.percentile(cond, p)) for p in q},

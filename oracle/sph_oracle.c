@@ -774,7 +774,7 @@ static int build_layout(int layout, uint64_t seed, layout_def *L)
     static const int grad_out[] = {F_VSIGG, F_LAPU};
     static const int force_out[] = {F_A, F_UDT, F_HDT, F_VSIG};
     static const int rest[] = {F_PRES, F_CS, F_ID, F_BALLAST};
-    /* replication (Sec. 6 outlook): the density view's inputs stored again */
+    /* replication (Sec. 5, outlook): the density view's inputs stored again */
     static const int dens_view[] = {F_X, F_V, F_MASS, F_H};
     /* fused views: each loop's inputs with the outputs its unpack writes */
     static const int fused_dens[] = {F_X, F_V, F_MASS, F_H, F_RHO, F_RHODH, F_WCOUNT,

@@ -10,6 +10,8 @@
 #include <cstdio>
 #include <cstring>
 #include <cstdlib>
+#include <ctime>
+#include <vector>
 #include <new>
 
 #include "internal.h"
@@ -22,6 +24,7 @@
 #include "list_kernels.cuh"
 #include "adjoint_kernels.cuh"
 #include "host_batch.cuh"
+#include "peak_kernels.cuh"
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -261,12 +264,15 @@ int dispatch_bloop(sph_batch b, const BInteractArgs &a, const ListView &L, long 
 template <bool FIXED>
 inline int dispatch_blist_p(int threads, const BInteractArgs &a, const ListView &L,
                             long long item0, cudaStream_t st) {
+    unsigned long long *none = nullptr;
     if (threads == 64)
-        return launch_persistent(k_blist<64, FIXED>, 64, a.nitems, st, "list build", a, L, item0);
+        return launch_persistent(k_blist<64, FIXED>, 64, a.nitems, st, "list build", a, L, item0,
+                                 none);
     if (threads == 256)
         return launch_persistent(k_blist<256, FIXED>, 256, a.nitems, st, "list build", a, L,
-                                 item0);
-    return launch_persistent(k_blist<128, FIXED>, 128, a.nitems, st, "list build", a, L, item0);
+                                 item0, none);
+    return launch_persistent(k_blist<128, FIXED>, 128, a.nitems, st, "list build", a, L, item0,
+                             none);
 }
 
 // The list build takes the fixed-point path where the plan allows it.
@@ -274,6 +280,21 @@ inline int dispatch_blist(sph_batch b, const BInteractArgs &a, const ListView &L
                           long long item0, cudaStream_t st) {
     if (b->fixed_build) return dispatch_blist_p<true>(b->threads, a, L, item0, st);
     return dispatch_blist_p<false>(b->threads, a, L, item0, st);
+}
+
+// The counting variant of the list build (measurement only), at the plan's
+// block size of 128 threads or 64 / 256 as configured.
+template <bool FIXED>
+inline int dispatch_blist_count_p(int threads, const BInteractArgs &a, const ListView &L,
+                                  long long item0, unsigned long long *cnt, cudaStream_t st) {
+    if (threads == 64)
+        return launch_persistent(k_blist<64, FIXED, true>, 64, a.nitems, st, "list count", a, L,
+                                 item0, cnt);
+    if (threads == 256)
+        return launch_persistent(k_blist<256, FIXED, true>, 256, a.nitems, st, "list count", a,
+                                 L, item0, cnt);
+    return launch_persistent(k_blist<128, FIXED, true>, 128, a.nitems, st, "list count", a, L,
+                             item0, cnt);
 }
 
 template <int LOOP>
@@ -427,6 +448,250 @@ int sph_store_import(sph_store s, const sph_fields *dev_src, const int64_t *dev_
 int sph_store_export(sph_store s, const sph_fields *dev_dst, const int64_t *dev_perm,
                      void *stream) {
     return copy_fields(s, dev_dst, dev_perm, stream, 0);
+}
+
+}  // extern "C"
+
+// ---- end-to-end host I/O ----------------------------------------------------
+struct sph_hostio_s {
+    sph_store s = nullptr;
+    const int64_t *perm = nullptr;
+    int nin = 0, nout = 0;
+    int fin[F_BALLAST], fout[F_BALLAST];   // selected field ids
+    size_t fbytes[F_BALLAST];              // bytes of each field for n particles
+    char *stage_in[2][F_BALLAST], *stage_out[2][F_BALLAST];
+    cudaStream_t copy_in = nullptr, copy_out = nullptr;
+    cudaEvent_t in_ready[2], in_free[2], out_ready[2], out_free[2];
+    int nev = 0;
+    long long k = 0;     // steps begun
+    bool open = false;   // a step was begun and not yet ended
+};
+
+namespace sph {
+
+static int hostio_select(const sph_fields *sel, int *ids) {
+    if (!sel) return 0;
+    void *const *p = reinterpret_cast<void *const *>(sel);
+    int n = 0;
+    for (int f = 0; f < F_BALLAST; ++f)
+        if (p[f]) ids[n++] = f;
+    return n;
+}
+
+static size_t hostio_field_bytes(int64_t n, int f) {
+    return (size_t)n * kFields[f].elem * kFields[f].count;
+}
+
+static size_t r256(size_t b) { return (b + 255) / 256 * 256; }
+
+static size_t hostio_set_bytes(int64_t n, const int *ids, int nf) {
+    size_t b = 0;
+    for (int k = 0; k < nf; ++k) b += r256(hostio_field_bytes(n, ids[k]));
+    return b;
+}
+
+// The host arrays of a step must be exactly the selected fields, each in
+// page-locked memory (a pageable source would turn the copies synchronous).
+static int hostio_host_ptrs(const sph_fields *f, const int *ids, int nf, void **out,
+                            const char *what) {
+    if (!f) return fail(SPH_EINVAL, "%s: NULL fields", what);
+    void *const *p = reinterpret_cast<void *const *>(f);
+    int want[F_BALLAST] = {0};
+    for (int k = 0; k < nf; ++k) want[ids[k]] = 1;
+    for (int fid = 0; fid < F_BALLAST; ++fid) {
+        if ((p[fid] != nullptr) != (want[fid] != 0))
+            return fail(SPH_EINVAL, "%s: field %d %s", what, fid,
+                        want[fid] ? "is selected but NULL" : "was not selected at create");
+    }
+    for (int k = 0; k < nf; ++k) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, p[ids[k]]) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SPH_EINVAL, "%s: field %d is not a host pointer CUDA knows", what, ids[k]);
+        }
+        if (at.type != cudaMemoryTypeHost)
+            return fail(SPH_EINVAL, "%s: field %d must be page-locked host memory", what, ids[k]);
+        out[k] = p[ids[k]];
+    }
+    return SPH_OK;
+}
+
+static void hostio_fields(char *const *stage, const int *ids, int nf, sph_fields *out) {
+    std::memset(out, 0, sizeof(*out));
+    void **p = reinterpret_cast<void **>(out);
+    for (int k = 0; k < nf; ++k) p[ids[k]] = stage[k];
+}
+
+}  // namespace sph
+
+extern "C" {
+
+size_t sph_hostio_bytes(int64_t n, const sph_fields *in_sel, const sph_fields *out_sel) {
+    if (n < 0) return 0;
+    int fi[F_BALLAST], fo[F_BALLAST];
+    const int ni = hostio_select(in_sel, fi), no = hostio_select(out_sel, fo);
+    return 2 * (hostio_set_bytes(n, fi, ni) + hostio_set_bytes(n, fo, no));
+}
+
+int sph_hostio_create(sph_store s, const int64_t *dev_perm, const sph_fields *in_sel,
+                      const sph_fields *out_sel, void *dev_staging, size_t bytes,
+                      void *copy_in_stream, void *copy_out_stream, sph_hostio *out) {
+    if (!out) return fail(SPH_EINVAL, "NULL out");
+    *out = nullptr;
+    if (int rc = check_store(s)) return rc;
+    if (!dev_perm && s->n > 0) return fail(SPH_EINVAL, "NULL permutation");
+    if (!aligned256(dev_staging)) return fail(SPH_EINVAL, "staging must be 256-byte aligned");
+    auto *io = new (std::nothrow) sph_hostio_s();
+    if (!io) return fail(SPH_ENOMEM, "host I/O handle");
+    io->s = s;
+    io->perm = dev_perm;
+    io->nin = hostio_select(in_sel, io->fin);
+    io->nout = hostio_select(out_sel, io->fout);
+    if (io->nin + io->nout == 0) {
+        delete io;
+        return fail(SPH_EINVAL, "no field selected");
+    }
+    const size_t need = sph_hostio_bytes(s->n, in_sel, out_sel);
+    if (bytes < need || (need > 0 && !dev_staging)) {
+        delete io;
+        return fail(SPH_EINVAL, "staging holds %zu bytes, needs %zu", bytes, need);
+    }
+    char *p = (char *)dev_staging;
+    for (int b = 0; b < 2; ++b) {
+        for (int k = 0; k < io->nin; ++k) {
+            io->stage_in[b][k] = p;
+            p += r256(hostio_field_bytes(s->n, io->fin[k]));
+        }
+        for (int k = 0; k < io->nout; ++k) {
+            io->stage_out[b][k] = p;
+            p += r256(hostio_field_bytes(s->n, io->fout[k]));
+        }
+    }
+    for (int f = 0; f < F_BALLAST; ++f) io->fbytes[f] = hostio_field_bytes(s->n, f);
+    io->copy_in = (cudaStream_t)copy_in_stream;
+    io->copy_out = (cudaStream_t)copy_out_stream;
+    cudaEvent_t *ev[8] = {&io->in_ready[0], &io->in_ready[1], &io->in_free[0], &io->in_free[1],
+                          &io->out_ready[0], &io->out_ready[1], &io->out_free[0],
+                          &io->out_free[1]};
+    for (int e = 0; e < 8; ++e) {
+        if (int rc = cuda_check(cudaEventCreateWithFlags(ev[e], cudaEventDisableTiming),
+                                "host I/O event")) {
+            for (int q = 0; q < io->nev; ++q) cudaEventDestroy(*ev[q]);
+            delete io;
+            return rc;
+        }
+        io->nev = e + 1;
+    }
+    *out = io;
+    return SPH_OK;
+}
+
+int sph_hostio_begin(sph_hostio io, const sph_fields *host_in, void *stream) {
+    if (!io) return fail(SPH_EINVAL, "NULL host I/O handle");
+    if (io->open) return fail(SPH_EINVAL, "host I/O: the previous step was not ended");
+    void *src[F_BALLAST];
+    if (int rc = hostio_host_ptrs(host_in, io->fin, io->nin, src, "host I/O begin")) return rc;
+    const int b = (int)(io->k & 1);
+    cudaStream_t st = (cudaStream_t)stream;
+    // staging set b was last read by the import of step k - 2
+    if (int rc = cuda_check(cudaStreamWaitEvent(io->copy_in, io->in_free[b], 0), "wait"))
+        return rc;
+    for (int k = 0; k < io->nin; ++k)
+        if (int rc = cuda_check(cudaMemcpyAsync(io->stage_in[b][k], src[k],
+                                                io->fbytes[io->fin[k]], cudaMemcpyHostToDevice,
+                                                io->copy_in),
+                                "host I/O H2D"))
+            return rc;
+    if (int rc = cuda_check(cudaEventRecord(io->in_ready[b], io->copy_in), "record")) return rc;
+    if (int rc = cuda_check(cudaStreamWaitEvent(st, io->in_ready[b], 0), "wait")) return rc;
+    if (io->nin > 0) {
+        sph_fields F;
+        hostio_fields(io->stage_in[b], io->fin, io->nin, &F);
+        if (int rc = sph_store_import(io->s, &F, io->perm, stream)) return rc;
+    }
+    if (int rc = cuda_check(cudaEventRecord(io->in_free[b], st), "record")) return rc;
+    io->open = true;
+    return SPH_OK;
+}
+
+int sph_hostio_end(sph_hostio io, const sph_fields *host_out, void *stream) {
+    if (!io) return fail(SPH_EINVAL, "NULL host I/O handle");
+    if (!io->open) return fail(SPH_EINVAL, "host I/O: no step was begun");
+    void *dst[F_BALLAST];
+    if (int rc = hostio_host_ptrs(host_out, io->fout, io->nout, dst, "host I/O end")) return rc;
+    const int b = (int)(io->k & 1);
+    cudaStream_t st = (cudaStream_t)stream;
+    // staging set b was last read by the D2H copies of step k - 2
+    if (int rc = cuda_check(cudaStreamWaitEvent(st, io->out_free[b], 0), "wait")) return rc;
+    if (io->nout > 0) {
+        sph_fields F;
+        hostio_fields(io->stage_out[b], io->fout, io->nout, &F);
+        if (int rc = sph_store_export(io->s, &F, io->perm, stream)) return rc;
+    }
+    if (int rc = cuda_check(cudaEventRecord(io->out_ready[b], st), "record")) return rc;
+    if (int rc = cuda_check(cudaStreamWaitEvent(io->copy_out, io->out_ready[b], 0), "wait"))
+        return rc;
+    for (int k = 0; k < io->nout; ++k)
+        if (int rc = cuda_check(cudaMemcpyAsync(dst[k], io->stage_out[b][k],
+                                                io->fbytes[io->fout[k]], cudaMemcpyDeviceToHost,
+                                                io->copy_out),
+                                "host I/O D2H"))
+            return rc;
+    if (int rc = cuda_check(cudaEventRecord(io->out_free[b], io->copy_out), "record")) return rc;
+    io->open = false;
+    ++io->k;
+    return SPH_OK;
+}
+
+int sph_hostio_drain(sph_hostio io, void *stream) {
+    if (!io) return fail(SPH_EINVAL, "NULL host I/O handle");
+    if (io->k == 0) return SPH_OK;
+    const int b = (int)((io->k - 1) & 1);
+    return cuda_check(cudaStreamWaitEvent((cudaStream_t)stream, io->out_free[b], 0), "wait");
+}
+
+int sph_hostio_info(sph_hostio io, int64_t info[3]) {
+    if (!io || !info) return fail(SPH_EINVAL, "NULL argument");
+    int64_t hin = 0, hout = 0;
+    for (int k = 0; k < io->nin; ++k) hin += (int64_t)io->fbytes[io->fin[k]];
+    for (int k = 0; k < io->nout; ++k) hout += (int64_t)io->fbytes[io->fout[k]];
+    info[0] = hin;
+    info[1] = hout;
+    info[2] = io->k;
+    return SPH_OK;
+}
+
+int sph_hostio_destroy(sph_hostio io) {
+    if (!io) return SPH_OK;
+    cudaEvent_t ev[8] = {io->in_ready[0], io->in_ready[1], io->in_free[0], io->in_free[1],
+                         io->out_ready[0], io->out_ready[1], io->out_free[0], io->out_free[1]};
+    for (int e = 0; e < io->nev; ++e) cudaEventDestroy(ev[e]);
+    delete io;
+    return SPH_OK;
+}
+
+// ---- arithmetic-peak microbenchmarks ----------------------------------------
+int sph_peak_run(int kind, int64_t iters, void *dev_sink, void *stream, double *flops_out) {
+    if (kind < 0 || kind > 2) return fail(SPH_EINVAL, "bad peak kind %d", kind);
+    if (iters <= 0 || !dev_sink || !aligned256(dev_sink))
+        return fail(SPH_EINVAL, "iters must be > 0 and the sink a 256-byte aligned pointer");
+    int dev = 0, sms = 0;
+    if (int rc = cuda_check(cudaGetDevice(&dev), "device")) return rc;
+    if (int rc = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev),
+                            "SM count"))
+        return rc;
+    const int blocks = 4 * sms, threads = 256;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (kind == 0)
+        k_peak<float, 0><<<blocks, threads, 0, st>>>(iters, 1.0f, (float *)dev_sink);
+    else if (kind == 1)
+        k_peak<double, 1><<<blocks, threads, 0, st>>>(iters, 1.0, (double *)dev_sink);
+    else
+        k_peak<double, 2><<<blocks, threads, 0, st>>>(iters, 1.0, (double *)dev_sink);
+    if (flops_out)
+        *flops_out = (double)blocks * threads * (double)iters * kPeakUnroll * kPeakChains *
+                     (kind == 2 ? 1.0 : 2.0);
+    return launch_check("peak microbenchmark");
 }
 
 int sph_tasks_build(int64_t n, const double *host_x, const float *host_h,
@@ -768,6 +1033,9 @@ int sph_sync(void *stream) {
     if (w) {
         unsigned int z = 0;
         cudaMemcpyToSymbol(g_error_word, &z, sizeof(z));
+        if (w & 8u)
+            return fail(SPH_EUNSUPPORTED, "a particle's support exceeds what the batched plan "
+                                          "was built for; rebuild the plan (word 0x%x)", w);
         if (w & 4u)
             return fail(SPH_ENOMEM, "neighbour list buffer too small: read "
                                     "sph_batch_list_status and grow it (word 0x%x)", w);
@@ -881,9 +1149,23 @@ int sph_ghost_host(sph_store s, int after_loop, const sph_params *p, int nthread
     return host_ghost(s, (float)p->kernel_gamma, (float)p->gamma, (float)p->balsara_eps, nthreads);
 }
 
-int sph_offload_loop_host(sph_store s, sph_tasks t, int loop, void *const host_in[2],
-                          void *const host_out[2], void *const dev_in[2], void *const dev_out[2],
-                          const sph_params *p, void *const streams[2], int nthreads) {
+}  // extern "C"
+
+namespace sph {
+
+static double host_now() {
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+// The host-staged cycle of one loop; with `stats`, every stage is timed: the
+// host pack, unpack and waits on the host clock, the copies and the kernel
+// of each bundle with CUDA events on its stream.
+static int offload_loop_host(sph_store s, sph_tasks t, int loop, void *const host_in[2],
+                             void *const host_out[2], void *const dev_in[2],
+                             void *const dev_out[2], const sph_params *p,
+                             void *const streams[2], int nthreads, sph_staged_stats *stats) {
     if (int rc = check_host_store(s)) return rc;
     if (!t) return fail(SPH_EINVAL, "NULL tasks handle");
     if (int rc = check_loop(loop)) return rc;
@@ -894,13 +1176,26 @@ int sph_offload_loop_host(sph_store s, sph_tasks t, int loop, void *const host_i
         if (!aligned256(host_in[k]) || !aligned256(host_out[k]) || !aligned256(dev_in[k]) ||
             !aligned256(dev_out[k]) || !host_in[k] || !host_out[k] || !dev_in[k] || !dev_out[k])
             return fail(SPH_EINVAL, "buffers must be non-NULL and 256-byte aligned");
+    const double t_start = host_now();
+    double t_pack = 0.0, t_unpack = 0.0, t_wait = 0.0;
+    int64_t h2d_bytes = 0, d2h_bytes = 0;
     if (int rc = host_init(s, loop, p->active_bin, nthreads)) return rc;
     const int nb = (int)t->bundle_slots.size();
     cudaStream_t st[2] = {(cudaStream_t)streams[0], (cudaStream_t)streams[1]};
     cudaEvent_t done[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> tev;   // per bundle: before H2D, after H2D, after kernel, after D2H
     int rc = SPH_OK;
     for (int k = 0; k < 2 && rc == SPH_OK; ++k)
         rc = cuda_check(cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming), "event");
+    if (stats && rc == SPH_OK) {
+        tev.assign(4 * (size_t)nb, nullptr);
+        for (size_t e = 0; e < tev.size() && rc == SPH_OK; ++e)
+            rc = cuda_check(cudaEventCreate(&tev[e]), "timing event");
+    }
+    auto mark = [&](int b, int q, cudaStream_t s_) -> int {
+        return stats ? cuda_check(cudaEventRecord(tev[4 * (size_t)b + q], s_), "event record")
+                     : SPH_OK;
+    };
     for (int b = 0; b < nb && rc == SPH_OK; ++b) {
         const int k = b & 1;
         int64_t off[16];
@@ -908,24 +1203,40 @@ int sph_offload_loop_host(sph_store s, sph_tasks t, int loop, void *const host_i
         const size_t out_b = (size_t)lane_offsets(loop, 1, t->bundle_slots[b], off);
         // buffers k were last used by bundle b-2, whose results were unpacked
         // after its event completed in the previous iteration
+        double t0 = host_now();
         if ((rc = sph_pack_host(s, t, loop, b, host_in[k], nthreads))) break;
+        t_pack += host_now() - t0;
+        if ((rc = mark(b, 0, st[k]))) break;
         if ((rc = cuda_check(cudaMemcpyAsync(dev_in[k], host_in[k], in_b,
                                              cudaMemcpyHostToDevice, st[k]), "H2D")))
             break;
+        if ((rc = mark(b, 1, st[k]))) break;
         if ((rc = interact(t, loop, b, dev_in[k], dev_out[k], p, nullptr, st[k]))) break;
+        if ((rc = mark(b, 2, st[k]))) break;
         if ((rc = cuda_check(cudaMemcpyAsync(host_out[k], dev_out[k], out_b,
                                              cudaMemcpyDeviceToHost, st[k]), "D2H")))
             break;
+        if ((rc = mark(b, 3, st[k]))) break;
+        h2d_bytes += (int64_t)in_b;
+        d2h_bytes += (int64_t)out_b;
         if ((rc = cuda_check(cudaEventRecord(done[k], st[k]), "event record"))) break;
         if (b >= 1) {
+            t0 = host_now();
             if ((rc = cuda_check(cudaEventSynchronize(done[k ^ 1]), "event wait"))) break;
+            const double t1 = host_now();
+            t_wait += t1 - t0;
             if ((rc = sph_unpack_host(s, t, loop, b - 1, host_out[k ^ 1], nthreads))) break;
+            t_unpack += host_now() - t1;
         }
     }
     if (rc == SPH_OK && nb > 0) {
         const int k = (nb - 1) & 1;
+        double t0 = host_now();
         rc = cuda_check(cudaEventSynchronize(done[k]), "event wait");
+        const double t1 = host_now();
+        t_wait += t1 - t0;
         if (rc == SPH_OK) rc = sph_unpack_host(s, t, loop, nb - 1, host_out[k], nthreads);
+        t_unpack += host_now() - t1;
     }
     if (rc != SPH_OK) {
         cudaStreamSynchronize(st[0]);
@@ -933,8 +1244,54 @@ int sph_offload_loop_host(sph_store s, sph_tasks t, int loop, void *const host_i
     }
     for (int k = 0; k < 2; ++k)
         if (done[k]) cudaEventDestroy(done[k]);
-    if (rc == SPH_OK && loop == SPH_DENSITY) rc = sph_ghost_host(s, SPH_DENSITY, p, nthreads);
+    if (rc == SPH_OK && loop == SPH_DENSITY) {
+        const double t0 = host_now();
+        rc = sph_ghost_host(s, SPH_DENSITY, p, nthreads);
+        t_unpack += host_now() - t0;
+    }
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        for (int b = 0; b < nb && rc == SPH_OK; ++b) {
+            float ms[3] = {0.f, 0.f, 0.f};
+            for (int q = 0; q < 3 && rc == SPH_OK; ++q)
+                rc = cuda_check(cudaEventElapsedTime(&ms[q], tev[4 * (size_t)b + q],
+                                                     tev[4 * (size_t)b + q + 1]),
+                                "elapsed time");
+            stats->h2d_ms += ms[0];
+            stats->kernel_ms += ms[1];
+            stats->d2h_ms += ms[2];
+        }
+        for (cudaEvent_t e : tev)
+            if (e) cudaEventDestroy(e);
+        stats->wall_s = host_now() - t_start;
+        stats->host_pack_s = t_pack;
+        stats->host_unpack_s = t_unpack;
+        stats->host_wait_s = t_wait;
+        stats->h2d_bytes = h2d_bytes;
+        stats->d2h_bytes = d2h_bytes;
+        stats->bundles = nb;
+    }
     return rc;
+}
+
+}  // namespace sph
+
+extern "C" {
+
+int sph_offload_loop_host(sph_store s, sph_tasks t, int loop, void *const host_in[2],
+                          void *const host_out[2], void *const dev_in[2], void *const dev_out[2],
+                          const sph_params *p, void *const streams[2], int nthreads) {
+    return offload_loop_host(s, t, loop, host_in, host_out, dev_in, dev_out, p, streams,
+                             nthreads, nullptr);
+}
+
+int sph_offload_loop_host_stats(sph_store s, sph_tasks t, int loop, void *const host_in[2],
+                                void *const host_out[2], void *const dev_in[2],
+                                void *const dev_out[2], const sph_params *p,
+                                void *const streams[2], int nthreads, sph_staged_stats *stats) {
+    if (!stats) return fail(SPH_EINVAL, "NULL stats");
+    return offload_loop_host(s, t, loop, host_in, host_out, dev_in, dev_out, p, streams,
+                             nthreads, stats);
 }
 
 // ---- batched (cell-dedup) pipeline ---------------------------------------
@@ -1432,6 +1789,37 @@ int sph_batch_list_build(sph_store s, sph_batch b, void *dev_buf_in, void *dev_l
             return rc;
     }
     return SPH_OK;
+}
+
+int sph_batch_list_count(sph_store s, sph_batch b, int bundle, const void *dev_buf_in,
+                         void *dev_list, size_t list_bytes, const sph_params *p,
+                         unsigned long long *dev_counts, void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (int rc = check_batch(b, bundle)) return rc;
+    if (int rc = check_params(p)) return rc;
+    if (s->n != b->n) return fail(SPH_EINVAL, "store and batch disagree on particle count");
+    if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_list || !aligned256(dev_list) ||
+        !dev_counts || ((uintptr_t)dev_counts & 7u))
+        return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers, the counts "
+                                "8-byte aligned");
+    const int64_t NI = (int64_t)b->items.size();
+    if ((int64_t)list_bytes < ListLayout::fixed(NI) + 512)
+        return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
+    cudaStream_t st = (cudaStream_t)stream;
+    ListView L = ListLayout::view(dev_list, NI, (int64_t)list_bytes);
+    if (bundle == 0)
+        if (int rc = cuda_check(cudaMemsetAsync(L.hdr, 0, sizeof(ListHdr), st),
+                                "reset list header"))
+            return rc;
+    const BatchBundle &bb = b->bundles[bundle];
+    if (bb.nitems == 0) return SPH_OK;
+    BInteractArgs a = interact_args(b, bundle, dev_buf_in, nullptr, p);
+    if (int rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st),
+                            "reset work queue"))
+        return rc;
+    if (b->fixed_build)
+        return dispatch_blist_count_p<true>(b->threads, a, L, bb.item0, dev_counts, st);
+    return dispatch_blist_count_p<false>(b->threads, a, L, bb.item0, dev_counts, st);
 }
 
 int sph_batch_list_build_bundle(sph_store s, sph_batch b, int bundle, const void *dev_buf_in,

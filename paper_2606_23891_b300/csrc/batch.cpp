@@ -35,6 +35,7 @@ namespace {
 // global cell indices.
 struct GlobalPlan {
     std::vector<int64_t> p0, cnt;      // store range of each cell
+    std::vector<float> hlim;           // largest support the plan holds per cell
     std::vector<int64_t> nb_start;     // CSR over cells
     std::vector<int32_t> nb_cell;
     std::vector<uint8_t> nb_code;
@@ -73,7 +74,9 @@ int assemble(const GlobalPlan &G, const sph_batch_params *bp, sph_batch_s *B) {
             cd.p0 = (int32_t)G.p0[c];
             cd.n = (int32_t)G.cnt[c];
             cd.slot = (int32_t)slot;
-            cd.pad = 0;
+            // a little above the plan's value: the kernels' H = gamma_K h
+            // may round differently from the host's
+            cd.hlim = G.hlim.empty() ? INFINITY : G.hlim[c] * (1.f + 1e-6f);
             B->cells.push_back(cd);
             slot += G.cnt[c];
         }
@@ -161,14 +164,18 @@ int build_batch(const sph_tasks_s *T, const sph_batch_params *bp, sph_batch_s *B
     // below half the box when every dimension has 5 or more cells
     B->fixed_build = nc[0] >= 5 && nc[1] >= 5 && nc[2] >= 5;
 
-    // cells with particles, in grid index order
+    // cells with particles, in grid index order; any support up to the
+    // shortest cell edge keeps every pair inside adjacent cells
     GlobalPlan G;
+    double edge = INFINITY;
+    for (int d = 0; d < 3; ++d) edge = std::min(edge, T->box[d] / nc[d]);
     std::vector<int32_t> id((size_t)ngrid, -1);
     for (int64_t c = 0; c < ngrid; ++c)
         if (count(c) > 0) {
             id[c] = (int32_t)G.cnt.size();
             G.p0.push_back(T->cell_start[c]);
             G.cnt.push_back(count(c));
+            G.hlim.push_back((float)edge);
         }
     // 27 periodic neighbours in (dz, dy, dx) order, empty cells dropped
     G.nb_start.push_back(0);
@@ -357,9 +364,11 @@ int tree_plan(int64_t n, const double *x, const float *h, const sph_tree_params 
     // the target's box, by a walk pruned with each subtree's box and H_max
     G.p0.resize((size_t)nleaf);
     G.cnt.resize((size_t)nleaf);
+    G.hlim.resize((size_t)nleaf);
     for (int64_t l = 0; l < nleaf; ++l) {
         G.p0[(size_t)l] = nodes[leaves[l]].b;
         G.cnt[(size_t)l] = nodes[leaves[l]].e - nodes[leaves[l]].b;
+        G.hlim[(size_t)l] = nodes[leaves[l]].hmax;
     }
     const int nth = omp_get_max_threads();
     std::vector<std::vector<int32_t>> tcell((size_t)nth);

@@ -207,6 +207,9 @@ __global__ void __launch_bounds__(128) k_bpack(BPackArgs a) {
         float hm = hred[0];
         for (int w = 1; w < (int)(blockDim.x >> 5); ++w) hm = fmaxf(hm, hred[w]);
         reinterpret_cast<float *>(a.buf + BL::cellh(a.S))[blockIdx.x] = hm;
+        // a support beyond what the plan was built for: the neighbour
+        // entries may miss pairs (bit 3 of the error word, SPH_EUNSUPPORTED)
+        if (hm > C.hlim) atomicOr(&g_error_word, 8u);
     }
     // octant key of particle k (0 when the cell keeps store order)
     auto key_of = [&](int k) -> int {

@@ -117,9 +117,13 @@ struct sph_tasks_s {
 
 // ---- batched (cell-dedup) pipeline records --------------------------------
 // A cell of a batched bundle: particles [p0, p0+n) of the store, packed at
-// bundle slots [slot, slot+n) (octant-sorted inside the cell).
+// bundle slots [slot, slot+n) (octant-sorted inside the cell).  hlim: the
+// largest support H the plan holds for the cell's particles (grid: the cell
+// edge; tree: the leaf's largest support when the plan was built); the
+// density pack reports a larger one (the plan must then be rebuilt).
 struct BCellDev {
-    int32_t p0, n, slot, pad;
+    int32_t p0, n, slot;
+    float hlim;
 };
 // A target cell: its local cell index and its neighbour entries
 // [nb0, nb0 + nnb) of the plan's neighbour list.

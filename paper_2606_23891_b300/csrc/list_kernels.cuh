@@ -91,8 +91,14 @@ struct ListLayout {
 // item's first particle is the image nearest each of its particles for every
 // pair that can interact, and no cell enters a target's entries twice.
 // Otherwise the two-float path: hi/lo records, shifts by the entry codes.
-template <int T, bool FIXED>
-__global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView L, long long item0) {
+// COUNT: the same build, also summing into cnt[0..4] the candidates staged,
+// the (particle, candidate) pairs that pass the warp-box cull (each one
+// prefiltered in pass 1), the pass-1 hits, the hits that take the exact
+// test, and the entries written (a measurement variant; the timed build has
+// COUNT = false and no counters).
+template <int T, bool FIXED, bool COUNT = false>
+__global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView L, long long item0,
+                                                       unsigned long long *cnt) {
     using BL = BLayout<SPH_DENSITY>;
     constexpr int kWarps = T / 32;
     __shared__ float4 smw[kWarps][2][kWTile];
@@ -155,6 +161,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
             hw = fmaxf(hw, __shfl_xor_sync(0xffffffffu, hw, o));
         }
         int count = 0;      // this lane's entries
+        unsigned int c_stage = 0, c_cull = 0, c_hit = 0, c_exact = 0;   // COUNT only
         int nch = 0;        // chunks of the item (warp-uniform)
         bool lost = false;  // the pool or the chain ran out (warp-uniform)
         const BTargetDev &Tg = a.targets[W.target];
@@ -214,7 +221,10 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
                         in = ex * ex + ey * ey + ez * ez < R2;
                     }
                     cw[w] = __ballot_sync(0xffffffffu, in);
+                    if constexpr (COUNT)
+                        if (valid) c_cull += __popc(cw[w]);
                 }
+                if constexpr (COUNT) c_stage += (unsigned int)jn;
                 __syncwarp();
                 // pass 1: hi-only prefilter under the wider (force) criterion;
                 // FIXED: also the hits certainly inside H_i
@@ -241,6 +251,10 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
                         h &= ~(1u << (i - j0 - 32 * w));
                     hm[w] = valid ? h : 0u;
                     sure[w] = su & hm[w];
+                    if constexpr (COUNT) {
+                        c_hit += __popc(hm[w]);
+                        c_exact += __popc(FIXED ? hm[w] & ~sure[w] : hm[w]);
+                    }
                 }
                 // FIXED: the exact decisions on the other hits (dm: r < H_i);
                 // hm keeps the accepted ones, in slot order
@@ -331,6 +345,19 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
         }
         L.lcount[gitem * 32 + lane] = valid && !lost ? (uint32_t)count : 0u;
         if (lane == 0) L.first[gitem] = nch > 0 && !lost ? chain[0] : kLNone;
+        if constexpr (COUNT) {
+            const unsigned int ce = __reduce_add_sync(0xffffffffu, valid ? (unsigned int)count : 0u);
+            const unsigned int cc = __reduce_add_sync(0xffffffffu, c_cull);
+            const unsigned int ch = __reduce_add_sync(0xffffffffu, c_hit);
+            const unsigned int cx = __reduce_add_sync(0xffffffffu, c_exact);
+            if (lane == 0) {
+                atomicAdd(&cnt[0], (unsigned long long)c_stage);
+                atomicAdd(&cnt[1], (unsigned long long)cc);
+                atomicAdd(&cnt[2], (unsigned long long)ch);
+                atomicAdd(&cnt[3], (unsigned long long)cx);
+                atomicAdd(&cnt[4], (unsigned long long)ce);
+            }
+        }
         __syncwarp();
     }
 }
@@ -356,8 +383,11 @@ struct AccL<SPH_GRADIENT> {
     __device__ __forceinline__ void body(const float4 *own, const float4 *oth, float dx,
                                          float dy, float dz, float r2, const PhysArgs &a) {
         const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-        // clamped: the list was decided on two-float separations, this
-        // fixed-point one may round a support-edge pair to just past q = 1
+        // clamped: on two-float plans the list was decided on two-float
+        // separations, and this fixed-point one may round a support-edge pair
+        // to just past q = 1; on fixed-point plans the prefilter settles hits
+        // on item-relative floats (inside H_i by a margin), and r * (1/H)
+        // rounds again here, so the clamp stays as a guard
         const float q = fminf(r2 * rinv * Hinv, 1.f);
         float w, dw;
         spline(q, w, dw);

@@ -415,69 +415,73 @@ def host_fields_struct(arrays: dict) -> sph.Fields:
     return F
 
 
+def pinned_fields(n: int, names) -> dict:
+    """Page-locked host tensors for the named fields of n particles."""
+    out = {}
+    for name in names:
+        dt, k = field_spec(name)
+        shape = (n, k) if k > 1 else (n,)
+        out[name] = torch.empty(shape, dtype=_TORCH_DT[dt]).pin_memory()
+    return out
+
+
 class StreamingSteps:
-    """End-to-end steps from pinned host inputs to pinned host results with
-    the copies overlapped: while step k computes on the offload's stream,
-    step k+1's inputs travel host -> device on one copy stream and step k-1's
-    results device -> host on another.  Each step still copies its inputs in
-    and its results out; two device staging sets alternate between steps."""
+    """End-to-end steps from pinned host inputs to pinned host results,
+    entirely through the library's host I/O handle (sph_hostio_*): each step
+    copies its inputs host -> device and imports them, runs `step_fn` (library
+    calls on the offload's stream), exports its results and copies them
+    device -> host.  The library double-buffers the device staging and issues
+    the copies on two copy streams, so step k+1's inputs and step k-1's
+    results travel while step k computes."""
 
     def __init__(self, off: "Offload", step_fn, names_in=INPUTS, names_out=OUTPUTS):
         self.off = off
         self.step_fn = step_fn
         self.names_in, self.names_out = tuple(names_in), tuple(names_out)
-        dev = off.device
-        self.dev_in = []
-        for _ in range(2):
-            d = {}
-            for name in self.names_in:
-                dt, k = field_spec(name)
-                shape = (off.n, k) if k > 1 else (off.n,)
-                d[name] = torch.empty(shape, dtype=torch.from_numpy(np.zeros(0, dt)).dtype,
-                                      device=dev)
-            self.dev_in.append(d)
-        self.dev_out = [off.device_fields(self.names_out) for _ in range(2)]
-        self.s_in = torch.cuda.Stream(dev)
-        self.s_out = torch.cuda.Stream(dev)
-        ev = lambda: torch.cuda.Event()
-        self.in_ready = [ev() for _ in range(2)]
-        self.in_free = [ev() for _ in range(2)]
-        self.out_ready = [ev() for _ in range(2)]
-        self.out_free = [ev() for _ in range(2)]
-        self.k = 0
+        sel_in, sel_out = sph.Fields(), sph.Fields()
+        for name in self.names_in:
+            setattr(sel_in, name, 1)
+        for name in self.names_out:
+            setattr(sel_out, name, 1)
+        nbytes = sph.sph_hostio_bytes(off.n, sel_in, sel_out)
+        self.staging = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=off.device)
+        self.s_in = torch.cuda.Stream(off.device)
+        self.s_out = torch.cuda.Stream(off.device)
+        self.io = sph.sph_hostio_create(off.store, off.d_perm.data_ptr(), sel_in, sel_out,
+                                        self.staging.data_ptr(), nbytes,
+                                        self.s_in.cuda_stream, self.s_out.cuda_stream)
+
+    def pinned_in(self) -> dict:
+        return pinned_fields(self.off.n, self.names_in)
+
+    def pinned_out(self) -> dict:
+        return pinned_fields(self.off.n, self.names_out)
 
     def bytes_per_step(self):
-        h2d = sum(t.numel() * t.element_size() for t in self.dev_in[0].values())
-        d2h = sum(t.numel() * t.element_size() for t in self.dev_out[0].values())
-        return h2d, d2h
+        info = sph.sph_hostio_info(self.io)
+        return info["h2d_bytes_per_step"], info["d2h_bytes_per_step"]
 
     def step(self, pin_in: dict, pin_out: dict) -> None:
-        """Enqueue one step: H2D of pin_in, the step, D2H into pin_out."""
-        b = self.k & 1
-        comp = torch.cuda.current_stream(self.off.device)
-        di, do = self.dev_in[b], self.dev_out[b]
-        self.s_in.wait_event(self.in_free[b])
-        with torch.cuda.stream(self.s_in):
-            for name in self.names_in:
-                di[name].copy_(pin_in[name], non_blocking=True)
-            self.in_ready[b].record(self.s_in)
-        comp.wait_event(self.in_ready[b])
-        self.off.import_device(di)
-        self.in_free[b].record(comp)
+        """Enqueue one step: H2D of pin_in, the step, D2H into pin_out (all
+        arrays page-locked, original particle order)."""
+        sph.sph_hostio_begin(self.io, fields_struct(pin_in), self.off.stream)
         self.step_fn()
-        comp.wait_event(self.out_free[b])
-        sph.sph_store_export(self.off.store, fields_struct(do), self.off.d_perm.data_ptr(),
-                             self.off.stream)
-        self.out_ready[b].record(comp)
-        self.s_out.wait_event(self.out_ready[b])
-        with torch.cuda.stream(self.s_out):
-            for name in self.names_out:
-                pin_out[name].copy_(do[name], non_blocking=True)
-            self.out_free[b].record(self.s_out)
-        self.k += 1
+        sph.sph_hostio_end(self.io, fields_struct(pin_out), self.off.stream)
 
     def drain(self) -> None:
-        torch.cuda.current_stream(self.off.device).wait_stream(self.s_out)
+        """The offload's stream waits for the last step's results."""
+        sph.sph_hostio_drain(self.io, self.off.stream)
+
+    def close(self) -> None:
+        if getattr(self, "io", None) is not None:
+            sph.sph_hostio_destroy(self.io)
+            self.io = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class HostOffload:
@@ -601,6 +605,20 @@ class HostOffload:
     def step(self) -> None:
         for loop in (sph.SPH_DENSITY, sph.SPH_GRADIENT, sph.SPH_FORCE):
             self.loop(loop)
+
+    def loop_stats(self, loop: int) -> dict:
+        """One loop of the host-staged cycle with every stage timed
+        (sph_offload_loop_host_stats)."""
+        return sph.sph_offload_loop_host_stats(
+            self.store, self.tasks, loop, [b[0].ctypes.data for b in self.host_in],
+            [b[0].ctypes.data for b in self.host_out], [d.data_ptr() for d in self.dev_in],
+            [d.data_ptr() for d in self.dev_out], self.params,
+            [s.cuda_stream for s in self.streams], self.nthreads)
+
+    def step_stats(self) -> list:
+        """A step with every stage timed: the stats of each loop."""
+        return [self.loop_stats(loop)
+                for loop in (sph.SPH_DENSITY, sph.SPH_GRADIENT, sph.SPH_FORCE)]
 
     def task_list(self):
         nt = self.info["ntasks"]

@@ -143,6 +143,7 @@ def lib() -> C.CDLL:
         "sph_batch_list_build_bundle": (i, [p, p, i, p, p, sz, p, p]),
         "sph_batch_list_fixed": (i, [p]),
         "sph_batch_list_status": (i, [p, p, p]),
+        "sph_batch_list_count": (i, [p, p, i, p, p, sz, p, p, p]),
         "sph_batch_offload_loop_list": (i, [p, p, i, p, p, p, sz, p, p]),
         "sph_batch_offload_step_list": (i, [p, p, p, p, p, sz, p, p]),
         "sph_batch_list_interact": (i, [p, i, i, p, p, p, sz, p, p]),
@@ -160,6 +161,15 @@ def lib() -> C.CDLL:
         "sph_init_host": (i, [p, i, p, i]),
         "sph_ghost_host": (i, [p, i, p, i]),
         "sph_offload_loop_host": (i, [p, p, i, p, p, p, p, p, p, i]),
+        "sph_offload_loop_host_stats": (i, [p, p, i, p, p, p, p, p, p, i, p]),
+        "sph_hostio_bytes": (sz, [i64, p, p]),
+        "sph_hostio_create": (i, [p, p, p, p, p, sz, p, p, p]),
+        "sph_hostio_begin": (i, [p, p, p]),
+        "sph_hostio_end": (i, [p, p, p]),
+        "sph_hostio_drain": (i, [p, p]),
+        "sph_hostio_info": (i, [p, p]),
+        "sph_hostio_destroy": (i, [p]),
+        "sph_peak_run": (i, [i, i64, p, p, p]),
         "sph_tasks_destroy": (i, [p]),
     }
     for name, (res, args) in sig.items():
@@ -357,6 +367,68 @@ def sph_offload_loop_host(s, t, loop: int, host_in, host_out, dev_in, dev_out, p
                                     arr(dev_out), C.byref(p), arr(streams), nthreads))
 
 
+class StagedStats(C.Structure):
+    _fields_ = [("wall_s", C.c_double), ("host_pack_s", C.c_double),
+                ("host_unpack_s", C.c_double), ("host_wait_s", C.c_double),
+                ("h2d_ms", C.c_double), ("kernel_ms", C.c_double), ("d2h_ms", C.c_double),
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64), ("bundles", C.c_int64)]
+
+
+def sph_offload_loop_host_stats(s, t, loop: int, host_in, host_out, dev_in, dev_out,
+                                p: Params, streams, nthreads: int = 0) -> dict:
+    """sph_offload_loop_host with every stage timed; returns the stats."""
+    arr = lambda v: (C.c_void_p * 2)(*[int(x) for x in v])
+    st = StagedStats()
+    _ok(lib().sph_offload_loop_host_stats(s, t, loop, arr(host_in), arr(host_out), arr(dev_in),
+                                          arr(dev_out), C.byref(p), arr(streams), nthreads,
+                                          C.byref(st)))
+    return {name: getattr(st, name) for name, _ in StagedStats._fields_}
+
+
+def sph_hostio_bytes(n: int, in_sel: Fields, out_sel: Fields) -> int:
+    return lib().sph_hostio_bytes(n, C.byref(in_sel), C.byref(out_sel))
+
+
+def sph_hostio_create(s, dev_perm: int, in_sel: Fields, out_sel: Fields, dev_staging: int,
+                      nbytes: int, copy_in_stream: int, copy_out_stream: int):
+    h = C.c_void_p()
+    _ok(lib().sph_hostio_create(s, dev_perm, C.byref(in_sel), C.byref(out_sel), dev_staging,
+                                nbytes, copy_in_stream, copy_out_stream, C.byref(h)))
+    return h
+
+
+def sph_hostio_begin(io, host_in: Fields, stream: int = 0) -> None:
+    _ok(lib().sph_hostio_begin(io, C.byref(host_in), stream))
+
+
+def sph_hostio_end(io, host_out: Fields, stream: int = 0) -> None:
+    _ok(lib().sph_hostio_end(io, C.byref(host_out), stream))
+
+
+def sph_hostio_drain(io, stream: int = 0) -> None:
+    _ok(lib().sph_hostio_drain(io, stream))
+
+
+def sph_hostio_info(io) -> dict:
+    info = (C.c_int64 * 3)()
+    _ok(lib().sph_hostio_info(io, info))
+    return dict(zip(("h2d_bytes_per_step", "d2h_bytes_per_step", "steps"), list(info)))
+
+
+def sph_hostio_destroy(io) -> None:
+    _ok(lib().sph_hostio_destroy(io))
+
+
+PEAK_FP32_FMA, PEAK_FP64_FMA, PEAK_FP64_ADD = 0, 1, 2
+
+
+def sph_peak_run(kind: int, iters: int, dev_sink: int, stream: int = 0) -> float:
+    """Launch one arithmetic-peak microbenchmark; returns its flop count."""
+    fl = C.c_double()
+    _ok(lib().sph_peak_run(kind, iters, dev_sink, stream, C.byref(fl)))
+    return fl.value
+
+
 def sph_batch_build(t, max_target_cells: int = 0, threads: int = 128):
     h = C.c_void_p()
     bp = BatchParams(max_target_cells, threads, 0)
@@ -443,6 +515,12 @@ def sph_batch_list_status(dev_list: int):
     need, ovf = C.c_int64(), C.c_int()
     _ok(lib().sph_batch_list_status(dev_list, C.byref(need), C.byref(ovf)))
     return need.value, ovf.value
+
+
+def sph_batch_list_count(s, b, bundle: int, dev_in: int, dev_list: int, list_bytes: int,
+                         p: Params, dev_counts: int, stream: int = 0):
+    _ok(lib().sph_batch_list_count(s, b, bundle, dev_in, dev_list, list_bytes, C.byref(p),
+                                   dev_counts, stream))
 
 
 def sph_batch_pack_list(s, b, loop: int, bundle: int, dev_in: int, p: Params, stream: int = 0):

@@ -150,3 +150,31 @@ def test_empty_particle_set_builds_no_tasks():
     assert info["ntasks"] == 0 and info["nbundles"] == 0
     assert sph.sph_buffer_bytes(t, 0, 0) == 0
     sph.sph_tasks_destroy(t)
+
+
+def test_host_io_and_measurement_calls_check_their_arguments():
+    """Sizes and argument checks of the host I/O handle, the staged-cycle
+    statistics and the peak microbenchmark, without a GPU."""
+    L = sph.lib()
+    assert C.sizeof(sph.StagedStats) == 80
+    src = open(os.path.join(ROOT, "include", "sph.h")).read()
+    body = src[src.index("typedef struct {\n    double wall_s;"):src.index("} sph_staged_stats;")]
+    assert re.findall(r"(?:double|int64_t) (\w+);", body) == [n for n, _ in sph.StagedStats._fields_]
+    ins, outs = sph.Fields(), sph.Fields()
+    ins.x = ins.v = 1          # selections: only non-NULL matters
+    outs.rho = 1
+    # two staging sets, each field rounded up to 256 bytes
+    assert sph.sph_hostio_bytes(1000, ins, outs) == 2 * (24064 + 12032 + 4096)
+    assert sph.sph_hostio_bytes(-1, ins, outs) == 0
+    h = C.c_void_p()
+    assert L.sph_hostio_create(None, None, C.byref(ins), C.byref(outs), None, 0, None, None,
+                               C.byref(h)) == 1
+    assert L.sph_hostio_begin(None, C.byref(ins), None) == 1
+    assert L.sph_hostio_destroy(None) == 0
+    fl = C.c_double()
+    assert L.sph_peak_run(7, 10, None, None, C.byref(fl)) == 1
+    assert L.sph_peak_run(0, 0, None, None, C.byref(fl)) == 1
+    st = sph.StagedStats()
+    arr = (C.c_void_p * 2)()
+    assert L.sph_offload_loop_host_stats(None, None, 0, arr, arr, arr, arr, None, arr, 0,
+                                         C.byref(st)) == 1

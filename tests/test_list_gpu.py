@@ -102,7 +102,8 @@ def test_streaming_steps_give_each_steps_results():
     """Overlapped end-to-end steps: step k's results in pinned memory equal a
     plain list step on step k's inputs, with the copies of neighbouring
     steps in flight."""
-    from paper_2606_23891_b300.pipeline import INPUTS, StreamingSteps, field_spec
+    from paper_2606_23891_b300.pipeline import (INPUTS, StreamingSteps, field_spec,
+                                                fields_struct, host_fields_struct)
     base = ragged(12, 60)
     fs = []
     for k in range(3):        # same positions (the plan holds), other v and u
@@ -121,13 +122,15 @@ def test_streaming_steps_give_each_steps_results():
     ss = StreamingSteps(off, off.list_step)
     pins_in, pins_out = [], []
     for f in fs:
-        d = {}
+        d = ss.pinned_in()
         for name in INPUTS:
             dt, _ = field_spec(name)
-            d[name] = torch.from_numpy(np.ascontiguousarray(f[name], dt)).pin_memory()
+            d[name].numpy()[...] = np.asarray(f[name], dt)
         pins_in.append(d)
-        pins_out.append({k: torch.empty(v.shape, dtype=v.dtype).pin_memory()
-                         for k, v in ss.dev_out[0].items()})
+        pins_out.append(ss.pinned_out())
+    h2d, d2h = ss.bytes_per_step()
+    assert h2d == sum(t.numel() * t.element_size() for t in pins_in[0].values())
+    assert d2h == sum(t.numel() * t.element_size() for t in pins_out[0].values())
     for k in range(3):
         ss.step(pins_in[k], pins_out[k])
     ss.drain()
@@ -135,6 +138,17 @@ def test_streaming_steps_give_each_steps_results():
     for k in range(3):
         for name, v in ref[k].items():
             np.testing.assert_array_equal(pins_out[k][name].numpy(), v, err_msg=name)
+    # pageable host memory and an unselected field are refused before any copy
+    bad = {k: v.numpy().copy() for k, v in pins_in[0].items()}
+    with pytest.raises(sph.SphError, match="page-locked"):
+        sph.sph_hostio_begin(ss.io, host_fields_struct(bad), off.stream)
+    extra = dict(pins_in[0])
+    extra["rho"] = pins_out[0]["rho"]
+    with pytest.raises(sph.SphError, match="not selected"):
+        sph.sph_hostio_begin(ss.io, fields_struct(extra), off.stream)
+    with pytest.raises(sph.SphError, match="no step was begun"):
+        sph.sph_hostio_end(ss.io, fields_struct(pins_out[0]), off.stream)
+    ss.close()
 
 
 def test_list_and_batch_api_reject_misuse():
@@ -321,3 +335,36 @@ def test_list_build_path_follows_the_plan_geometry():
         assert sph.sph_batch_list_fixed(off.bplan) == fixed
         off.list_step()
         check_physics(f, off.export())
+
+
+def test_supports_beyond_the_plan_are_reported():
+    """A plan holds for the supports it was built from: the density pack
+    reports one beyond the cell's limit (grid: the cell edge; tree: the
+    leaf's largest support at build time) at the next sph_sync, and a step
+    within the limits is unaffected."""
+    f = ragged(12, 5)
+    grid = Offload(f, layout=6)
+    grid.batch()
+    grid.list_step()
+    sph.sph_sync(grid.stream)
+    # 1% larger supports stay below the grid's cell edge: no report
+    grid.import_fields({"h": (f["h"] * np.float32(1.01)).astype(np.float32)}, ("h",))
+    grid.list_step()
+    sph.sph_sync(grid.stream)
+    big = f["h"].copy()
+    big[17] *= np.float32(3.0)                 # beyond the cell edge
+    grid.import_fields({"h": big}, ("h",))
+    grid.list_step()
+    with pytest.raises(sph.SphError, match="rebuild the plan"):
+        sph.sph_sync(grid.stream)
+    grid.import_fields({"h": f["h"]}, ("h",))
+    grid.list_step()
+    sph.sph_sync(grid.stream)
+    # a tree plan's limit is each leaf's largest support at build time
+    tree = Offload(f, layout=6, plan="tree")
+    tree.list_step()
+    sph.sph_sync(tree.stream)
+    tree.import_fields({"h": (f["h"] * np.float32(1.01)).astype(np.float32)}, ("h",))
+    tree.list_step()
+    with pytest.raises(sph.SphError, match="rebuild the plan"):
+        sph.sph_sync(tree.stream)

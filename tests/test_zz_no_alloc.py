@@ -43,10 +43,20 @@ def test_noalloc_entry_point_matches_the_buffered_one_twice():
     want = ref.export(OUTPUTS)
     # same particles and tasks, a fresh store, the library's own scratch
     off = Offload(f, layout="pack_force_type", share=ref)
+    torch.cuda.synchronize()
     for call in range(2):
-        for loop in (sph.SPH_DENSITY, sph.SPH_GRADIENT, sph.SPH_FORCE):
-            sph.sph_offload_loop_noalloc(off.store, off.tasks, loop, off.params, off.stream)
-        sph.sph_sync(off.stream)
+        # the library's next device allocation of its own would fail (host-side
+        # injector): the calls must not need one; torch allocates nothing either
+        before = torch.cuda.memory_allocated()
+        sph.sph_fault_inject(sph.SPH_FAULT_DEVICE_ALLOC, 1)
+        try:
+            for loop in (sph.SPH_DENSITY, sph.SPH_GRADIENT, sph.SPH_FORCE):
+                sph.sph_offload_loop_noalloc(off.store, off.tasks, loop, off.params,
+                                             off.stream)
+            sph.sph_sync(off.stream)
+        finally:
+            sph.sph_fault_inject(sph.SPH_FAULT_NONE, 0)
+        assert torch.cuda.memory_allocated() == before
         got = off.export(OUTPUTS)
         for k in OUTPUTS:
             # same kernels, same bundles, same order: identical; the bar used
