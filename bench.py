@@ -1209,9 +1209,10 @@ def run_ours(args, ws, rank, local):
         "peaks": {"fp32_tflops": sig(peaks.get("fp32_tflops")),
                   "fp64_fma_tflops": sig(peaks.get("fp64_fma_tflops")),
                   "fp64_add_tflops": sig(peaks.get("fp64_add_tflops")),
-                  "hbm_gbs": mpeaks.get("hbm_gbs"),
-                  "h2d_gbs": sig(link["h2d_GBps"]), "d2h_gbs": sig(link["d2h_GBps"])},
+                  "hbm_gbs": mpeaks.get("hbm_gbs")},
     }
+    if link is not None:
+        line["peaks"].update(h2d_gbs=sig(link["h2d_GBps"]), d2h_gbs=sig(link["d2h_GBps"]))
     if staged is not None:
         line["staged"] = {
             lname: {"ms": sig(v["ms_per_step"]),

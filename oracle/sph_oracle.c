@@ -157,11 +157,14 @@ int64_t oracle_density(int64_t n, const double *x, const float *v,
 /* Conditioning scales of the two h-derivative sums of the density loop.     */
 /* Their terms change sign at q = 1/2 and largely cancel, so the value says  */
 /* nothing about the rounding a sum of them can carry; the sum of the terms' */
-/* magnitudes (self term included) does.  These are tolerance scales for    */
-/* comparisons, not results of the method.                                  */
+/* magnitudes does.  The self term of wcount_dh is an exact cancellation,   */
+/* (4 pi / 3)(3 H^2 W(0) + H^3 dW/dH(0)) = 0, which any evaluation leaves as */
+/* a rounding residue of its parts, so it enters with the magnitude of its   */
+/* two parts.  These are tolerance scales for comparisons, not results of   */
+/* the method.                                                               */
 /*   out[2 k + 0] = m_i |dW/dH(0, H_i)| + sum m_j |dW/dH(r, H_i)|            */
-/*   out[2 k + 1] = the same for the wcount_dh terms                         */
-/*                  (4 pi / 3) |3 H^2 W + H^3 dW/dH|                         */
+/*   out[2 k + 1] = (4 pi / 3)(3 H^2 W(0) + H^3 |dW/dH(0)|)                  */
+/*                  + sum (4 pi / 3) |3 H^2 W + H^3 dW/dH|                   */
 /* over j != i with r_ij < H_i.                                              */
 /* ------------------------------------------------------------------------ */
 void oracle_dh_scales(int64_t n, const double *x, const float *m, const float *h,
@@ -175,8 +178,8 @@ void oracle_dh_scales(int64_t n, const double *x, const float *m, const float *h
         double H2 = Hi * Hi * (1.0 + P->support_eps);
         double c = 4.0 * ORACLE_PI / 3.0;
         double s_rho = (double)m[i] * fabs(oracle_dWdH(0.0, Hi));
-        double s_w = c * fabs(3.0 * Hi * Hi * oracle_W(0.0, Hi) +
-                              Hi * Hi * Hi * oracle_dWdH(0.0, Hi));
+        double s_w = c * (3.0 * Hi * Hi * oracle_W(0.0, Hi) +
+                          Hi * Hi * Hi * fabs(oracle_dWdH(0.0, Hi)));
         for (int64_t j = 0; j < n; ++j) {
             if (j == i) continue;
             double d[3];

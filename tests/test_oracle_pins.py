@@ -626,24 +626,32 @@ def test_store_encoding_reads_back_through_numpy(layout):
 
 # ------------------------------------------------- h-derivative scales ---
 def test_dh_scales_bound_the_h_derivative_sums():
-    """The conditioning scales (sums of the terms' magnitudes) bound the
-    h-derivative sums and equal them when no term changes sign: the wcount_dh
-    terms never do (d/dH (H^3 W) = -(sigma/H) q w'(q) >= 0), and the rho_dh
-    terms do not for neighbours inside H/2 (3 w + q w' > 0 there)."""
+    """The conditioning scales (sums of the terms' magnitudes, the exactly
+    cancelling self term of wcount_dh by its two parts) bound the sums; the
+    rho_dh terms cancel for most particles of a random set; the wcount_dh
+    terms never change sign (d/dH (H^3 W) = -(sigma/H) q w'(q) >= 0), so
+    past its self term the scale is the sum itself; and a lone particle's
+    scales are its self terms in closed form, 3 m sigma / H^4 and
+    (4 pi / 3) 6 sigma / H, while its wcount_dh is 0."""
     f = _random_box(400, seed=71)
     P = oracle.params()
     out = oracle.chain(f, P)
     s_rho, s_w = oracle.dh_scales(f, P)
+    H = oracle.KERNEL_GAMMA * f["h"].astype(np.float64)
+    sigma = 8.0 / math.pi
+    self_w = 4 * math.pi / 3 * 6 * sigma / H
     assert np.all(np.abs(out["rho_dh"]) <= s_rho * (1 + 1e-12))
-    # the terms cancel for most particles of a random set
     assert np.median(s_rho / np.abs(out["rho_dh"])) > 1.1
-    np.testing.assert_allclose(s_w, np.abs(out["wcount_dh"]), rtol=1e-10)
+    np.testing.assert_allclose(s_w - self_w, np.abs(out["wcount_dh"]), rtol=1e-9,
+                               atol=1e-12 * self_w.max())
     g = ics.empty_fields(2)
-    g["x"][:] = [[0.5, 0.5, 0.5], [0.52, 0.5, 0.5]]
+    g["x"][:] = [[0.2, 0.5, 0.5], [0.7, 0.5, 0.5]]     # 0.5 apart: no neighbour
     g["mass"][:] = 0.25
-    g["h"][:] = 0.05                          # H = 0.091 > 2 x 0.02
+    g["h"][:] = 0.0625
     g["u"][:] = 1.0
-    two = oracle.chain(g, P)
+    lone = oracle.chain(g, P)
     s2, w2 = oracle.dh_scales(g, P)
-    np.testing.assert_allclose(s2, np.abs(two["rho_dh"]), rtol=1e-13)
-    np.testing.assert_allclose(w2, np.abs(two["wcount_dh"]), rtol=1e-13)
+    H1 = oracle.KERNEL_GAMMA * 0.0625
+    np.testing.assert_allclose(s2, 3 * 0.25 * sigma / H1 ** 4, rtol=1e-14)
+    np.testing.assert_allclose(w2, 4 * math.pi / 3 * 6 * sigma / H1, rtol=1e-14)
+    assert np.all(np.abs(lone["wcount_dh"]) <= 1e-12 * w2)
