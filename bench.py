@@ -158,7 +158,9 @@ class ClockSampler:
                 except (ValueError, IndexError):
                     continue
         threading.Thread(target=reader, daemon=True).start()
-        time.sleep(0.5)                       # NVML up before the first region
+        t_end = time.time() + 20.0            # NVML up before the first region
+        while not samples and time.time() < t_end and proc.poll() is None:
+            time.sleep(0.05)
         return proc, samples, info
 
     def start(self):
@@ -328,9 +330,11 @@ def oracle_sample(f, nsample: int, seed: int):
     return pairs, dt
 
 
-def precision_study(off, f, sel, ref, steps, mixed_step):
-    """Per-loop error of the mixed-precision and the all-FP64 batched paths
-    against the oracle on the sampled particles, and the FP64 step time."""
+def precision_study(off, f, sel, ref, steps, mixed_step, x64_step=None):
+    """Per-loop error of the mixed-precision path (FP32, two-float and
+    fixed-point separations), of the FP64-separation arm (FP32 fields, FP64
+    pair separations; list pipeline) and of the all-FP64 batched path against
+    the oracle on the sampled particles, with the step times of the last two."""
     import torch
     import oracle
     from oracle import compare
@@ -342,6 +346,22 @@ def precision_study(off, f, sel, ref, steps, mixed_step):
     res["mixed"] = {"per_loop": compare.per_loop(e), "fields": e,
                     "rho_dh": compare.relative_distribution(got["rho_dh"][sel], ref["rho_dh"],
                                                             sc[0])}
+    if x64_step is not None:
+        x64_step()                                    # warm-up (allocates the lanes)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            x64_step()
+        e1.record()
+        torch.cuda.synchronize()
+        res["fp64_separation_ms_per_step"] = e0.elapsed_time(e1) / steps
+        got = off.export()
+        e = compare.errors({k: v[sel] for k, v in got.items()}, ref, sc)
+        res["fp64_separation"] = {"per_loop": compare.per_loop(e), "fields": e}
+        off.x64 = None
+        torch.cuda.empty_cache()
     off.fp64_step()                                   # warm-up (allocates buffers)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -975,6 +995,7 @@ def run_ours(args, ws, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
+    ClockSampler(local)                       # the sampling process, started early
     mpeaks = measured_peaks()
     peaks = measure_peaks(local) if args.peaks else {}
     link = measure_link() if args.host_steps > 0 else None
@@ -1144,7 +1165,8 @@ def run_ours(args, ws, rank, local):
         sel, ref = oracle_sample.last
         precision = precision_study(off, f, sel, ref, args.precision_steps,
                                     off.list_step if args.head_pipeline == "list"
-                                    else off.batch_step)
+                                    else off.batch_step,
+                                    off.list_step_x64 if args.head_pipeline == "list" else None)
         precision["mixed_ms_per_step"] = ms_step
     cfg_vals = {"tasks": base.info["ntasks"], "bundles": base.info["nbundles"],
                 "bbundles": base.binfo["nbundles"],

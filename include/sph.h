@@ -540,6 +540,10 @@ int sph_tree_plan(int64_t n, const double *host_x, const float *host_h,
 /* info[0] plan kind (0 grid, 1 tree), [1] cells or leaves with particles,
  * [2] largest cell / leaf population, [3] neighbour entries (all cells). */
 int sph_batch_plan_info(sph_batch b, int64_t info[4]);
+/* The cells one bundle packs, in pack order (host-side copy): *ncells gets
+ * their count and, when cells is non-NULL, cells gets three int32 per cell:
+ * its first store particle, its particle count and its first bundle slot. */
+int sph_batch_cells(sph_batch b, int bundle, int32_t *cells, int64_t *ncells);
 /* 1 when the plan's list build decides pairs on 32-bit fixed-point
  * separations (every cell or leaf extent plus the largest support is below
  * half the box, so minimum images are unambiguous), 0 when it uses two-float
@@ -627,6 +631,22 @@ int sph_batch_offload_loop_host(sph_store s, sph_batch b, int loop, void *const 
                                 void *const host_out[2], void *const dev_in[2],
                                 void *const dev_out[2], const sph_params *p,
                                 void *const streams[2], int nthreads);
+
+/* Precision study (the paper fixes no precision; this is the arrangement
+ * that keeps FP64 only where cancellation bites): the list step of
+ * sph_batch_offload_step_list with every pair separation in the three loops
+ * taken as the difference of the two FP64 positions, its periodic image
+ * chosen in FP64, then rounded to FP32; the fields, the pair bodies, the
+ * compensated density sum and the lists (decided as in the list step) are
+ * unchanged.  dev_x64: caller device memory of sph_batch_x64_bytes(b) bytes,
+ * 256-byte aligned, where each pack's slots get their FP64 positions.
+ * Slower than the list step: the B300's FP64 pipe runs a small fraction of
+ * its FP32 rate. */
+size_t sph_batch_x64_bytes(sph_batch b);
+int sph_batch_offload_step_list_x64(sph_store s, sph_batch b, void *dev_buf_in,
+                                    void *dev_buf_out, void *dev_list, size_t list_bytes,
+                                    void *dev_x64, size_t x64_bytes, const sph_params *p,
+                                    void *stream);
 
 /* ---- adjoint of density -> ghost -> force (differentiation) --------------
  * Gradient of L = sum_i |a_i|^2 + sum_i (du_i/dt)^2 (active particles) with

@@ -8,8 +8,10 @@ sums, ghost update, force sums; h, v and the switches' coefficients held
 fixed) with whatever upstream adjoints of a and du/dt the loss passes, as
 gradients with respect to x, m and u.  Outputs of inactive particles are
 constants of the step (their adjoints are dropped).  The backward reads the
-state the forward left in the Offload: run it before the next forward on the
-same Offload.
+state the forward left in the store (densities, the ghost's fields): run it
+before the next forward on the same Offload.  The pair lists are not kept
+for it: the backward rebuilds them from the store's positions and supports
+(one list build) before the adjoint kernels run.
 """
 from __future__ import annotations
 

@@ -261,6 +261,22 @@ int dispatch_bloop(sph_batch b, const BInteractArgs &a, const ListView &L, long 
     return dispatch_bloop_w<LOOP, kLLoopWarpsGrid>(b->threads, a, L, item0, st);
 }
 
+// The FP64-separation list loops of the precision study, at the grid
+// plan's residency.
+template <int LOOP>
+int dispatch_bloop64(sph_batch b, const BInteractArgs &a, const ListView &L, long long item0,
+                     cudaStream_t st) {
+    constexpr int W = kLLoopWarpsGrid;
+    if (b->threads == 64)
+        return launch_persistent(k_bloop<LOOP, 64, W, true>, 64, a.nitems, st, "list loop (FP64 "
+                                 "separations)", a, L, item0);
+    if (b->threads == 256)
+        return launch_persistent(k_bloop<LOOP, 256, W, true>, 256, a.nitems, st, "list loop "
+                                 "(FP64 separations)", a, L, item0);
+    return launch_persistent(k_bloop<LOOP, 128, W, true>, 128, a.nitems, st, "list loop (FP64 "
+                             "separations)", a, L, item0);
+}
+
 template <bool FIXED>
 inline int dispatch_blist_p(int threads, const BInteractArgs &a, const ListView &L,
                             long long item0, cudaStream_t st) {
@@ -1392,6 +1408,21 @@ int sph_batch_list_fixed(sph_batch b) {
     return b->fixed_build ? 1 : 0;
 }
 
+int sph_batch_cells(sph_batch b, int bundle, int32_t *cells, int64_t *ncells) {
+    if (int rc = check_batch(b, bundle)) return rc;
+    if (!ncells) return fail(SPH_EINVAL, "NULL argument");
+    const BatchBundle &bb = b->bundles[bundle];
+    *ncells = bb.ncells;
+    if (!cells) return SPH_OK;
+    for (int64_t c = 0; c < bb.ncells; ++c) {
+        const BCellDev &cd = b->cells[bb.cell0 + c];
+        cells[3 * c + 0] = cd.p0;
+        cells[3 * c + 1] = cd.n;
+        cells[3 * c + 2] = cd.slot;
+    }
+    return SPH_OK;
+}
+
 int sph_batch_plan_info(sph_batch b, int64_t info[4]) {
     if (!b || !info) return fail(SPH_EINVAL, "NULL argument");
     info[0] = b->kind;
@@ -1469,18 +1500,33 @@ static int batch_pack(sph_store s, sph_batch b, int loop, int bundle, void *dev_
     a.delta = (float)(4e-6 * bmax);
     if (bb.ncells == 0) return SPH_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const unsigned g = (unsigned)bb.ncells;
-    // one CTA per cell; 64 threads suit cells of a few dozen particles
-    // (measured against 128: faster on the uniform and the clustered sets)
+    a.ncells = (int)bb.ncells;
+    a.min_n = kWPack + 1;
+    // cells of up to kWPack particles: one warp each (k_bpack_w); larger ones:
+    // one 64-thread CTA each (k_bpack), launched only when the plan has them
+    const unsigned gw = (unsigned)((bb.ncells + 3) / 4), g = (unsigned)bb.ncells;
+    const bool big = b->plan_max_cell > kWPack;
     // the list loops' density pack writes only the fixed-point lanes where the
     // list build reads nothing else (plans on the fixed-point path)
-    if (loop == SPH_DENSITY && compact && b->fixed_build)
-        k_bpack<SPH_DENSITY, true><<<g, 64, 0, st>>>(a);
-    else if (loop == SPH_DENSITY) k_bpack<SPH_DENSITY><<<g, 64, 0, st>>>(a);
-    else if (loop == SPH_GRADIENT && compact) k_bpack<SPH_GRADIENT, true><<<g, 64, 0, st>>>(a);
-    else if (loop == SPH_GRADIENT) k_bpack<SPH_GRADIENT><<<g, 64, 0, st>>>(a);
-    else if (compact) k_bpack<SPH_FORCE, true><<<g, 64, 0, st>>>(a);
-    else k_bpack<SPH_FORCE><<<g, 64, 0, st>>>(a);
+    if (loop == SPH_DENSITY && compact && b->fixed_build) {
+        k_bpack_w<SPH_DENSITY, true><<<gw, 128, 0, st>>>(a);
+        if (big) k_bpack<SPH_DENSITY, true><<<g, 64, 0, st>>>(a);
+    } else if (loop == SPH_DENSITY) {
+        k_bpack_w<SPH_DENSITY><<<gw, 128, 0, st>>>(a);
+        if (big) k_bpack<SPH_DENSITY><<<g, 64, 0, st>>>(a);
+    } else if (loop == SPH_GRADIENT && compact) {
+        k_bpack_w<SPH_GRADIENT, true><<<gw, 128, 0, st>>>(a);
+        if (big) k_bpack<SPH_GRADIENT, true><<<g, 64, 0, st>>>(a);
+    } else if (loop == SPH_GRADIENT) {
+        k_bpack_w<SPH_GRADIENT><<<gw, 128, 0, st>>>(a);
+        if (big) k_bpack<SPH_GRADIENT><<<g, 64, 0, st>>>(a);
+    } else if (compact) {
+        k_bpack_w<SPH_FORCE, true><<<gw, 128, 0, st>>>(a);
+        if (big) k_bpack<SPH_FORCE, true><<<g, 64, 0, st>>>(a);
+    } else {
+        k_bpack_w<SPH_FORCE><<<gw, 128, 0, st>>>(a);
+        if (big) k_bpack<SPH_FORCE><<<g, 64, 0, st>>>(a);
+    }
     return launch_check("batch pack");
 }
 
@@ -1858,6 +1904,77 @@ int sph_batch_list_status(const void *dev_list, int64_t *chunks_needed, int *ove
         return rc;
     *chunks_needed = (int64_t)h.chunks_used;
     *overflow = (int)h.overflow;
+    return SPH_OK;
+}
+
+size_t sph_batch_x64_bytes(sph_batch b) {
+    if (!b) return 0;
+    return 3 * (size_t)((8 * b->max_slots + 255) / 256 * 256);
+}
+
+int sph_batch_offload_step_list_x64(sph_store s, sph_batch b, void *dev_buf_in,
+                                    void *dev_buf_out, void *dev_list, size_t list_bytes,
+                                    void *dev_x64, size_t x64_bytes, const sph_params *p,
+                                    void *stream) {
+    if (int rc = check_store(s)) return rc;
+    if (!b) return fail(SPH_EINVAL, "NULL batch handle");
+    if (int rc = check_params(p)) return rc;
+    if (s->n != b->n) return fail(SPH_EINVAL, "store and batch disagree on particle count");
+    if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_buf_out || !aligned256(dev_buf_out) ||
+        !dev_list || !aligned256(dev_list) || !dev_x64 || !aligned256(dev_x64))
+        return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
+    if (x64_bytes < sph_batch_x64_bytes(b))
+        return fail(SPH_EINVAL, "FP64 position buffer holds %zu bytes, needs %zu", x64_bytes,
+                    sph_batch_x64_bytes(b));
+    const int64_t NI = (int64_t)b->items.size();
+    if ((int64_t)list_bytes < ListLayout::fixed(NI) + 512)
+        return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (int rc = cuda_check(cudaMemsetAsync(dev_list, 0, sizeof(ListHdr), st),
+                            "reset list header"))
+        return rc;
+    const size_t lane = (size_t)((8 * b->max_slots + 255) / 256 * 256);
+    double *xd[3] = {(double *)dev_x64, (double *)((char *)dev_x64 + lane),
+                     (double *)((char *)dev_x64 + 2 * lane)};
+    const CompPtr x0 = at(s, F_X, 0), x1 = at(s, F_X, 1), x2 = at(s, F_X, 2);
+    ListView L = ListLayout::view(dev_list, NI, (int64_t)list_bytes);
+    for (int loop = 0; loop < 3; ++loop)
+        for (int k = 0; k < (int)b->bundles.size(); ++k) {
+            const BatchBundle &bb = b->bundles[k];
+            if (int rc = sph_batch_pack_list(s, b, loop, k, dev_buf_in, p, stream)) return rc;
+            if (bb.slots > 0) {
+                const int64_t S = bb.slots;
+                const int64_t perm_off = loop == SPH_DENSITY ? BLayout<SPH_DENSITY>::perm(S)
+                                         : loop == SPH_GRADIENT ? BLayout<SPH_GRADIENT>::perm(S)
+                                                                : BLayout<SPH_FORCE>::perm(S);
+                k_pack_x64<<<grid_for(S, 256), 256, 0, st>>>(
+                    (const int32_t *)((const char *)dev_buf_in + perm_off), S, x0, x1, x2, xd[0],
+                    xd[1], xd[2]);
+                if (int rc = launch_check("FP64 positions")) return rc;
+            }
+            if (loop == SPH_DENSITY)
+                if (int rc = sph_batch_list_build_bundle(s, b, k, dev_buf_in, dev_list,
+                                                         list_bytes, p, stream))
+                    return rc;
+            if (bb.nitems > 0) {
+                BInteractArgs a = interact_args(b, k, dev_buf_in, dev_buf_out, p);
+                for (int d = 0; d < 3; ++d) {
+                    a.xd[d] = xd[d];
+                    a.box_d[d] = b->box[d];
+                    a.half_d[d] = 0.5 * b->box[d];
+                }
+                if (int rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st),
+                                        "reset work queue"))
+                    return rc;
+                int rc = loop == SPH_DENSITY    ? dispatch_bloop64<SPH_DENSITY>(b, a, L, bb.item0, st)
+                         : loop == SPH_GRADIENT ? dispatch_bloop64<SPH_GRADIENT>(b, a, L, bb.item0, st)
+                                                : dispatch_bloop64<SPH_FORCE>(b, a, L, bb.item0, st);
+                if (rc) return rc;
+            }
+            if (int rc = sph_batch_unpack_write(s, b, loop, k, dev_buf_out, dev_buf_in, p,
+                                                loop == SPH_DENSITY ? 1 : 0, stream))
+                return rc;
+        }
     return SPH_OK;
 }
 

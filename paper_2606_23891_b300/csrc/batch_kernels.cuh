@@ -54,6 +54,8 @@ struct BPackArgs {
     const BCellDev *cells;
     char *buf;
     long long S;
+    int ncells;           // cells of the bundle
+    int min_n;            // k_bpack: cells with fewer particles are left to k_bpack_w
     double fx_scale[3];   // 2^32 / box edge: fixed-point position units
     CompPtr src[R_NUM];
     float kernel_gamma, gamma, delta;
@@ -162,6 +164,7 @@ __global__ void __launch_bounds__(128) k_bpack(BPackArgs a) {
     __shared__ float hred[4];
     __shared__ int hist[8 * kChunksMax];
     const BCellDev C = a.cells[blockIdx.x];
+    if (C.n < a.min_n) return;   // a small cell: k_bpack_w packs it
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned int lt = (1u << lane) - 1u;
     const bool sort = C.n <= kBSortMax && C.n > 32;
@@ -299,6 +302,10 @@ struct BInteractArgs {
     float fx_unit[3];                 // box edge / 2^32: one fixed-point position unit
     int active_bin;
     PhysArgs pa;  // parameters the pair bodies read (beta)
+    // the FP64-separation list loops (precision study): each slot's position
+    // in FP64 (three lanes), the box and half of it
+    const double *xd[3];
+    double box_d[3], half_d[3];
 };
 
 // a + b for two-float a and b (Knuth's TwoSum on the high parts); exact to
@@ -320,6 +327,139 @@ constexpr int kWTile = 64;  // j records a warp stages at a time (2 mask words)
 #ifndef SPH_BMINB_FORCE
 #define SPH_BMINB_FORCE 1024
 #endif
+// Warp-per-cell pack of the cells of at most kWPack particles: the records
+// and slot order of k_bpack (the same bounding box, octant keys and stable
+// counting order, so the same bits), with each particle's position loaded and
+// split once and kept in registers, the octant ranks taken from ballots
+// (per-row key counts packed bytewise in one 64-bit word, their prefix sums
+// by one multiplication), and each record written by the lane of its slot,
+// so consecutive lanes store consecutive slots.  Four cells per 128-thread
+// CTA and no block barrier; larger cells are left to k_bpack.
+constexpr int kWPack = 128;
+constexpr int kWRows = kWPack / 32;
+
+template <int LOOP, bool COMPACT = false>
+__global__ void __launch_bounds__(128) k_bpack_w(BPackArgs a) {
+    using BL = BLayout<LOOP>;
+    constexpr int nf = COMPACT ? NFC<LOOP>::value : BL::nf;
+    __shared__ unsigned char inv_s[4][kWPack];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cell = blockIdx.x * 4 + warp;
+    if (cell >= a.ncells) return;
+    const BCellDev C = a.cells[cell];
+    if (C.n > kWPack || C.n <= 0) return;
+    const unsigned int lt = (1u << lane) - 1u;
+    const int rows = (C.n + 31) >> 5;
+    // positions (hi parts) and the largest support; bounding box
+    float hx[kWRows][3];
+    float mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float hmax = 0.f;
+#pragma unroll
+    for (int r = 0; r < kWRows; ++r) {
+        const int k = r * 32 + lane;
+        hx[r][0] = hx[r][1] = hx[r][2] = 0.f;
+        if (r < rows && k < C.n) {
+            const long long p = (long long)C.p0 + k;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                float lo;
+                split_f64(ld<double>(a.src[R_X0 + d], p), hx[r][d], lo);
+                mn[d] = fminf(mn[d], hx[r][d]);
+                mx[d] = fmaxf(mx[d], hx[r][d]);
+            }
+            hmax = fmaxf(hmax, a.kernel_gamma * ld<float>(a.src[R_H], p));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = fminf(mn[d], __shfl_xor_sync(0xffffffffu, mn[d], o));
+            mx[d] = fmaxf(mx[d], __shfl_xor_sync(0xffffffffu, mx[d], o));
+        }
+        hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+    }
+    if (lane == 0) {
+        reinterpret_cast<float *>(a.buf + BL::cellh(a.S))[cell] = hmax;
+        // a support beyond what the plan was built for (see k_bpack)
+        if (hmax > C.hlim) atomicOr(&g_error_word, 8u);
+    }
+    // slot of each particle: stable counting order by octant key
+    int pos[kWRows];
+    if (C.n > 32) {
+        float ctr[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) ctr[d] = 0.5f * (mn[d] + mx[d]);
+        int key[kWRows];
+        unsigned long long cnt[kWRows], total = 0ull;
+#pragma unroll
+        for (int r = 0; r < kWRows; ++r) {
+            key[r] = 8;
+            cnt[r] = 0ull;
+            if (r < rows) {
+                if (r * 32 + lane < C.n)
+                    key[r] = (hx[r][0] > ctr[0] ? 1 : 0) | (hx[r][1] > ctr[1] ? 2 : 0) |
+                             (hx[r][2] > ctr[2] ? 4 : 0);
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    cnt[r] |= (unsigned long long)__popc(__ballot_sync(0xffffffffu, key[r] == q))
+                              << (8 * q);
+            }
+            total += cnt[r];
+        }
+        // bytewise exclusive prefix over keys (every partial sum <= 128)
+        const unsigned long long excl = total * 0x0101010101010101ull - total;
+        unsigned long long before = 0ull;   // earlier rows' counts per key
+#pragma unroll
+        for (int r = 0; r < kWRows; ++r) {
+            pos[r] = 0;
+            if (r < rows) {
+                const unsigned int peers = __match_any_sync(0xffffffffu, key[r]);
+                if (key[r] < 8)
+                    pos[r] = (int)((excl >> (8 * key[r])) & 0xffull) +
+                             (int)((before >> (8 * key[r])) & 0xffull) + __popc(peers & lt);
+            }
+            before += cnt[r];
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < kWRows; ++r) pos[r] = r * 32 + lane;
+    }
+#pragma unroll
+    for (int r = 0; r < kWRows; ++r)
+        if (r < rows && r * 32 + lane < C.n) inv_s[warp][pos[r]] = (unsigned char)(r * 32 + lane);
+    __syncwarp();
+    // records in slot order
+#pragma unroll 1
+    for (int r = 0; r < rows; ++r) {
+        const int j = r * 32 + lane;
+        if (j >= C.n) continue;
+        const long long p = (long long)C.p0 + inv_s[warp][j];
+        float4 rec[BL::nf];
+        float hf;
+        make_record<LOOP, COMPACT>(a, p, rec, hf);
+        const long long sl = checked((long long)C.slot + j, a.S);
+#pragma unroll
+        for (int f = 0; f < nf; ++f)
+            reinterpret_cast<float4 *>(a.buf + BL::rec(f, a.S))[sl] = rec[f];
+        reinterpret_cast<int32_t *>(a.buf + BL::perm(a.S))[sl] = (int32_t)p;
+        if (LOOP == SPH_DENSITY) {
+            float X[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                X[d] = fixed_coord(ld<double>(a.src[R_X0 + d], p), a.fx_scale[d]);
+            reinterpret_cast<float4 *>(a.buf + BL::fx(0, a.S))[sl] =
+                make_float4(X[0], X[1], X[2], rec[0].w);
+            reinterpret_cast<float4 *>(a.buf + BL::fx(1, a.S))[sl] =
+                make_float4(rec[2].x, rec[2].y, rec[2].z, rec[1].w);
+        }
+        if (LOOP == SPH_FORCE) {
+            reinterpret_cast<int8_t *>(a.buf + BL::tb(a.S))[sl] = ld<int8_t>(a.src[R_TB], p);
+            reinterpret_cast<float *>(a.buf + BL::hf(a.S))[sl] = hf;
+        }
+    }
+}
+
 template <int LOOP, int T>
 __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? SPH_BMINB_FORCE : 1024) / T)
     k_binteract(BInteractArgs a) {

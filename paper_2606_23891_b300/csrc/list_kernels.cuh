@@ -464,7 +464,18 @@ struct AccL<SPH_FORCE> {
 // lengths differ more, 48 warps hide more (step 133.5 against 135.7 ms).  So
 // grid plans use 28 and tree plans 48.
 constexpr int kLLoopWarpsGrid = 28, kLLoopWarpsTree = 48;
-template <int LOOP, int T, int WARPS>
+// SEP64 (the precision study of FP64 separations): every pair separation is
+// the difference of the two FP64 positions (a.xd, gathered per slot by
+// k_pack_x64), its periodic image chosen in FP64, then rounded to FP32; the
+// rest of each pair body is unchanged.
+__device__ __forceinline__ float sep64(double xi, double xj, double box, double half) {
+    double d = xi - xj;
+    if (d > half) d -= box;
+    else if (d < -half) d += box;
+    return (float)d;
+}
+
+template <int LOOP, int T, int WARPS, bool SEP64 = false>
 __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
     k_bloop(BInteractArgs a, ListView L, long long item0) {
     using BL = BLayout<LOOP>;
@@ -499,6 +510,10 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
         const long long slot = (long long)C.slot + i;
         float4 own[nf];
         float ox = 0.f, oy = 0.f, oz = 0.f;  // own fixed-point position (density, gradient)
+        double xi[3] = {0.0, 0.0, 0.0};      // SEP64: own FP64 position
+        if constexpr (SEP64)
+            if (valid)
+                for (int d = 0; d < 3; ++d) xi[d] = a.xd[d][checked(slot, a.S)];
         AccL<LOOP> acc;
         bool active = false;
         if (valid) {
@@ -551,7 +566,14 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
 #pragma unroll
             for (int f = 0; f < nf; ++f) o[f] = __ldg(&rec[f][checked(e & 0x7fffffffu, a.S)]);
         };
-        auto pair = [&](float4 *oth) {
+        auto pair = [&](float4 *oth, long long js) {
+            if constexpr (SEP64) {
+                const float dx = sep64(xi[0], a.xd[0][js], a.box_d[0], a.half_d[0]);
+                const float dy = sep64(xi[1], a.xd[1][js], a.box_d[1], a.half_d[1]);
+                const float dz = sep64(xi[2], a.xd[2][js], a.box_d[2], a.half_d[2]);
+                acc.body(own, oth, dx, dy, dz, dx * dx + dy * dy + dz * dz, a.pa);
+                return;
+            }
             // periodic image: the hi-part separation exceeds half the box
             const float ax = own[0].x - oth[0].x, ay = own[0].y - oth[0].y,
                         az = own[0].z - oth[0].z;
@@ -579,6 +601,7 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
             float4 nxt[nf];
             bool un = uses(e, 0);
             if (un) gather(nxt, e);
+            long long jn = e & 0x7fffffffu;
             e = next_ent();
 #pragma unroll 1
             for (int k = 0; k < maxc; ++k) {
@@ -586,10 +609,12 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
 #pragma unroll
                 for (int f = 0; f < nf; ++f) oth[f] = nxt[f];
                 const bool u = un;
+                const long long jc = jn;
                 un = uses(e, k + 1);
                 if (un) gather(nxt, e);
+                jn = e & 0x7fffffffu;
                 e = next_ent();
-                if (u) pair(oth);
+                if (u) pair(oth, checked(jc, a.S));
             }
         } else {
             // density and gradient: two gathered lanes per pair; the
@@ -602,10 +627,19 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
                 e = next_ent();
                 if (!uses(cur, k)) continue;
                 const long long js = checked(cur & 0x7fffffffu, a.S);
-                const float4 j0 = __ldg(&g0[js]), j1 = __ldg(&g1[js]);
-                const float dx = fixed_sep(ox, j0.x, a.fx_unit[0]);
-                const float dy = fixed_sep(oy, j0.y, a.fx_unit[1]);
-                const float dz = fixed_sep(oz, j0.z, a.fx_unit[2]);
+                const float4 j0 = (SEP64 && LOOP == SPH_DENSITY) ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                                                 : __ldg(&g0[js]);
+                const float4 j1 = __ldg(&g1[js]);
+                float dx, dy, dz;
+                if constexpr (SEP64) {
+                    dx = sep64(xi[0], a.xd[0][js], a.box_d[0], a.half_d[0]);
+                    dy = sep64(xi[1], a.xd[1][js], a.box_d[1], a.half_d[1]);
+                    dz = sep64(xi[2], a.xd[2][js], a.box_d[2], a.half_d[2]);
+                } else {
+                    dx = fixed_sep(ox, j0.x, a.fx_unit[0]);
+                    dy = fixed_sep(oy, j0.y, a.fx_unit[1]);
+                    dz = fixed_sep(oz, j0.z, a.fx_unit[2]);
+                }
                 float4 oth[nf];
                 oth[0] = make_float4(0.f, 0.f, 0.f, 0.f);
                 // m_j (density: fx1.w) or m_j / rho_j (gradient: record 0 .w)
@@ -632,6 +666,20 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
                 reinterpret_cast<float2 *>(a.out + BL::r256(a.S * 16))[slot] = o1;
             }
         }
+    }
+}
+
+// The FP64 positions of a bundle's slots for the SEP64 loops: slot sl
+// holds store particle perm[sl] (the pack's store-index lane).
+__global__ void __launch_bounds__(256) k_pack_x64(const int32_t *perm, long long S, CompPtr x0,
+                                                  CompPtr x1, CompPtr x2, double *xd0, double *xd1,
+                                                  double *xd2) {
+    for (long long sl = (long long)blockIdx.x * blockDim.x + threadIdx.x; sl < S;
+         sl += (long long)gridDim.x * blockDim.x) {
+        const long long p = perm[sl];
+        xd0[sl] = ld<double>(x0, p);
+        xd1[sl] = ld<double>(x1, p);
+        xd2[sl] = ld<double>(x2, p);
     }
 }
 

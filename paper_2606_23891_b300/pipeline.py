@@ -140,13 +140,21 @@ class Offload:
                              self.stream)
         return dev
 
-    def adjoint(self, abar, ebar):
+    def adjoint(self, abar, ebar, recompute_lists: bool = True):
         """Gradient of sum |a|^2 + sum (du/dt)^2 through the last list step,
         for upstream adjoints abar (n, 3) and ebar (n,) on the device; returns
-        device tensors (dL/dx (n, 3) FP64, dL/dm (n,), dL/du (n,))."""
+        device tensors (dL/dx (n, 3) FP64, dL/dm (n,), dL/du (n,)).
+
+        The pair lists are recomputed from the store's positions and
+        supports before the backward (one list build), so the backward does
+        not depend on lists kept from the forward; the pool they are built
+        in is the Offload's own list buffer, reused rather than duplicated.
+        recompute_lists=False takes the lists the last step left instead."""
         need = sph.sph_batch_adjoint_bytes(self.bplan)
         if need == 0:
             raise sph.SphError(6, "the adjoint needs a plan of one bundle")
+        if recompute_lists or getattr(self, "blist", None) is None:
+            self.list_build()
         if getattr(self, "adj_scratch", None) is None or self.adj_scratch.numel() < need:
             self.adj_scratch = torch.empty(need, dtype=torch.uint8, device=self.device)
         abar = abar.to(self.device, torch.float32).contiguous()
@@ -360,6 +368,18 @@ class Offload:
                                         self.bbuf_out.data_ptr(), self.blist.data_ptr(),
                                         self.blist_bytes, self.params, self.stream)
 
+    def list_step_x64(self) -> None:
+        """The list step with FP64 pair separations (precision study)."""
+        if getattr(self, "blist", None) is None:
+            self.list_build()
+        need = sph.sph_batch_x64_bytes(self.bplan)
+        if getattr(self, "x64", None) is None or self.x64.numel() < need:
+            self.x64 = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+        sph.sph_batch_offload_step_list_x64(self.store, self.bplan, self.bbuf_in.data_ptr(),
+                                            self.bbuf_out.data_ptr(), self.blist.data_ptr(),
+                                            self.blist_bytes, self.x64.data_ptr(),
+                                            self.x64.numel(), self.params, self.stream)
+
     def resize(self) -> None:
         """Size the list pool again for the current positions (one
         synchronous build and status read)."""
@@ -368,6 +388,7 @@ class Offload:
 
     def close_batch(self) -> None:
         self.f64_in = self.f64_out = None
+        self.x64 = None
         self.blist = None
         if getattr(self, "bplan", None) is not None:
             if not getattr(self, "bshared", False):

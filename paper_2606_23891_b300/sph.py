@@ -138,6 +138,7 @@ def lib() -> C.CDLL:
         "sph_batch_buffer_bytes_fp64": (sz, [p, i]),
         "sph_batch_build_tree": (i, [i64, p, p, p, p, p, p]),
         "sph_batch_plan_info": (i, [p, p]),
+        "sph_batch_cells": (i, [p, i, p, p]),
         "sph_batch_list_bytes": (sz, [p, i64]),
         "sph_batch_list_build": (i, [p, p, p, p, sz, p, p]),
         "sph_batch_list_build_bundle": (i, [p, p, i, p, p, sz, p, p]),
@@ -148,6 +149,8 @@ def lib() -> C.CDLL:
         "sph_batch_offload_step_list": (i, [p, p, p, p, p, sz, p, p]),
         "sph_batch_list_interact": (i, [p, i, i, p, p, p, sz, p, p]),
         "sph_batch_adjoint_bytes": (sz, [p]),
+        "sph_batch_x64_bytes": (sz, [p]),
+        "sph_batch_offload_step_list_x64": (i, [p, p, p, p, p, sz, p, sz, p, p]),
         "sph_batch_offload_loop_host": (i, [p, p, i, p, p, p, p, p, p, i]),
         "sph_batch_adjoint": (i, [p, p, p, p, sz, p, sz, p, p, p, p, p, p, p, p]),
         "sph_tree_plan": (i, [i64, p, p, p, p, p, p, p, p, i64, p]),
@@ -484,6 +487,16 @@ def sph_batch_plan_info(b) -> dict:
     return dict(zip(("kind", "cells", "max_cell", "nbrs"), list(info)))
 
 
+def sph_batch_cells(b, bundle: int):
+    """(p0, n, slot) of every cell the bundle packs, an int32 array (ncells, 3)."""
+    import numpy as np
+    nc = C.c_int64()
+    _ok(lib().sph_batch_cells(b, bundle, None, C.byref(nc)))
+    out = np.empty((max(nc.value, 1), 3), np.int32)
+    _ok(lib().sph_batch_cells(b, bundle, out.ctypes.data, C.byref(nc)))
+    return out[:nc.value]
+
+
 def sph_batch_count_pairs(s, b, loop: int, dev_in: int, p: Params, dev_count: int,
                           stream: int = 0):
     _ok(lib().sph_batch_count_pairs(s, b, loop, dev_in, C.byref(p), dev_count, stream))
@@ -539,6 +552,17 @@ def sph_batch_offload_loop_host(s, b, loop: int, host_in, host_out, dev_in, dev_
     _ok(lib().sph_batch_offload_loop_host(s, b, loop, arr(*host_in), arr(*host_out),
                                           arr(*dev_in), arr(*dev_out), C.byref(p),
                                           arr(*streams), nthreads))
+
+
+def sph_batch_x64_bytes(b) -> int:
+    return lib().sph_batch_x64_bytes(b)
+
+
+def sph_batch_offload_step_list_x64(s, b, dev_in: int, dev_out: int, dev_list: int,
+                                    list_bytes: int, dev_x64: int, x64_bytes: int, p: Params,
+                                    stream: int = 0):
+    _ok(lib().sph_batch_offload_step_list_x64(s, b, dev_in, dev_out, dev_list, list_bytes,
+                                              dev_x64, x64_bytes, C.byref(p), stream))
 
 
 def sph_batch_adjoint_bytes(b) -> int:

@@ -347,8 +347,10 @@ def test_supports_beyond_the_plan_are_reported():
     grid.batch()
     grid.list_step()
     sph.sph_sync(grid.stream)
-    # 1% larger supports stay below the grid's cell edge: no report
+    # 1% larger supports stay below the grid's cell edge: no report (the
+    # list pool is sized again for the extra neighbours)
     grid.import_fields({"h": (f["h"] * np.float32(1.01)).astype(np.float32)}, ("h",))
+    grid.resize()
     grid.list_step()
     sph.sph_sync(grid.stream)
     big = f["h"].copy()
@@ -368,3 +370,28 @@ def test_supports_beyond_the_plan_are_reported():
     tree.list_step()
     with pytest.raises(sph.SphError, match="rebuild the plan"):
         sph.sph_sync(tree.stream)
+
+
+@pytest.mark.parametrize("case", ["gresho32", "ragged24", "lognormal24"])
+def test_fp64_separation_step_matches_the_oracle(case):
+    """The precision study's arm with FP64 pair separations (FP32 fields):
+    within the oracle bars, and within rounding of the list step."""
+    if case == "lognormal24":
+        f = ics.lognormal(n_side=24, seed=31)
+        off = Offload(f, layout="pack_force_type", plan="tree")
+    else:
+        f = PARITY_CASES[case]() if case in PARITY_CASES else ragged(24, 8)
+        off = Offload(f, layout="pack_force_type")
+        off.batch()
+    off.list_step_x64()
+    got = off.export()
+    check_physics(f, got)
+    off.list_step()
+    ref = off.export()
+    for k in ref:
+        assert rms_err(got[k], ref[k]) <= 1e-5, k
+    with pytest.raises(sph.SphError, match="needs"):
+        sph.sph_batch_offload_step_list_x64(off.store, off.bplan, off.bbuf_in.data_ptr(),
+                                            off.bbuf_out.data_ptr(), off.blist.data_ptr(),
+                                            off.blist_bytes, off.x64.data_ptr(), 256,
+                                            off.params, off.stream)
