@@ -99,20 +99,34 @@ def measured_peaks() -> dict:
 
 # ---------------------------------------------------------------- clocks --
 _SAMPLER = r"""
-import sys, time
-import pynvml
-pynvml.nvmlInit()
-uuid, index, period = sys.argv[1], int(sys.argv[2]), float(sys.argv[3])
-try:
-    h = pynvml.nvmlDeviceGetHandleByUUID(uuid)
-except Exception:
-    h = pynvml.nvmlDeviceGetHandleByIndex(index)
-print("max %f" % pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM), flush=True)
+import ctypes as C, sys, time
+ids, period = sys.argv[1:-1], float(sys.argv[-1])
+nv = C.CDLL("libnvidia-ml.so.1")
+if nv.nvmlInit_v2() != 0:
+    sys.exit("nvmlInit failed")
+h = C.c_void_p()
+ok = False
+for i in ids:
+    if i.startswith("pci:"):
+        ok = nv.nvmlDeviceGetHandleByPciBusId_v2(i[4:].encode(), C.byref(h)) == 0
+    else:
+        ok = nv.nvmlDeviceGetHandleByUUID(i.encode(), C.byref(h)) == 0
+    if ok:
+        break
+if not ok:
+    sys.exit("no NVML handle for %s" % ids)
+SM = 1
+mx = C.c_uint()
+nv.nvmlDeviceGetMaxClockInfo(h, SM, C.byref(mx))
+reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+    nv.nvmlDeviceGetCurrentClocksThrottleReasons
+print("max %d" % mx.value, flush=True)
+clk, rs = C.c_uint(), C.c_ulonglong()
 while True:
     t = time.time()
-    mhz = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
-    rs = pynvml.nvmlDeviceGetCurrentClocksEventReasons(h)
-    print("%.6f %d %d" % (t, mhz, rs), flush=True)
+    nv.nvmlDeviceGetClockInfo(h, SM, C.byref(clk))
+    reasons(h, C.byref(rs))
+    print("%.6f %d %d" % (t, clk.value, rs.value), flush=True)
     time.sleep(period)
 """
 
@@ -135,33 +149,75 @@ class ClockSampler:
         self.t0 = None
 
     @staticmethod
+    def _ids(index):
+        """NVML names of the CUDA device: its UUID (with and without the GPU-
+        prefix) and its PCI bus id (CUDA and NVML number devices differently)."""
+        import torch
+        pr = torch.cuda.get_device_properties(index)
+        ids = []
+        u = getattr(pr, "uuid", None)
+        if u is not None:
+            u = str(u)
+            ids += [u if u.startswith("GPU-") else "GPU-" + u, u]
+        try:
+            ids.append("pci:%08X:%02X:%02X.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id))
+        except AttributeError:
+            pass
+        return ids
+
+    @staticmethod
     def _launch(index, period):
         import threading
-        import torch
-        uuid = str(torch.cuda.get_device_properties(index).uuid)
-        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
-        samples, info = [], {"max": 0.0}
+        samples, info = [], {"max": 0.0, "source": "nvml"}
+        ids = ClockSampler._ids(index)
         try:
-            proc = subprocess.Popen([sys.executable, "-c", _SAMPLER, uuid, str(index), str(period)],
-                                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            proc = subprocess.Popen([sys.executable, "-c", _SAMPLER] + ids + [str(period)],
+                                    stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
         except OSError:
             return None, samples, info
 
-        def reader():
-            for line in proc.stdout:
-                parts = line.split()
+        def reader(p, parse):
+            for line in p.stdout:
                 try:
-                    if parts[0] == "max":
-                        info["max"] = float(parts[1])
-                    else:
-                        samples.append((float(parts[0]), float(parts[1]), int(parts[2])))
+                    parse(line)
                 except (ValueError, IndexError):
                     continue
-        threading.Thread(target=reader, daemon=True).start()
-        t_end = time.time() + 20.0            # NVML up before the first region
+
+        def parse_nvml(line):
+            parts = line.split()
+            if parts[0] == "max":
+                info["max"] = float(parts[1])
+            else:
+                samples.append((float(parts[0]), float(parts[1]), int(parts[2])))
+        threading.Thread(target=reader, args=(proc, parse_nvml), daemon=True).start()
+        t_end = time.time() + 20.0            # sampling before the first region
         while not samples and time.time() < t_end and proc.poll() is None:
             time.sleep(0.05)
-        return proc, samples, info
+        if samples:
+            return proc, samples, info
+        # NVML unavailable: nvidia-smi at its shortest loop, with timestamps
+        info["error"] = (proc.stderr.read() if proc.poll() is not None else "no sample")[-200:]
+        info["source"] = "nvidia-smi"
+        try:
+            smi = subprocess.Popen(
+                ["nvidia-smi", "-i", ids[0] if ids else str(index),
+                 "--query-gpu=timestamp,clocks.sm,clocks.max.sm,clocks_event_reasons.active",
+                 "--format=csv,noheader,nounits", "-lms", "20"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            return None, samples, info
+        import datetime
+
+        def parse_smi(line):
+            parts = [q.strip() for q in line.split(",")]
+            t = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            info["max"] = max(info["max"], float(parts[2]))
+            samples.append((t, float(parts[1]), int(parts[3], 16)))
+        threading.Thread(target=reader, args=(smi, parse_smi), daemon=True).start()
+        t_end = time.time() + 20.0
+        while not samples and time.time() < t_end and smi.poll() is None:
+            time.sleep(0.05)
+        return smi, samples, info
 
     def start(self):
         self.t0 = time.time()
@@ -178,7 +234,7 @@ class ClockSampler:
                          if any(r & bit for _, r in inside))
         return {"sm_mhz": statistics.median(m for m, _ in inside),
                 "sm_max_mhz": self.info["max"], "reasons": reasons, "samples": len(inside),
-                "region_s": round(t1 - self.t0, 3)}
+                "region_s": round(t1 - self.t0, 3), "source": self.info["source"]}
 
     @classmethod
     def close_all(cls):
@@ -1099,10 +1155,17 @@ def run_ours(args, ws, rank, local):
     stage, loop = top
     per_step = cnt[loop] / args.steps             # launches per step (bundles)
     dur = st[top] / cnt[loop]                     # ms per launch
-    fp32_peak = peaks.get("fp32_tflops") or FP32_PEAK_DERIVED
-    fp32_src = ("measured: sph_peak_run FP32 FMA at %.0f MHz" % peaks["clocks"]["sm_mhz"]
-                if peaks.get("fp32_tflops") and peaks.get("clocks")
-                else "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz")
+    # the measured FP32 peak, at the median SM clock of the headline's timed
+    # region (the FMA microbenchmark may run at a power-capped clock)
+    fp32_peak, fp32_src = FP32_PEAK_DERIVED, "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"
+    if peaks.get("fp32_tflops"):
+        fp32_peak, fp32_src = peaks["fp32_tflops"], "measured (sph_peak_run FP32 FMA)"
+        pc = peaks.get("clocks") or {}
+        if pc.get("sm_mhz") and cl and cl.get("sm_mhz"):
+            fp32_peak = peaks["fp32_tflops"] * cl["sm_mhz"] / pc["sm_mhz"]
+            fp32_src = ("measured (sph_peak_run FP32 FMA, %.4g TFLOP/s at %.0f MHz), scaled to "
+                        "the timed region's %.0f MHz" % (peaks["fp32_tflops"], pc["sm_mhz"],
+                                                         cl["sm_mhz"]))
     build_counts = None
     if args.head_pipeline == "list":
         build_counts = list_build_counts(off)
