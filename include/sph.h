@@ -584,6 +584,17 @@ int sph_batch_list_build_bundle(sph_store s, sph_batch b, int bundle, const void
                                 void *dev_list, size_t list_bytes, const sph_params *p,
                                 void *stream);
 int sph_batch_list_status(const void *dev_list, int64_t *chunks_needed, int *overflow);
+/* The list build tests each cell pair once where the plan allows it (one
+ * bundle whose targets are all its cells, the fixed-point path, a symmetric
+ * neighbour relation: grid plans of at least 5 cells per dimension): a
+ * first pass tests the target's own cell and the cells after it and keeps
+ * the hit masks of the latter in the list buffer (sph_batch_list_bytes
+ * counts them); a second pass gives each particle the pairs its cell's
+ * earlier neighbours found, by transposing their masks.  The lists hold the
+ * same pairs either way (in another order).  enable 0 / 1 turns it off / on
+ * for later builds, a negative value only asks; returns 1 when later builds
+ * of this plan use it, 0 when not, a negative status on error. */
+int sph_batch_list_symmetric(sph_batch b, int enable);
 /* Measurement variant of sph_batch_list_build_bundle (the paper has no
  * counterpart; it states the list build's work from what it tests): builds
  * the same lists and adds into dev_counts[0..4] (device uint64, 8-byte

@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(128, 4) k_adj_pairs(AdjArgs a) {
         if (un) {
 #pragma unroll
             for (int f = 0; f < kAdjRec; ++f)
-                nxt[f] = __ldg(&a.rec[kAdjRec * checked(e & 0x7fffffffu, a.S) + f]);
+                nxt[f] = __ldg(&a.rec[kAdjRec * checked(e, a.S) + f]);
         }
         e = next_ent();
 #pragma unroll 1
@@ -283,12 +283,12 @@ __global__ void __launch_bounds__(128, 4) k_adj_pairs(AdjArgs a) {
             if (un) {
 #pragma unroll
                 for (int f = 0; f < kAdjRec; ++f)
-                    nxt[f] = __ldg(&a.rec[kAdjRec * checked(e & 0x7fffffffu, a.S) + f]);
+                    nxt[f] = __ldg(&a.rec[kAdjRec * checked(e, a.S) + f]);
             }
             en = e;
             e = next_ent();
             if (!u) continue;
-            const long long js = (long long)(ent & 0x7fffffffu);
+            const long long js = (long long)ent;
             float dx, dy, dz;
             image_sep(own, oth, a, dx, dy, dz);
             const float r2 = dx * dx + dy * dy + dz * dz;
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(128, 4) k_adj_pairs(AdjArgs a) {
                 }
             } else {
                 float gd[3];
-                if (ent & 0x80000000u) {        // r < H_own: own's density term
+                if (r2 < own[0].w * own[0].w) {  // r < H_own: own's density term
                     density_back(own, gS, gR, oth, dx, dy, dz, r2, gd);
                     gx += gd[0]; gy += gd[1]; gz += gd[2];
                 }

@@ -291,9 +291,38 @@ inline int dispatch_blist_p(int threads, const BInteractArgs &a, const ListView 
                              none);
 }
 
-// The list build takes the fixed-point path where the plan allows it.
+// The list build takes the fixed-point path where the plan allows it, and
+// the symmetric build (two passes) where the plan holds its data.
+template <bool COUNT>
+int dispatch_blist_sym(int threads, const BInteractArgs &a, const ListView &L, long long item0,
+                       unsigned long long *cnt, cudaStream_t st) {
+    const char *w1 = "list build (symmetric, first pass)", *w2 = "list build (second pass)";
+    int rc;
+    if (threads == 64)
+        rc = launch_persistent(k_blist<64, true, COUNT, true>, 64, a.nitems, st, w1, a, L, item0,
+                               cnt);
+    else if (threads == 256)
+        rc = launch_persistent(k_blist<256, true, COUNT, true>, 256, a.nitems, st, w1, a, L,
+                               item0, cnt);
+    else
+        rc = launch_persistent(k_blist<128, true, COUNT, true>, 128, a.nitems, st, w1, a, L,
+                               item0, cnt);
+    if (rc) return rc;
+    if ((rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st),
+                         "reset work queue")))
+        return rc;
+    if (threads == 64)
+        return launch_persistent(k_blist_rev<64, COUNT>, 64, a.nitems, st, w2, a, L, item0, cnt);
+    if (threads == 256)
+        return launch_persistent(k_blist_rev<256, COUNT>, 256, a.nitems, st, w2, a, L, item0,
+                                 cnt);
+    return launch_persistent(k_blist_rev<128, COUNT>, 128, a.nitems, st, w2, a, L, item0, cnt);
+}
+
 inline int dispatch_blist(sph_batch b, const BInteractArgs &a, const ListView &L,
                           long long item0, cudaStream_t st) {
+    if (b->sym && b->sym_on)
+        return dispatch_blist_sym<false>(b->threads, a, L, item0, nullptr, st);
     if (b->fixed_build) return dispatch_blist_p<true>(b->threads, a, L, item0, st);
     return dispatch_blist_p<false>(b->threads, a, L, item0, st);
 }
@@ -1319,6 +1348,10 @@ static int check_batch(sph_batch b, int bundle) {
 }
 
 static void batch_free(sph_batch b) {
+    if (b->d_naux) cudaFree(b->d_naux);
+    if (b->d_mbase) cudaFree(b->d_mbase);
+    b->d_naux = nullptr;
+    b->d_mbase = nullptr;
     if (b->d_cells) cudaFree(b->d_cells);
     if (b->d_targets) cudaFree(b->d_targets);
     if (b->d_items) cudaFree(b->d_items);
@@ -1346,7 +1379,11 @@ static int batch_upload(sph_batch b, int rc, sph_batch *out) {
          (rc = up((void **)&b->d_items, b->items.data(), b->items.size() * sizeof(BItemDev),
                   "batch items")) ||
          (rc = up((void **)&b->d_counter, nullptr,
-                  (b->bundles.size() + 1) * sizeof(unsigned int), "batch counters")))) {
+                  (b->bundles.size() + 1) * sizeof(unsigned int), "batch counters")) ||
+         (b->sym && ((rc = up((void **)&b->d_naux, b->naux.data(),
+                              b->naux.size() * sizeof(int32_t), "symmetric list entries")) ||
+                     (rc = up((void **)&b->d_mbase, b->mbase.data(),
+                              b->mbase.size() * sizeof(long long), "symmetric list masks")))))) {
     }
     if (rc) {
         batch_free(b);
@@ -1406,6 +1443,12 @@ int sph_tree_plan(int64_t n, const double *host_x, const float *host_h,
 int sph_batch_list_fixed(sph_batch b) {
     if (!b) return -fail(SPH_EINVAL, "NULL batch handle");
     return b->fixed_build ? 1 : 0;
+}
+
+int sph_batch_list_symmetric(sph_batch b, int enable) {
+    if (!b) return -fail(SPH_EINVAL, "NULL batch handle");
+    if (enable >= 0) b->sym_on = enable != 0;
+    return b->sym && b->sym_on ? 1 : 0;
 }
 
 int sph_batch_cells(sph_batch b, int bundle, int32_t *cells, int64_t *ncells) {
@@ -1534,6 +1577,9 @@ static BInteractArgs interact_args(sph_batch b, int bundle, const void *dev_buf_
                                    void *dev_buf_out, const sph_params *p) {
     const BatchBundle &bb = b->bundles[bundle];
     BInteractArgs a{};
+    a.naux = b->d_naux;
+    a.mbase = b->d_mbase;
+    a.sym_words = b->sym_words;
     a.cells = b->d_cells + bb.cell0;
     a.targets = b->d_targets + bb.target0;
     a.nbrs = b->d_nbrs;
@@ -1810,7 +1856,7 @@ int sph_batch_count_pairs(sph_store s, sph_batch b, int loop, void *dev_buf_in,
 // ---- neighbour-list variant of the batched cycle ---------------------------
 size_t sph_batch_list_bytes(sph_batch b, int64_t chunks) {
     if (!b || chunks < 0) return 0;
-    return (size_t)ListLayout::bytes((int64_t)b->items.size(), chunks);
+    return (size_t)ListLayout::bytes((int64_t)b->items.size(), b->mask_words, chunks);
 }
 
 int sph_batch_list_build(sph_store s, sph_batch b, void *dev_buf_in, void *dev_list,
@@ -1822,7 +1868,7 @@ int sph_batch_list_build(sph_store s, sph_batch b, void *dev_buf_in, void *dev_l
     if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_list || !aligned256(dev_list))
         return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
     const int64_t NI = (int64_t)b->items.size();
-    if ((int64_t)list_bytes < ListLayout::fixed(NI) + 512)
+    if ((int64_t)list_bytes < ListLayout::fixed(NI, b->mask_words) + 512)
         return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
     // the header is reset here too, so a plan without bundles leaves it valid
     if (int rc = cuda_check(cudaMemsetAsync(dev_list, 0, sizeof(ListHdr), (cudaStream_t)stream),
@@ -1849,10 +1895,10 @@ int sph_batch_list_count(sph_store s, sph_batch b, int bundle, const void *dev_b
         return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers, the counts "
                                 "8-byte aligned");
     const int64_t NI = (int64_t)b->items.size();
-    if ((int64_t)list_bytes < ListLayout::fixed(NI) + 512)
+    if ((int64_t)list_bytes < ListLayout::fixed(NI, b->mask_words) + 512)
         return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
     cudaStream_t st = (cudaStream_t)stream;
-    ListView L = ListLayout::view(dev_list, NI, (int64_t)list_bytes);
+    ListView L = ListLayout::view(dev_list, NI, b->mask_words, (int64_t)list_bytes);
     if (bundle == 0)
         if (int rc = cuda_check(cudaMemsetAsync(L.hdr, 0, sizeof(ListHdr), st),
                                 "reset list header"))
@@ -1863,6 +1909,8 @@ int sph_batch_list_count(sph_store s, sph_batch b, int bundle, const void *dev_b
     if (int rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st),
                             "reset work queue"))
         return rc;
+    if (b->sym && b->sym_on)
+        return dispatch_blist_sym<true>(b->threads, a, L, bb.item0, dev_counts, st);
     if (b->fixed_build)
         return dispatch_blist_count_p<true>(b->threads, a, L, bb.item0, dev_counts, st);
     return dispatch_blist_count_p<false>(b->threads, a, L, bb.item0, dev_counts, st);
@@ -1879,10 +1927,10 @@ int sph_batch_list_build_bundle(sph_store s, sph_batch b, int bundle, const void
     if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_list || !aligned256(dev_list))
         return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
     const int64_t NI = (int64_t)b->items.size();
-    if ((int64_t)list_bytes < ListLayout::fixed(NI) + 512)
+    if ((int64_t)list_bytes < ListLayout::fixed(NI, b->mask_words) + 512)
         return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
     cudaStream_t st = (cudaStream_t)stream;
-    ListView L = ListLayout::view(dev_list, NI, (int64_t)list_bytes);
+    ListView L = ListLayout::view(dev_list, NI, b->mask_words, (int64_t)list_bytes);
     if (bundle == 0)
         if (int rc = cuda_check(cudaMemsetAsync(L.hdr, 0, sizeof(ListHdr), st),
                                 "reset list header"))
@@ -1927,7 +1975,7 @@ int sph_batch_offload_step_list_x64(sph_store s, sph_batch b, void *dev_buf_in,
         return fail(SPH_EINVAL, "FP64 position buffer holds %zu bytes, needs %zu", x64_bytes,
                     sph_batch_x64_bytes(b));
     const int64_t NI = (int64_t)b->items.size();
-    if ((int64_t)list_bytes < ListLayout::fixed(NI) + 512)
+    if ((int64_t)list_bytes < ListLayout::fixed(NI, b->mask_words) + 512)
         return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
     cudaStream_t st = (cudaStream_t)stream;
     if (int rc = cuda_check(cudaMemsetAsync(dev_list, 0, sizeof(ListHdr), st),
@@ -1937,7 +1985,7 @@ int sph_batch_offload_step_list_x64(sph_store s, sph_batch b, void *dev_buf_in,
     double *xd[3] = {(double *)dev_x64, (double *)((char *)dev_x64 + lane),
                      (double *)((char *)dev_x64 + 2 * lane)};
     const CompPtr x0 = at(s, F_X, 0), x1 = at(s, F_X, 1), x2 = at(s, F_X, 2);
-    ListView L = ListLayout::view(dev_list, NI, (int64_t)list_bytes);
+    ListView L = ListLayout::view(dev_list, NI, b->mask_words, (int64_t)list_bytes);
     for (int loop = 0; loop < 3; ++loop)
         for (int k = 0; k < (int)b->bundles.size(); ++k) {
             const BatchBundle &bb = b->bundles[k];
@@ -1989,12 +2037,12 @@ int sph_batch_list_interact(sph_batch b, int loop, int bundle, const void *dev_b
         !dev_list || !aligned256(dev_list))
         return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
     const int64_t NI = (int64_t)b->items.size();
-    if ((int64_t)list_bytes < ListLayout::fixed(NI) + 512)
+    if ((int64_t)list_bytes < ListLayout::fixed(NI, b->mask_words) + 512)
         return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
     const BatchBundle &bb = b->bundles[bundle];
     if (bb.nitems == 0) return SPH_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    ListView L = ListLayout::view(const_cast<void *>(dev_list), NI, (int64_t)list_bytes);
+    ListView L = ListLayout::view(const_cast<void *>(dev_list), NI, b->mask_words, (int64_t)list_bytes);
     BInteractArgs a = interact_args(b, bundle, dev_buf_in, dev_buf_out, p);
     if (int rc = cuda_check(cudaMemsetAsync(a.counter, 0, sizeof(unsigned int), st),
                             "reset work queue"))
@@ -2015,7 +2063,7 @@ int sph_batch_offload_loop_list(sph_store s, sph_batch b, int loop, void *dev_bu
     if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_buf_out || !aligned256(dev_buf_out) ||
         !dev_list || !aligned256(dev_list))
         return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
-    if ((int64_t)list_bytes < ListLayout::fixed((int64_t)b->items.size()) + 512)
+    if ((int64_t)list_bytes < ListLayout::fixed((int64_t)b->items.size(), b->mask_words) + 512)
         return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
     for (int k = 0; k < (int)b->bundles.size(); ++k) {
         if (int rc = sph_batch_pack_list(s, b, loop, k, dev_buf_in, p, stream)) return rc;
@@ -2039,7 +2087,7 @@ int sph_batch_offload_step_list(sph_store s, sph_batch b, void *dev_buf_in, void
     if (!dev_buf_in || !aligned256(dev_buf_in) || !dev_buf_out || !aligned256(dev_buf_out) ||
         !dev_list || !aligned256(dev_list))
         return fail(SPH_EINVAL, "buffers must be 256-byte aligned device pointers");
-    if ((int64_t)list_bytes < ListLayout::fixed((int64_t)b->items.size()) + 512)
+    if ((int64_t)list_bytes < ListLayout::fixed((int64_t)b->items.size(), b->mask_words) + 512)
         return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
     if (int rc = cuda_check(cudaMemsetAsync(dev_list, 0, sizeof(ListHdr), (cudaStream_t)stream),
                             "reset list header"))
@@ -2092,7 +2140,7 @@ int sph_batch_adjoint(sph_store s, sph_batch b, void *dev_buf_in, const void *de
     if (scratch_bytes < sph_batch_adjoint_bytes(b))
         return fail(SPH_EINVAL, "scratch smaller than sph_batch_adjoint_bytes");
     const int64_t NI = (int64_t)b->items.size();
-    if ((int64_t)list_bytes < ListLayout::fixed(NI) + 512)
+    if ((int64_t)list_bytes < ListLayout::fixed(NI, b->mask_words) + 512)
         return fail(SPH_EINVAL, "list buffer smaller than sph_batch_list_bytes(b, 0)");
     const BatchBundle &bb = b->bundles[0];
     if (bb.nitems == 0) return SPH_OK;
@@ -2106,7 +2154,7 @@ int sph_batch_adjoint(sph_store s, sph_batch b, void *dev_buf_in, const void *de
     a.counter = b->d_counter;
     a.nitems = (int)bb.nitems;
     a.item0 = bb.item0;
-    a.L = ListLayout::view(const_cast<void *>(dev_list), NI, (int64_t)list_bytes);
+    a.L = ListLayout::view(const_cast<void *>(dev_list), NI, b->mask_words, (int64_t)list_bytes);
     a.S = bb.slots;
     a.perm = reinterpret_cast<const int32_t *>((const char *)dev_buf_in +
                                                BLayout<SPH_DENSITY>::perm(bb.slots));

@@ -200,7 +200,78 @@ int build_batch(const sph_tasks_s *T, const sph_batch_params *bp, sph_batch_s *B
                 }
         G.nb_start.push_back((int64_t)G.nb_cell.size());
     }
-    return assemble(G, bp, B);
+    if (int rc = assemble(G, bp, B)) return rc;
+    build_sym(B);
+    return SPH_OK;
+}
+
+// The symmetric list build needs one bundle whose targets are all its cells
+// in order (every cell pair then has both cells' warps in the same launch),
+// the fixed-point path, and a neighbour relation that is symmetric: a target
+// never lists a cell twice, its self entry has no shift, and for every entry
+// A -> B (shift s) the entries of B hold B -> A with the opposite shift.
+// Grid plans (uniform cells) only: their masks are small (a tree plan's
+// larger leaves and more entries would make the mask traffic outweigh it).
+void build_sym(sph_batch_s *B) {
+    B->sym = false;
+    B->mask_words = 0;
+    B->naux.clear();
+    B->mbase.clear();
+    if (B->kind != 0 || !B->fixed_build || B->bundles.size() != 1) return;
+    const BatchBundle &bb = B->bundles[0];
+    const int64_t nt = bb.ntargets;
+    if (nt != bb.ncells) return;
+    for (int64_t t = 0; t < nt; ++t)
+        if (B->targets[bb.target0 + t].cell != t) return;
+    constexpr int kSelfCode = 1 | (1 << 2) | (1 << 4);
+    auto mirror = [](int code) {
+        int m = 0;
+        for (int d = 0; d < 3; ++d) m |= (2 - ((code >> (2 * d)) & 3)) << (2 * d);
+        return m;
+    };
+    std::vector<int32_t> aux(B->nbrs.size(), -1);
+    std::vector<int32_t> nfwd((size_t)nt, 0);
+    for (int64_t t = 0; t < nt; ++t) {
+        const BTargetDev &T = B->targets[bb.target0 + t];
+        std::vector<int32_t> seen;
+        for (int e = T.nb0; e < T.nb0 + T.nnb; ++e) {
+            const int nb = B->nbrs[e].cell;
+            for (int32_t q : seen)
+                if (q == nb) return;
+            seen.push_back(nb);
+            if (nb == t) {
+                if (B->nbrs[e].code != kSelfCode) return;
+            } else if (nb > t) {
+                aux[e] = nfwd[t]++;
+            }
+        }
+    }
+    for (int64_t t = 0; t < nt; ++t) {
+        const BTargetDev &T = B->targets[bb.target0 + t];
+        for (int e = T.nb0; e < T.nb0 + T.nnb; ++e) {
+            const int a = B->nbrs[e].cell;
+            if (a == t) continue;
+            // the entry a -> t with the opposite shift
+            const BTargetDev &TA = B->targets[bb.target0 + a];
+            int found = -1;
+            for (int q = TA.nb0; q < TA.nb0 + TA.nnb; ++q)
+                if (B->nbrs[q].cell == t && B->nbrs[q].code == mirror(B->nbrs[e].code)) found = q;
+            if (found < 0) return;
+            if (a < t) aux[e] = aux[found];
+        }
+    }
+    const int W = (int)((B->plan_max_cell + 31) / 32);
+    std::vector<int64_t> mb((size_t)nt + 1, 0);
+    for (int64_t t = 0; t < nt; ++t) {
+        const int64_t n = B->cells[bb.cell0 + t].n;
+        mb[t + 1] = mb[t] + ((n + 31) / 32) * nfwd[t] * W * 32;
+    }
+    for (int64_t t = 0; t < nt; ++t) B->targets[bb.target0 + t].pad = nfwd[t];
+    B->sym = true;
+    B->sym_words = W;
+    B->naux = std::move(aux);
+    B->mbase.assign(mb.begin(), mb.end() - 1);
+    B->mask_words = mb[nt];
 }
 
 // ---------------------------------------------------------------- tree plan

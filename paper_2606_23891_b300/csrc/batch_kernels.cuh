@@ -306,6 +306,11 @@ struct BInteractArgs {
     // in FP64 (three lanes), the box and half of it
     const double *xd[3];
     double box_d[3], half_d[3];
+    // the symmetric list build: per entry its forward ordinal (naux), per
+    // target its first mask word (mbase), mask words per entry and chunk
+    const int32_t *naux;
+    const long long *mbase;
+    int sym_words;
 };
 
 // a + b for two-float a and b (Knuth's TwoSum on the high parts); exact to

@@ -161,6 +161,21 @@ struct sph_batch_s {
     // extent plus the largest support stays below half the box
     bool fixed_build = false;
     int64_t plan_cells = 0, plan_max_cell = 0, plan_nbrs = 0;
+    // symmetric list build (one bundle, fixed-point path, every cell pair in
+    // both targets' entries): each cell pair is tested once, from the lower
+    // cell ("forward" entries), whose warps store their hit masks; the higher
+    // cell's lists get the pair by transposing them.  naux: per entry, the
+    // forward ordinal (forward entries) or the ordinal of this target among
+    // the other cell's forward entries (backward ones), -1 for self; mbase:
+    // per target, its first mask word; targets' pad field: forward entries.
+    bool sym = false;
+    bool sym_on = true;                 // sph_batch_list_symmetric
+    int sym_words = 0;                  // mask words per entry and chunk (32 candidates each)
+    int64_t mask_words = 0;             // mask region of the list buffer (0 when off)
+    std::vector<int32_t> naux;
+    std::vector<int64_t> mbase;
+    int32_t *d_naux = nullptr;
+    long long *d_mbase = nullptr;
     BCellDev *d_cells = nullptr;
     BTargetDev *d_targets = nullptr;
     BNbrDev *d_nbrs = nullptr;
@@ -170,6 +185,8 @@ struct sph_batch_s {
 
 namespace sph {
 int build_batch(const sph_tasks_s *T, const sph_batch_params *bp, sph_batch_s *B);
+// The symmetric list build's plan data (sym, naux, mbase, mask_words).
+void build_sym(sph_batch_s *B);
 int build_batch_tree(int64_t n, const double *x, const float *h, const sph_tree_params *tp,
                      const sph_batch_params *bp, int64_t *perm_out, sph_batch_s *B);
 int tree_plan_host(int64_t n, const double *x, const float *h, const sph_tree_params *tp,

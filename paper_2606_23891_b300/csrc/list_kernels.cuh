@@ -9,7 +9,8 @@
 //           cull by the warp box, prefilter on hi-only separations, take the
 //           exact decision of both loop criteria (r < H_i for density and
 //           gradient, r < max(H_i, H_j) for force) and append each accepted
-//           j's bundle slot to the lane's list, bit 31 set when r < H_i.  Lists are stored in chunks of 64 entries per lane for
+//           j's bundle slot to the lane's list (the force loop's pairs; the
+//           density and gradient loops keep those with r < H_i).  Lists are stored in chunks of 64 entries per lane for
 //           the 32 lanes of an item (lane-interleaved, so the loops read them
 //           coalesced); chunks come from a pool through an atomic counter
 //           and are chained per item.  The content and order of each list
@@ -48,33 +49,38 @@ struct ListView {
     ListHdr *hdr;
     uint32_t *first;    // per plan item: first chunk (kLNone: empty)
     uint32_t *lcount;   // per plan item and lane: list length
+    uint32_t *masks;    // symmetric build: hit masks of the forward cell pairs
     uint32_t *next;     // per chunk: next chunk of the same item
     uint32_t *entries;  // pool of chunks
     unsigned long long pool;
 };
 
-// Byte layout of a list buffer: header, first[NI], lcount[32 NI], next[pool],
+// Byte layout of a list buffer: header, first[NI], lcount[32 NI], masks[MW]
+// (MW words, the symmetric build's; 0 otherwise), next[pool],
 // entries[pool * kLChunk], each starting on a 256-byte boundary.
 struct ListLayout {
     static int64_t r256(int64_t b) { return (b + 255) / 256 * 256; }
-    static int64_t fixed(int64_t nitems) { return 256 + r256(4 * nitems) + r256(128 * nitems); }
-    static int64_t bytes(int64_t nitems, int64_t pool) {
-        return fixed(nitems) + r256(4 * pool) + r256(4 * pool * kLChunk);
+    static int64_t fixed(int64_t nitems, int64_t mwords) {
+        return 256 + r256(4 * nitems) + r256(128 * nitems) + r256(4 * mwords);
     }
-    static int64_t pool_for(int64_t nitems, int64_t bytes) {
-        int64_t p = (bytes - fixed(nitems)) / (4 + 4 * (int64_t)kLChunk);
-        while (p > 0 && ListLayout::bytes(nitems, p) > bytes) --p;
+    static int64_t bytes(int64_t nitems, int64_t mwords, int64_t pool) {
+        return fixed(nitems, mwords) + r256(4 * pool) + r256(4 * pool * kLChunk);
+    }
+    static int64_t pool_for(int64_t nitems, int64_t mwords, int64_t bytes) {
+        int64_t p = (bytes - fixed(nitems, mwords)) / (4 + 4 * (int64_t)kLChunk);
+        while (p > 0 && ListLayout::bytes(nitems, mwords, p) > bytes) --p;
         return p < 0 ? 0 : p;
     }
-    static ListView view(void *base, int64_t nitems, int64_t bytes) {
+    static ListView view(void *base, int64_t nitems, int64_t mwords, int64_t bytes) {
         ListView v{};
         char *b = (char *)base;
-        v.pool = (unsigned long long)pool_for(nitems, bytes);
+        v.pool = (unsigned long long)pool_for(nitems, mwords, bytes);
         v.hdr = (ListHdr *)b;
         v.first = (uint32_t *)(b + 256);
         v.lcount = (uint32_t *)(b + 256 + r256(4 * nitems));
-        v.next = (uint32_t *)(b + fixed(nitems));
-        v.entries = (uint32_t *)(b + fixed(nitems) + r256(4 * (int64_t)v.pool));
+        v.masks = (uint32_t *)(b + 256 + r256(4 * nitems) + r256(128 * nitems));
+        v.next = (uint32_t *)(b + fixed(nitems, mwords));
+        v.entries = (uint32_t *)(b + fixed(nitems, mwords) + r256(4 * (int64_t)v.pool));
         return v;
     }
 };
@@ -96,7 +102,12 @@ struct ListLayout {
 // prefiltered in pass 1), the pass-1 hits, the hits that take the exact
 // test, and the entries written (a measurement variant; the timed build has
 // COUNT = false and no counters).
-template <int T, bool FIXED, bool COUNT = false>
+// SYM (the symmetric build's first pass, one-bundle fixed-point grid plans):
+// only the self entry and the forward entries (cells after the target) are
+// tested; for each forward entry and tile the final hit masks are also
+// stored, one word per lane and 32 candidates, where the second pass
+// (k_blist_rev) of the other cell's items reads and transposes them.
+template <int T, bool FIXED, bool COUNT = false, bool SYM = false>
 __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView L, long long item0,
                                                        unsigned long long *cnt) {
     using BL = BLayout<SPH_DENSITY>;
@@ -169,6 +180,13 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
         for (int e = Tg.nb0; e < Tg.nb0 + Tg.nnb; ++e) {
             const BNbrDev E = a.nbrs[e];
             const int nb = E.cell;
+            uint32_t *mrow = nullptr;   // SYM, forward entry: this item's mask rows
+            if constexpr (SYM) {
+                if (nb < tcell) continue;   // the other cell's warps test this pair
+                if (nb > tcell)
+                    mrow = L.masks + a.mbase[tcell] +
+                           ((long long)(W.i0 >> 5) * Tg.pad + a.naux[e]) * a.sym_words * 32;
+            }
             const BCellDev Cn = a.cells[nb];
             const int code = E.code;
             float sh[3], sl[3];
@@ -256,12 +274,10 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
                         c_exact += __popc(FIXED ? hm[w] & ~sure[w] : hm[w]);
                     }
                 }
-                // FIXED: the exact decisions on the other hits (dm: r < H_i);
-                // hm keeps the accepted ones, in slot order
-                unsigned int dm[kWTile / 32];
+                // FIXED: the exact decisions on the other hits; hm keeps the
+                // accepted ones, in slot order
 #pragma unroll
                 for (int w = 0; w < kWTile / 32; ++w) {
-                    dm[w] = sure[w];
                     if constexpr (FIXED) {
                         unsigned int m = hm[w] & ~sure[w];
                         while (m) {
@@ -272,11 +288,14 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
                             const float dy = fixed_sep(o1.y, p1.y, a.fx_unit[1]);
                             const float dz = fixed_sep(o1.z, p1.z, a.fx_unit[2]);
                             const float r2 = dx * dx + dy * dy + dz * dz;
-                            if (r2 < H2i) dm[w] |= 1u << b;
-                            else if (!(r2 < fmaxf(H2i, p1.w))) hm[w] &= ~(1u << b);
+                            if (!(r2 < fmaxf(H2i, p1.w))) hm[w] &= ~(1u << b);
                         }
                     }
                     nh += __popc(hm[w]);
+                    if constexpr (SYM) {
+                        const int wj = (j0 >> 5) + w;
+                        if (mrow && wj * 32 < Cn.n) mrow[wj * 32 + lane] = hm[w];
+                    }
                 }
                 // room for up to nh more entries in every lane's chain; once
                 // an item is lost its further chunks are still counted, so the
@@ -312,7 +331,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
                             if (!lost) {
                                 const uint32_t js = (uint32_t)(Cn.slot + j0 + 32 * w + b);
                                 L.entries[checked(chain[count / kLPer], (long long)L.pool) * kLChunk +
-                                          (count % kLPer) * 32 + lane] = js | ((dm[w] >> b) & 1u) << 31;
+                                          (count % kLPer) * 32 + lane] = js;
                             }
                             ++count;
                         }
@@ -330,12 +349,11 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
                             const float dy = (o0.y - p0.y) + (o1.y - p1.y);
                             const float dz = (o0.z - p0.z) + (o1.z - p1.z);
                             const float r2 = dx * dx + dy * dy + dz * dz;
-                            const bool dens = r2 < H2i;
-                            if (!(dens || r2 < fmaxf(H2i, p1.w))) continue;
+                            if (!(r2 < fmaxf(H2i, p1.w))) continue;
                             if (!lost) {
                                 const uint32_t js = (uint32_t)(Cn.slot + j0 + j);
                                 L.entries[checked(chain[count / kLPer], (long long)L.pool) * kLChunk +
-                                          (count % kLPer) * 32 + lane] = js | (dens ? 0x80000000u : 0u);
+                                          (count % kLPer) * 32 + lane] = js;
                             }
                             ++count;
                         }
@@ -362,6 +380,141 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView
     }
 }
 
+// Transpose of a 32 x 32 bit matrix held one row per lane (bit c of lane r
+// is entry (r, c)): afterwards bit c of lane r is entry (c, r).  Five
+// butterfly stages, each swapping the off-diagonal blocks of half the size
+// between lane pairs.
+__device__ __forceinline__ unsigned int warp_transpose32(unsigned int x, int lane) {
+    const unsigned int mask[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int s = 0, j = 16; s < 5; ++s, j >>= 1) {
+        const unsigned int m = mask[s];
+        const unsigned int y = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y & m) << j));
+    }
+    return x;
+}
+
+// Second pass of the symmetric build: each item continues its lanes' lists
+// (left by k_blist<.., SYM>) with its backward entries, the cells A before its
+// target B.  A's warps stored, for each chunk of A and each chunk of B, the
+// hits of A's particles (one word per A lane, bit b for B's particle b);
+// transposed, lane b holds the A particles that hit its particle, appended
+// in slot order.  The pair decisions are the first pass's: the same
+// fixed-point words, the criterion r < max(H_i, H_j) is symmetric.
+template <int T, bool COUNT = false>
+__global__ void __launch_bounds__(T, 1024 / T) k_blist_rev(BInteractArgs a, ListView L,
+                                                           long long item0,
+                                                           unsigned long long *cnt) {
+    constexpr int kWarps = T / 32;
+    __shared__ uint32_t chainw[kWarps][kLMaxChain];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *chain = chainw[warp];
+    for (;;) {
+        int it = 0;
+        if (lane == 0) it = (int)atomicAdd(a.counter, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= a.nitems) break;
+        const long long gitem = item0 + it;
+        const BItemDev W = a.items[it];
+        const BTargetDev &Tg = a.targets[W.target];
+        const int tcell = Tg.cell;
+        const BCellDev C = a.cells[tcell];
+        const bool valid = W.i0 + lane < C.n;
+        const int cB = W.i0 >> 5;
+        int count = valid ? (int)L.lcount[gitem * 32 + lane] : 0;
+        // the item's chain so far
+        const int have = __reduce_max_sync(0xffffffffu, (unsigned)count);
+        int nch = (have + kLPer - 1) / kLPer;
+        bool lost = false;
+        uint32_t c = L.first[gitem];
+        if (nch > 0 && c == kLNone) lost = true;   // the first pass lost this item
+        for (int k = 0; k < nch && !lost; ++k) {
+            if (lane == 0) chain[k] = c;
+            if (k + 1 < nch) c = L.next[checked(c, (long long)L.pool)];
+        }
+        __syncwarp();
+        int added = 0;
+        // the (backward entry, chunk of A) pairs in entry order, their mask
+        // words loaded kRevBatch at a time so the loads are in flight together
+        constexpr int kRevBatch = 4;
+        const int eend = Tg.nb0 + Tg.nnb;
+        int e = Tg.nb0, cA = 0;
+        while (e < eend && a.nbrs[e].cell >= tcell) ++e;   // self and forward: the first pass's
+#pragma unroll 1
+        while (e < eend) {
+            unsigned int wd[kRevBatch];
+            int slot0[kRevBatch];
+            int nb = 0;
+#pragma unroll
+            for (int k = 0; k < kRevBatch; ++k) {
+                wd[k] = 0u;
+                slot0[k] = 0;
+                if (e < eend) {
+                    const int A = a.nbrs[e].cell;
+                    const BTargetDev &TA = a.targets[A];
+                    const BCellDev CA = a.cells[TA.cell];
+                    wd[k] = L.masks[a.mbase[A] +
+                                    (((long long)cA * TA.pad + a.naux[e]) * a.sym_words + cB) * 32 +
+                                    lane];
+                    slot0[k] = CA.slot + cA * 32;
+                    nb = k + 1;
+                    if (++cA * 32 >= CA.n) {
+                        cA = 0;
+                        ++e;
+                        while (e < eend && a.nbrs[e].cell >= tcell) ++e;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < kRevBatch; ++k) {
+                if (k >= nb) break;
+                unsigned int x = warp_transpose32(wd[k], lane);
+                if (!valid) x = 0u;
+                const int nh = __popc(x);
+                const int need = __reduce_max_sync(0xffffffffu, count + nh);
+                while (need > nch * kLPer) {
+                    uint32_t cc = kLNone;
+                    if (lane == 0) {
+                        const unsigned long long u = atomicAdd(&L.hdr->chunks_used, 1ull);
+                        if (!lost && u < L.pool && nch < kLMaxChain) {
+                            cc = (uint32_t)u;
+                            chain[nch] = cc;
+                            L.next[cc] = kLNone;
+                            if (nch > 0) L.next[chain[nch - 1]] = cc;
+                        } else if (!lost) {
+                            atomicMax(&L.hdr->overflow, nch < kLMaxChain ? 1u : 2u);
+                            atomicOr(&g_error_word, 4u);
+                        }
+                    }
+                    cc = __shfl_sync(0xffffffffu, cc, 0);
+                    __syncwarp();
+                    if (cc == kLNone) lost = true;
+                    ++nch;
+                }
+                while (x) {
+                    const int l = __ffs(x) - 1;
+                    x &= x - 1;
+                    if (!lost) {
+                        const uint32_t js = (uint32_t)(slot0[k] + l);
+                        L.entries[checked(chain[count / kLPer], (long long)L.pool) * kLChunk +
+                                  (count % kLPer) * 32 + lane] = js;
+                    }
+                    ++count;
+                    ++added;
+                }
+            }
+        }
+        L.lcount[gitem * 32 + lane] = valid && !lost ? (uint32_t)count : 0u;
+        if (lane == 0) L.first[gitem] = nch > 0 && !lost ? chain[0] : kLNone;
+        if constexpr (COUNT) {
+            const unsigned int ce = __reduce_add_sync(0xffffffffu, valid ? (unsigned)added : 0u);
+            if (lane == 0) atomicAdd(&cnt[4], (unsigned long long)ce);
+        }
+        __syncwarp();
+    }
+}
+
 // ---------------------------------------------------------------- loops --
 // Pair bodies of the gradient and force loops on compact records (the same
 // sums as Acc<LOOP>, with c = sqrt(gamma (gamma - 1) u) and P = (gamma - 1)
@@ -371,11 +524,12 @@ struct AccL : Acc<LOOP> {};
 
 template <>
 struct AccL<SPH_GRADIENT> {
-    float vsig, slap, ci, ui, Hinv, gg;
+    float vsig, slap, ci, ui, Hinv, gg, H2;
     __device__ __forceinline__ void init(const float4 *own, float, const PhysArgs &pa) {
         vsig = 0.f;
         slap = 0.f;
         Hinv = 1.f / own[0].w;
+        H2 = own[0].w * own[0].w;
         gg = pa.gamma * (pa.gamma - 1.f);
         ui = own[2].w;
         ci = sqrtf(gg * ui);
@@ -394,7 +548,9 @@ struct AccL<SPH_GRADIENT> {
         const float wdot = ((own[2].x - oth[2].x) * dx + (own[2].y - oth[2].y) * dy +
                             (own[2].z - oth[2].z) * dz) * rinv;
         const float vs = ci + sqrtf(gg * oth[2].w) - a.beta * fminf(0.f, wdot);
-        vsig = fmaxf(vsig, vs);
+        // the lists hold the force loop's pairs: the signal velocity takes
+        // those inside H_i (the Laplacian's terms vanish beyond, dw(1) = 0)
+        vsig = r2 < H2 ? fmaxf(vsig, vs) : vsig;
         slap = fmaf(oth[1].w * (ui - oth[2].w), dw * rinv, slap);
     }
     __device__ __forceinline__ void write(const PhysArgs &a, long long s, const float4 *) const {
@@ -559,12 +715,10 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
             if (kl % kLPer == 0 && kl < maxc) chunk = L.next[chunk];
             return e;
         };
-        auto uses = [&](uint32_t e, int k) {
-            return k < cnt && (LOOP == SPH_FORCE || (e & 0x80000000u) != 0u);
-        };
+        auto uses = [&](uint32_t, int k) { return k < cnt; };
         auto gather = [&](float4 *o, uint32_t e) {
 #pragma unroll
-            for (int f = 0; f < nf; ++f) o[f] = __ldg(&rec[f][checked(e & 0x7fffffffu, a.S)]);
+            for (int f = 0; f < nf; ++f) o[f] = __ldg(&rec[f][checked(e, a.S)]);
         };
         auto pair = [&](float4 *oth, long long js) {
             if constexpr (SEP64) {
@@ -601,7 +755,7 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
             float4 nxt[nf];
             bool un = uses(e, 0);
             if (un) gather(nxt, e);
-            long long jn = e & 0x7fffffffu;
+            long long jn = e;
             e = next_ent();
 #pragma unroll 1
             for (int k = 0; k < maxc; ++k) {
@@ -612,21 +766,24 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
                 const long long jc = jn;
                 un = uses(e, k + 1);
                 if (un) gather(nxt, e);
-                jn = e & 0x7fffffffu;
+                jn = e;
                 e = next_ent();
                 if (u) pair(oth, checked(jc, a.S));
             }
         } else {
             // density and gradient: two gathered lanes per pair; the
             // separation from the fixed-point positions (minimum image by the
-            // integer wrap-around)
+            // integer wrap-around).  The lists hold the force loop's pairs
+            // (r < max(H_i, H_j)); a pair beyond H_i adds nothing to these
+            // sums (q is clamped to 1, where w and dw vanish) and the
+            // gradient's signal velocity takes only those inside H_i.
             uint32_t e = next_ent();
 #pragma unroll 1
             for (int k = 0; k < maxc; ++k) {
                 const uint32_t cur = e;
                 e = next_ent();
                 if (!uses(cur, k)) continue;
-                const long long js = checked(cur & 0x7fffffffu, a.S);
+                const long long js = checked(cur, a.S);
                 const float4 j0 = (SEP64 && LOOP == SPH_DENSITY) ? make_float4(0.f, 0.f, 0.f, 0.f)
                                                                  : __ldg(&g0[js]);
                 const float4 j1 = __ldg(&g1[js]);

@@ -145,6 +145,7 @@ def lib() -> C.CDLL:
         "sph_batch_list_fixed": (i, [p]),
         "sph_batch_list_status": (i, [p, p, p]),
         "sph_batch_list_count": (i, [p, p, i, p, p, sz, p, p, p]),
+        "sph_batch_list_symmetric": (i, [p, i]),
         "sph_batch_offload_loop_list": (i, [p, p, i, p, p, p, sz, p, p]),
         "sph_batch_offload_step_list": (i, [p, p, p, p, p, sz, p, p]),
         "sph_batch_list_interact": (i, [p, i, i, p, p, p, sz, p, p]),
@@ -528,6 +529,15 @@ def sph_batch_list_status(dev_list: int):
     need, ovf = C.c_int64(), C.c_int()
     _ok(lib().sph_batch_list_status(dev_list, C.byref(need), C.byref(ovf)))
     return need.value, ovf.value
+
+
+def sph_batch_list_symmetric(b, enable: int = -1) -> bool:
+    """Turn the symmetric list build on (1) / off (0) or ask (-1); returns
+    whether later builds of the plan use it."""
+    r = lib().sph_batch_list_symmetric(b, enable)
+    if r < 0:
+        _ok(-r)
+    return r == 1
 
 
 def sph_batch_list_count(s, b, bundle: int, dev_in: int, dev_list: int, list_bytes: int,

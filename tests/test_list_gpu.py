@@ -395,3 +395,79 @@ def test_fp64_separation_step_matches_the_oracle(case):
                                             off.bbuf_out.data_ptr(), off.blist.data_ptr(),
                                             off.blist_bytes, off.x64.data_ptr(), 256,
                                             off.params, off.stream)
+
+
+def read_lists(off):
+    """The lists of a list buffer: {(item, lane): sorted bundle slots}."""
+    b = off.bplan
+    NI = off.binfo["items"]
+    fixed = sph.sph_batch_list_bytes(b, 0)
+    lo, hi = 0, 1
+    while sph.sph_batch_list_bytes(b, hi) <= off.blist_bytes:
+        hi *= 2
+    while hi - lo > 1:                      # the pool: the most chunks that fit
+        mid = (lo + hi) // 2
+        if sph.sph_batch_list_bytes(b, mid) <= off.blist_bytes:
+            lo = mid
+        else:
+            hi = mid
+    pool = lo
+    r256 = lambda x: (x + 255) // 256 * 256
+    torch.cuda.synchronize()
+    buf = off.blist.cpu().numpy()
+    u32 = lambda off_b, n: buf[off_b:off_b + 4 * n].view(np.uint32)
+    first = u32(256, NI)
+    lcount = u32(256 + r256(4 * NI), 32 * NI).reshape(NI, 32)
+    nxt = u32(fixed, pool)
+    ents = u32(fixed + r256(4 * pool), pool * 2048)
+    out = {}
+    for it in range(NI):
+        chain, c = [], int(first[it])
+        for _ in range((int(lcount[it].max()) + 63) // 64):
+            chain.append(c)
+            c = int(nxt[c])
+        for lane in range(32):
+            n = int(lcount[it, lane])
+            if n:
+                out[(it, lane)] = sorted(int(ents[chain[k // 64] * 2048 + (k % 64) * 32 + lane])
+                                         for k in range(n))
+    return out
+
+
+@pytest.mark.parametrize("case", ["ragged24", "gresho32"])
+def test_symmetric_list_build_holds_the_same_pairs(case):
+    """Testing each cell pair once (a first pass over the forward cells with
+    stored hit masks, a second pass transposing them) gives every particle
+    the same pairs as testing all neighbour cells per item."""
+    f = ragged(24, 8) if case == "ragged24" else PARITY_CASES[case]()
+    off = Offload(f, layout="pack_force_type")
+    off.batch()
+    assert sph.sph_batch_list_symmetric(off.bplan)
+    off.list_step()
+    sym = read_lists(off)
+    got_sym = off.export()
+    check_physics(f, got_sym)
+    assert not sph.sph_batch_list_symmetric(off.bplan, 0)
+    off.list_step()
+    one = read_lists(off)
+    got_one = off.export()
+    assert sym.keys() == one.keys() and len(sym) > 0
+    for key in one:
+        assert sym[key] == one[key], key
+    for k in got_one:       # the same pairs summed in another order (the bar of
+        # the other order-changing comparisons: 1e-5 of rms, for the cancelling sums)
+        assert rms_err(got_sym[k], got_one[k]) <= 1e-5, k
+    # the counting variant counts the same entries either way
+    cnt = {}
+    for on in (1, 0):
+        sph.sph_batch_list_symmetric(off.bplan, on)
+        c = torch.zeros(5, dtype=torch.int64, device="cuda")
+        sph.sph_batch_pack_list(off.store, off.bplan, 0, 0, off.bbuf_in.data_ptr(), off.params,
+                                off.stream)
+        sph.sph_batch_list_count(off.store, off.bplan, 0, off.bbuf_in.data_ptr(),
+                                 off.blist.data_ptr(), off.blist_bytes, off.params, c.data_ptr(),
+                                 off.stream)
+        sph.sph_sync(off.stream)
+        cnt[on] = c.cpu().tolist()
+    assert cnt[1][4] == cnt[0][4] == sum(len(v) for v in one.values())
+    assert cnt[1][1] < 0.7 * cnt[0][1]      # roughly half the prefiltered pairs
