@@ -74,7 +74,7 @@ NCU_TRAFFIC = {
                              "file": "physics_kernels.cuh"},
     # the symmetric list build's two passes together (128^3 capture:
     # 1130.9 MB + 808.1 MB DRAM over 2,097,152 particles)
-    ("list", "list", 0): {"bytes_per_unit": 924.6, "src": "bbb9590e483a22ca",
+    ("list", "list", 0): {"bytes_per_unit": 924.6, "src": "3692fe39dc20eab9",
                           "file": "list_kernels.cuh"},
 }
 # bytes per particle of the batched pack records (nf float4 + index lanes)

@@ -524,12 +524,11 @@ struct AccL : Acc<LOOP> {};
 
 template <>
 struct AccL<SPH_GRADIENT> {
-    float vsig, slap, ci, ui, Hinv, gg, H2;
+    float vsig, slap, ci, ui, Hinv, gg;
     __device__ __forceinline__ void init(const float4 *own, float, const PhysArgs &pa) {
         vsig = 0.f;
         slap = 0.f;
         Hinv = 1.f / own[0].w;
-        H2 = own[0].w * own[0].w;
         gg = pa.gamma * (pa.gamma - 1.f);
         ui = own[2].w;
         ci = sqrtf(gg * ui);
@@ -542,7 +541,8 @@ struct AccL<SPH_GRADIENT> {
         // to just past q = 1; on fixed-point plans the prefilter settles hits
         // on item-relative floats (inside H_i by a margin), and r * (1/H)
         // rounds again here, so the clamp stays as a guard
-        const float q = fminf(r2 * rinv * Hinv, 1.f);
+        const float qr = r2 * rinv * Hinv;
+        const float q = fminf(qr, 1.f);
         float w, dw;
         spline(q, w, dw);
         const float wdot = ((own[2].x - oth[2].x) * dx + (own[2].y - oth[2].y) * dy +
@@ -550,7 +550,7 @@ struct AccL<SPH_GRADIENT> {
         const float vs = ci + sqrtf(gg * oth[2].w) - a.beta * fminf(0.f, wdot);
         // the lists hold the force loop's pairs: the signal velocity takes
         // those inside H_i (the Laplacian's terms vanish beyond, dw(1) = 0)
-        vsig = r2 < H2 ? fmaxf(vsig, vs) : vsig;
+        vsig = qr < 1.f ? fmaxf(vsig, vs) : vsig;
         slap = fmaf(oth[1].w * (ui - oth[2].w), dw * rinv, slap);
     }
     __device__ __forceinline__ void write(const PhysArgs &a, long long s, const float4 *) const {
