@@ -1350,8 +1350,12 @@ static int check_batch(sph_batch b, int bundle) {
 static void batch_free(sph_batch b) {
     if (b->d_naux) cudaFree(b->d_naux);
     if (b->d_mbase) cudaFree(b->d_mbase);
+    if (b->d_rev) cudaFree(b->d_rev);
+    if (b->d_rev_start) cudaFree(b->d_rev_start);
     b->d_naux = nullptr;
     b->d_mbase = nullptr;
+    b->d_rev = nullptr;
+    b->d_rev_start = nullptr;
     if (b->d_cells) cudaFree(b->d_cells);
     if (b->d_targets) cudaFree(b->d_targets);
     if (b->d_items) cudaFree(b->d_items);
@@ -1383,7 +1387,12 @@ static int batch_upload(sph_batch b, int rc, sph_batch *out) {
          (b->sym && ((rc = up((void **)&b->d_naux, b->naux.data(),
                               b->naux.size() * sizeof(int32_t), "symmetric list entries")) ||
                      (rc = up((void **)&b->d_mbase, b->mbase.data(),
-                              b->mbase.size() * sizeof(long long), "symmetric list masks")))))) {
+                              b->mbase.size() * sizeof(long long), "symmetric list masks")) ||
+                     (rc = up((void **)&b->d_rev, b->rev.data(),
+                              b->rev.size() * sizeof(RevEntDev), "symmetric list neighbours")) ||
+                     (rc = up((void **)&b->d_rev_start, b->rev_start.data(),
+                              b->rev_start.size() * sizeof(int32_t),
+                              "symmetric list neighbour starts")))))) {
     }
     if (rc) {
         batch_free(b);
@@ -1579,6 +1588,8 @@ static BInteractArgs interact_args(sph_batch b, int bundle, const void *dev_buf_
     BInteractArgs a{};
     a.naux = b->d_naux;
     a.mbase = b->d_mbase;
+    a.rev = b->d_rev;
+    a.rev_start = b->d_rev_start;
     a.sym_words = b->sym_words;
     a.cells = b->d_cells + bb.cell0;
     a.targets = b->d_targets + bb.target0;

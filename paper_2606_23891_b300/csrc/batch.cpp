@@ -217,6 +217,8 @@ void build_sym(sph_batch_s *B) {
     B->mask_words = 0;
     B->naux.clear();
     B->mbase.clear();
+    B->rev.clear();
+    B->rev_start.clear();
     if (B->kind != 0 || !B->fixed_build || B->bundles.size() != 1) return;
     const BatchBundle &bb = B->bundles[0];
     const int64_t nt = bb.ntargets;
@@ -267,10 +269,30 @@ void build_sym(sph_batch_s *B) {
         mb[t + 1] = mb[t] + ((n + 31) / 32) * nfwd[t] * W * 32;
     }
     for (int64_t t = 0; t < nt; ++t) B->targets[bb.target0 + t].pad = nfwd[t];
+    // the backward neighbours of every target, as the second pass reads them
+    std::vector<RevEntDev> rev;
+    std::vector<int32_t> rstart((size_t)nt + 1, 0);
+    for (int64_t t = 0; t < nt; ++t) {
+        const BTargetDev &T = B->targets[bb.target0 + t];
+        for (int e = T.nb0; e < T.nb0 + T.nnb; ++e) {
+            const int a = B->nbrs[e].cell;
+            if (a >= t) continue;
+            const BCellDev &CA = B->cells[bb.cell0 + a];
+            RevEntDev r{};
+            r.mrow = mb[a] + (int64_t)aux[e] * W * 32;
+            r.stride = nfwd[a] * W * 32;
+            r.slot = CA.slot;
+            r.n = CA.n;
+            rev.push_back(r);
+        }
+        rstart[t + 1] = (int32_t)rev.size();
+    }
     B->sym = true;
     B->sym_words = W;
     B->naux = std::move(aux);
     B->mbase.assign(mb.begin(), mb.end() - 1);
+    B->rev = std::move(rev);
+    B->rev_start = std::move(rstart);
     B->mask_words = mb[nt];
 }
 

@@ -310,6 +310,8 @@ struct BInteractArgs {
     // target its first mask word (mbase), mask words per entry and chunk
     const int32_t *naux;
     const long long *mbase;
+    const RevEntDev *rev;      // per target, its backward neighbours (second pass)
+    const int32_t *rev_start;
     int sym_words;
 };
 

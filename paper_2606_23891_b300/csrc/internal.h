@@ -140,6 +140,14 @@ struct BNbrDev {
 struct BItemDev {
     int32_t target, i0;
 };
+// A backward neighbour of a target in the symmetric list build: where the
+// masks of the (neighbour, target) pair start (the target's first chunk
+// word), the stride between the neighbour's 32-particle chunks, and the
+// neighbour's first slot and particle count.
+struct RevEntDev {
+    long long mrow;
+    int32_t stride, slot, n, pad;
+};
 struct BatchBundle {
     int64_t cell0 = 0, ncells = 0, slots = 0;
     int64_t target0 = 0, ntargets = 0;
@@ -174,8 +182,12 @@ struct sph_batch_s {
     int64_t mask_words = 0;             // mask region of the list buffer (0 when off)
     std::vector<int32_t> naux;
     std::vector<int64_t> mbase;
+    std::vector<RevEntDev> rev;         // per target, its backward neighbours in entry order
+    std::vector<int32_t> rev_start;     // per target (+1): its first entry of rev
     int32_t *d_naux = nullptr;
     long long *d_mbase = nullptr;
+    RevEntDev *d_rev = nullptr;
+    int32_t *d_rev_start = nullptr;
     BCellDev *d_cells = nullptr;
     BTargetDev *d_targets = nullptr;
     BNbrDev *d_nbrs = nullptr;

@@ -435,14 +435,15 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist_rev(BInteractArgs a, List
         }
         __syncwarp();
         int added = 0;
-        // the (backward entry, chunk of A) pairs in entry order, their mask
-        // words loaded kRevBatch at a time so the loads are in flight together
+        // the (backward neighbour, chunk of it) pairs in entry order, their
+        // mask words loaded kRevBatch at a time so the loads are in flight together
         constexpr int kRevBatch = 4;
-        const int eend = Tg.nb0 + Tg.nnb;
-        int e = Tg.nb0, cA = 0;
-        while (e < eend && a.nbrs[e].cell >= tcell) ++e;   // self and forward: the first pass's
+        const int rend = a.rev_start[W.target + 1];
+        int r = a.rev_start[W.target], cA = 0;
+        RevEntDev R{};
+        if (r < rend) R = a.rev[r];
 #pragma unroll 1
-        while (e < eend) {
+        while (r < rend) {
             unsigned int wd[kRevBatch];
             int slot0[kRevBatch];
             int nb = 0;
@@ -450,19 +451,13 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist_rev(BInteractArgs a, List
             for (int k = 0; k < kRevBatch; ++k) {
                 wd[k] = 0u;
                 slot0[k] = 0;
-                if (e < eend) {
-                    const int A = a.nbrs[e].cell;
-                    const BTargetDev &TA = a.targets[A];
-                    const BCellDev CA = a.cells[TA.cell];
-                    wd[k] = L.masks[a.mbase[A] +
-                                    (((long long)cA * TA.pad + a.naux[e]) * a.sym_words + cB) * 32 +
-                                    lane];
-                    slot0[k] = CA.slot + cA * 32;
+                if (r < rend) {
+                    wd[k] = L.masks[R.mrow + (long long)cA * R.stride + cB * 32 + lane];
+                    slot0[k] = R.slot + cA * 32;
                     nb = k + 1;
-                    if (++cA * 32 >= CA.n) {
+                    if (++cA * 32 >= R.n) {
                         cA = 0;
-                        ++e;
-                        while (e < eend && a.nbrs[e].cell >= tcell) ++e;
+                        if (++r < rend) R = a.rev[r];
                     }
                 }
             }
