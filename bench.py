@@ -286,7 +286,7 @@ def measure_peaks(index: int, target_ms: float = 150.0) -> dict:
             best = max(best, fl[0] / (ms * 1e-3) / 1e12)
         out[name] = best
     out["clocks"] = clocks.stop()
-    out["how"] = ("sph_peak_run: 4 x 256 threads per SM, 8 independent chains of FMA "
+    out["how"] = ("sph_peak_run: 8 x 256 threads per SM, 8 independent chains of FMA "
                   "(2 flops) or add; best of 3 launches of ~%d ms, CUDA events" % target_ms)
     return out
 

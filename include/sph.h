@@ -695,7 +695,7 @@ int sph_offload_loop_noalloc(sph_store s, sph_tasks t, int loop, const sph_param
  * The paper has no counterpart to this call: it measures the arithmetic
  * peaks that the interaction loops' roofline is stated against (they run on
  * the FP32 CUDA cores; an FP64 separation would use the FP64 pipe).  One
- * launch of 4 CTAs of 256 threads per SM, each thread running 8 independent
+ * launch of 8 CTAs of 256 threads per SM, each thread running 8 independent
  * chains of `iters` x 16 operations: kind 0 FP32 fused multiply-add (2 flops
  * each), 1 FP64 fused multiply-add (2 flops), 2 FP64 add (1 flop).
  * *flops_out gets the launch's flop count; the caller times the launch on

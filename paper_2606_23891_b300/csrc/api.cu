@@ -252,12 +252,20 @@ int dispatch_bloop_w(int threads, const BInteractArgs &a, const ListView &L, lon
 }
 
 // The list loops' residency by plan kind (grid: 28 warps per SM, tree: 48).
+// The force loop on grid plans runs one CTA per SM over chunks of
+// consecutive items (k_bloop's CH mode): 6.35 against 6.57 ms at Gresho256.
+// The same mode made the density and gradient loops slower (4.69 / 4.58
+// against 3.99 / 3.79 ms), so they keep the launch-wide item queue.
 template <int LOOP>
 int dispatch_bloop(sph_batch b, const BInteractArgs &a, const ListView &L, long long item0,
                    cudaStream_t st) {
     if constexpr (LOOP != SPH_FORCE)
         if (b->kind == 1)
             return dispatch_bloop_w<LOOP, kLLoopWarpsTree>(b->threads, a, L, item0, st);
+    if constexpr (LOOP == SPH_FORCE)
+        if (b->kind == 0)
+            return launch_persistent(k_bloop<LOOP, 32 * kLLoopWarpsGrid, kLLoopWarpsGrid, false, true>,
+                                     32 * kLLoopWarpsGrid, a.nitems, st, "list loop", a, L, item0);
     return dispatch_bloop_w<LOOP, kLLoopWarpsGrid>(b->threads, a, L, item0, st);
 }
 
@@ -725,7 +733,7 @@ int sph_peak_run(int kind, int64_t iters, void *dev_sink, void *stream, double *
     if (int rc = cuda_check(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev),
                             "SM count"))
         return rc;
-    const int blocks = 4 * sms, threads = 256;
+    const int blocks = 8 * sms, threads = 256;   // 64 warps per SM
     cudaStream_t st = (cudaStream_t)stream;
     if (kind == 0)
         k_peak<float, 0><<<blocks, threads, 0, st>>>(iters, 1.0f, (float *)dev_sink);

@@ -626,7 +626,13 @@ __device__ __forceinline__ float sep64(double xi, double xj, double box, double 
     return (float)d;
 }
 
-template <int LOOP, int T, int WARPS, bool SEP64 = false>
+// CH: one CTA per SM, whose warps share the work items of the CTA's chunks
+// of kLoopChunk consecutive items (chunks dealt round-robin over the CTAs).
+// Consecutive items are the chunks of neighbouring cells, so the warps of
+// an SM gather overlapping neighbour records, which stay in its L1.
+// Otherwise every warp takes the next item of the whole launch.
+constexpr int kLoopChunk = 64;
+template <int LOOP, int T, int WARPS, bool SEP64 = false, bool CH = false>
 __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
     k_bloop(BInteractArgs a, ListView L, long long item0) {
     using BL = BLayout<LOOP>;
@@ -648,11 +654,26 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
                            ? reinterpret_cast<const float4 *>(a.in + BLayout<SPH_DENSITY>::fx(1, a.S))
                            : rec[1 % nf];
     const bool broken = L.hdr->overflow != 0u;
+    __shared__ unsigned int s_tick;
+    if constexpr (CH) {
+        if (threadIdx.x == 0) s_tick = 0u;
+        __syncthreads();
+    }
     for (;;) {
         int it = 0;
-        if (lane == 0) it = (int)atomicAdd(a.counter, 1u);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= a.nitems) break;
+        if constexpr (CH) {
+            unsigned int t = 0u;
+            if (lane == 0) t = atomicAdd(&s_tick, 1u);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            const long long item = ((long long)blockIdx.x + (long long)(t / kLoopChunk) * gridDim.x) *
+                                       kLoopChunk + t % kLoopChunk;
+            if (item >= a.nitems) break;
+            it = (int)item;
+        } else {
+            if (lane == 0) it = (int)atomicAdd(a.counter, 1u);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if (it >= a.nitems) break;
+        }
         const long long gitem = item0 + it;
         const BItemDev W = a.items[it];
         const BCellDev C = a.cells[a.targets[W.target].cell];

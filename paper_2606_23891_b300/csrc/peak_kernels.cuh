@@ -17,7 +17,7 @@ constexpr int kPeakUnroll = 16;
 
 // KIND 0: FP32 fma, 1: FP64 fma, 2: FP64 add.
 template <typename T, int KIND>
-__global__ void __launch_bounds__(256) k_peak(long long iters, T seed, T *sink) {
+__global__ void __launch_bounds__(256, 8) k_peak(long long iters, T seed, T *sink) {
     T a[kPeakChains];
 #pragma unroll
     for (int c = 0; c < kPeakChains; ++c) a[c] = seed + (T)(threadIdx.x + c);

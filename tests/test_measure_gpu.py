@@ -28,7 +28,7 @@ def test_peak_microbenchmark_counts_its_flops():
         e1.record()
         torch.cuda.synchronize()
         per_op = 1 if kind == sph.PEAK_FP64_ADD else 2
-        assert fl == 4 * sms * 256 * iters * 16 * 8 * per_op
+        assert fl == 8 * sms * 256 * iters * 16 * 8 * per_op
         rates[kind] = fl / (e0.elapsed_time(e1) * 1e-3)
     assert rates[sph.PEAK_FP32_FMA] > rates[sph.PEAK_FP64_FMA]
     sph.sph_sync(0)
