@@ -436,8 +436,10 @@ __global__ void __launch_bounds__(T, 1024 / T) k_blist_rev(BInteractArgs a, List
         __syncwarp();
         int added = 0;
         // the (backward neighbour, chunk of it) pairs in entry order, their
-        // mask words loaded kRevBatch at a time so the loads are in flight together
-        constexpr int kRevBatch = 4;
+        // mask words loaded kRevBatch at a time so the loads are in flight
+        // together (Gresho256 second pass: 1, 2, 3, 4, 6, 8 at a time gave
+        // 3.31, 3.33, 3.24, 3.56, 3.57, 3.85 ms)
+        constexpr int kRevBatch = 3;
         const int rend = a.rev_start[W.target + 1];
         int r = a.rev_start[W.target], cA = 0;
         RevEntDev R{};
