@@ -264,17 +264,18 @@ int dispatch_bloop(sph_batch b, const BInteractArgs &a, const ListView &L, long 
             return dispatch_bloop_w<LOOP, kLLoopWarpsTree>(b->threads, a, L, item0, st);
     if constexpr (LOOP == SPH_FORCE)
         if (b->kind == 0)
-            return launch_persistent(k_bloop<LOOP, 32 * kLLoopWarpsGrid, kLLoopWarpsGrid, false, true>,
-                                     32 * kLLoopWarpsGrid, a.nitems, st, "list loop", a, L, item0);
-    return dispatch_bloop_w<LOOP, kLLoopWarpsGrid>(b->threads, a, L, item0, st);
+            return launch_persistent(
+                k_bloop<LOOP, 32 * kLLoopWarpsForce, kLLoopWarpsForce, false, true>,
+                32 * kLLoopWarpsForce, a.nitems, st, "list loop", a, L, item0);
+    return dispatch_bloop_w<LOOP, kLLoopWarpsGrid<LOOP>>(b->threads, a, L, item0, st);
 }
 
-// The FP64-separation list loops of the precision study, at the grid
-// plan's residency.
+// The FP64-separation list loops of the precision study (more registers:
+// capped for 28 warps).
 template <int LOOP>
 int dispatch_bloop64(sph_batch b, const BInteractArgs &a, const ListView &L, long long item0,
                      cudaStream_t st) {
-    constexpr int W = kLLoopWarpsGrid;
+    constexpr int W = kLLoopWarpsForce;
     if (b->threads == 64)
         return launch_persistent(k_bloop<LOOP, 64, W, true>, 64, a.nitems, st, "list loop (FP64 "
                                  "separations)", a, L, item0);

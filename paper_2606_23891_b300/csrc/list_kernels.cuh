@@ -609,14 +609,20 @@ struct AccL<SPH_FORCE> {
     }
 };
 
-// Resident warps per SM the list loops are compiled for (WARPS), measured.  The
-// force loop runs at 28, with its j record prefetched at 72 registers.  The
-// density and gradient loops are bound by L1 on their gathers: on the
-// uniform Gresho set 28 warps thrash L1 less than 48 (6.25 / 5.81 against
-// 6.74 / 6.32 ms), while on the clustered lognormal set, whose lanes' list
-// lengths differ more, 48 warps hide more (step 133.5 against 135.7 ms).  So
-// grid plans use 28 and tree plans 48.
-constexpr int kLLoopWarpsGrid = 28, kLLoopWarpsTree = 48;
+// WARPS: the resident warps per SM a list loop's registers are capped for
+// (the launch fills each SM with as many CTAs as its registers allow).  The
+// force loop holds its j record one pair ahead at 72 registers: 28 warps.
+// The density and gradient loops wait on their gathers, so more resident
+// warps pay as long as nothing spills: at Gresho256 the density loop runs
+// 3.73 ms capped for 48 warps against 3.99 ms at its uncapped 48 registers
+// (40 warps), the gradient loop (its j lanes one pair ahead) 3.58 ms capped
+// for 40 against 3.66 ms at 56 registers and 3.67 ms capped for 48 (where
+// it spills).  Holding them to fewer warps than the registers allow (28 to
+// 36, by the grid size) was slower in every case.  Tree plans run both at
+// 48 (the clustered lognormal set's lanes differ more in list length).
+constexpr int kLLoopWarpsTree = 48, kLLoopWarpsForce = 28;
+template <int LOOP>
+constexpr int kLLoopWarpsGrid = LOOP == SPH_DENSITY ? 48 : LOOP == SPH_GRADIENT ? 40 : 28;
 // SEP64 (the precision study of FP64 separations): every pair separation is
 // the difference of the two FP64 positions (a.xd, gathered per slot by
 // k_pack_x64), its periodic image chosen in FP64, then rounded to FP32; the
@@ -795,11 +801,11 @@ __global__ void __launch_bounds__(T, (LOOP == SPH_FORCE ? 28 : WARPS) * 32 / T)
             // (r < max(H_i, H_j)); a pair beyond H_i adds nothing to these
             // sums (q is clamped to 1, where w and dw vanish) and the
             // gradient's signal velocity takes only those inside H_i.
-            // The gradient loop loads the two lanes of the next pair one pair
-            // ahead (its list entry two ahead): 3.66 against 3.79 ms at
-            // Gresho256.  The density loop lost that way (4.72 against 3.99 ms)
-            // and loads them when it uses them.
-            constexpr bool kAhead = LOOP == SPH_GRADIENT;
+            // The gradient loop on grid plans loads the two lanes of the next
+            // pair one pair ahead (its list entry two ahead): 3.66 against
+            // 3.79 ms at Gresho256.  The density loop lost that way (4.72
+            // against 3.99 ms) and loads them when it uses them.
+            constexpr bool kAhead = LOOP == SPH_GRADIENT && WARPS < 48;   // (spills at 48)
             auto gather2 = [&](uint32_t en, float4 &q0, float4 &q1) {
                 const long long jq = checked(en, a.S);
                 q0 = (SEP64 && LOOP == SPH_DENSITY) ? make_float4(0.f, 0.f, 0.f, 0.f)
