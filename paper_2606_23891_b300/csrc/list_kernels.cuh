@@ -107,8 +107,11 @@ struct ListLayout {
 // tested; for each forward entry and tile the final hit masks are also
 // stored, one word per lane and 32 candidates, where the second pass
 // (k_blist_rev) of the other cell's items reads and transposes them.
+// Registers are capped for 48 resident warps per SM (40 registers, 4 bytes
+// spilled): the symmetric first pass ran 7.09 ms at Gresho256, against 7.33
+// ms capped for 32 warps (58 registers) and 7.86 ms for 40 (48 registers).
 template <int T, bool FIXED, bool COUNT = false, bool SYM = false>
-__global__ void __launch_bounds__(T, 1024 / T) k_blist(BInteractArgs a, ListView L, long long item0,
+__global__ void __launch_bounds__(T, 1536 / T) k_blist(BInteractArgs a, ListView L, long long item0,
                                                        unsigned long long *cnt) {
     using BL = BLayout<SPH_DENSITY>;
     constexpr int kWarps = T / 32;
@@ -402,8 +405,11 @@ __device__ __forceinline__ unsigned int warp_transpose32(unsigned int x, int lan
 // transposed, lane b holds the A particles that hit its particle, appended
 // in slot order.  The pair decisions are the first pass's: the same
 // fixed-point words, the criterion r < max(H_i, H_j) is symmetric.
+// Registers capped for 56 resident warps per SM (32 registers, no spill):
+// the warps wait on their mask loads, and more of them hide it (Gresho256:
+// 2.85 ms, against 3.13 capped for 48 and 3.24 for 32).
 template <int T, bool COUNT = false>
-__global__ void __launch_bounds__(T, 1024 / T) k_blist_rev(BInteractArgs a, ListView L,
+__global__ void __launch_bounds__(T, 1792 / T) k_blist_rev(BInteractArgs a, ListView L,
                                                            long long item0,
                                                            unsigned long long *cnt) {
     constexpr int kWarps = T / 32;
