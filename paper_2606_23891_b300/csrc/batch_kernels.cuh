@@ -345,8 +345,11 @@ constexpr int kWTile = 64;  // j records a warp stages at a time (2 mask words)
 constexpr int kWPack = 128;
 constexpr int kWRows = kWPack / 32;
 
+// Registers capped for 12 CTAs per SM: at Gresho256 the density pack ran
+// 0.30 ms against 0.33 uncapped, and the gradient unpack with the force pack
+// 0.53 against 0.56 ms (capped for 16 CTAs: 0.30 and 0.64 ms).
 template <int LOOP, bool COMPACT = false>
-__global__ void __launch_bounds__(128) k_bpack_w(BPackArgs a) {
+__global__ void __launch_bounds__(128, 12) k_bpack_w(BPackArgs a) {
     using BL = BLayout<LOOP>;
     constexpr int nf = COMPACT ? NFC<LOOP>::value : BL::nf;
     __shared__ unsigned char inv_s[4][kWPack];
