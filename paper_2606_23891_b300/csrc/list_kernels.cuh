@@ -443,9 +443,9 @@ __global__ void __launch_bounds__(T, 1792 / T) k_blist_rev(BInteractArgs a, List
         int added = 0;
         // the (backward neighbour, chunk of it) pairs in entry order, their
         // mask words loaded kRevBatch at a time so the loads are in flight
-        // together (Gresho256 second pass: 1, 2, 3, 4, 6, 8 at a time gave
-        // 3.31, 3.33, 3.24, 3.56, 3.57, 3.85 ms)
-        constexpr int kRevBatch = 3;
+        // together (Gresho256 second pass, registers capped for 56 warps:
+        // 2, 3, 4, 6 at a time gave 2.77, 2.84, 2.85, 2.89 ms)
+        constexpr int kRevBatch = 2;
         const int rend = a.rev_start[W.target + 1];
         int r = a.rev_start[W.target], cA = 0;
         RevEntDev R{};
