@@ -73,8 +73,8 @@ NCU_TRAFFIC = {
     ("plain", "kernel", 2): {"bytes_per_unit": 92.1, "src": "e4b699e728bdf76e",
                              "file": "physics_kernels.cuh"},
     # the symmetric list build's two passes together (128^3 capture:
-    # 1198.0 MB + 831.9 MB DRAM over 2,097,152 particles)
-    ("list", "list", 0): {"bytes_per_unit": 967.9, "src": "6135c627c09fd15a",
+    # 1197.0 MB + 829.5 MB DRAM over 2,097,152 particles)
+    ("list", "list", 0): {"bytes_per_unit": 966.3, "src": "59da718261f29ae0",
                           "file": "list_kernels.cuh"},
 }
 # bytes per particle of the batched pack records (nf float4 + index lanes)
