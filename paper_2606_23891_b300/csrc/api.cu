@@ -251,7 +251,7 @@ int dispatch_bloop_w(int threads, const BInteractArgs &a, const ListView &L, lon
     return launch_persistent(k_bloop<LOOP, 128, W>, 128, a.nitems, st, "list loop", a, L, item0);
 }
 
-// The list loops' residency by plan kind (grid: 28 warps per SM, tree: 48).
+// The list loops' register caps by plan kind (kLLoopWarpsGrid / kLLoopWarpsTree).
 // The force loop on grid plans runs one CTA per SM over chunks of
 // consecutive items (k_bloop's CH mode): 6.35 against 6.57 ms at Gresho256.
 // The same mode made the density and gradient loops slower (4.69 / 4.58
