@@ -1699,7 +1699,13 @@ static int batch_unpack(sph_store s, sph_batch b, int loop, int bundle, const vo
     cudaStream_t st = (cudaStream_t)stream;
     const unsigned g = (unsigned)bb.ntargets;
     if (ghost) {
-        k_bunpack<SPH_DENSITY, true, true><<<g, 64, 0, st>>>(a);
+        // rho_dh .. rot_v as seven consecutive words of one record, and small
+        // enough cells: the form that writes them in store order
+        bool run7 = b->plan_max_cell <= kUnpC;
+        for (int j = 2; j < 8 && run7; ++j)
+            run7 = a.dst[j].stride == a.dst[1].stride && a.dst[j].ptr == a.dst[1].ptr + 4 * (j - 1);
+        if (run7) k_bunpack_dg<<<g, 64, 0, st>>>(a);
+        else k_bunpack<SPH_DENSITY, true, true><<<g, 64, 0, st>>>(a);
     } else if (write) {
         if (loop == SPH_DENSITY) k_bunpack<SPH_DENSITY, true><<<g, 64, 0, st>>>(a);
         else if (loop == SPH_GRADIENT) k_bunpack<SPH_GRADIENT, true><<<g, 64, 0, st>>>(a);

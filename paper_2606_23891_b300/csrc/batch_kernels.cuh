@@ -704,4 +704,49 @@ __global__ void __launch_bounds__(128) k_bunpack(BUnpackArgs a) {
     }
 }
 
+// The density unpack with the ghost when rho_dh, wcount, wcount_dh, div_v
+// and rot_v are seven consecutive 4-byte words of one record (dst[1..7]; the
+// by-type splits and the fused view) and no cell holds more than kUnpC
+// particles: those seven words of the cell's particles go through shared
+// memory in store order (a cell's particles are the store range
+// [p0, p0 + n), its slots a permutation of it) and are written word after
+// word, so a warp's stores cover whole sectors instead of one word in each
+// of 32 records; rho and the ghost's four outputs are written directly.
+// The values and bytes written are those of k_bunpack<density, write, ghost>.
+constexpr int kUnpC = 128;
+__global__ void __launch_bounds__(128) k_bunpack_dg(BUnpackArgs a) {
+    __shared__ float sres[7 * kUnpC];
+    const BCellDev C = a.cells[a.targets[blockIdx.x].cell];
+    if (C.n > kUnpC) return;   // the caller launches this form only below the limit
+    const long long r16 = (a.S * 16 + 255) / 256 * 256;
+    for (int k = threadIdx.x; k < C.n; k += blockDim.x) {
+        const long long sl = checked((long long)C.slot + k, a.S);
+        const long long p = a.perm[sl];
+        const float4 o0 = reinterpret_cast<const float4 *>(a.out)[sl];
+        const float4 o1 = reinterpret_cast<const float4 *>(a.out + r16)[sl];
+        float sums[8] = {0.f + o0.x, 0.f + o0.y, 0.f + o0.z, 0.f + o0.w,
+                         0.f + o1.x, 0.f + o1.y, 0.f + o1.z, 0.f + o1.w};
+        float g[11];
+        ghost_point(sums, ld<float>(a.gin[0], p), ld<float>(a.gin[1], p), ld<float>(a.gin[2], p),
+                    a.kernel_gamma, a.gamma, a.balsara_eps, g);
+        st<float>(a.dst[0], p, g[0]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) st<float>(a.gout[q], p, g[7 + q]);
+        // rho_dh, wcount, wcount_dh, div_v, rot_v: the words k_bunpack stores
+        const float w7[7] = {g[1], g[2], sums[3], g[3], g[4], g[5], g[6]};
+        const long long q = p - C.p0;
+        if (q >= 0 && q < C.n) {
+#pragma unroll
+            for (int j = 0; j < 7; ++j) sres[7 * q + j] = w7[j];
+        }
+    }
+    __syncthreads();
+    char *base = a.dst[1].ptr + a.dst[1].stride * (long long)C.p0;
+    const long long R = a.dst[1].stride;
+    for (int w = threadIdx.x; w < 7 * C.n; w += blockDim.x) {
+        const int q = w / 7, j = w - 7 * q;
+        *reinterpret_cast<float *>(base + R * q + 4 * j) = sres[w];
+    }
+}
+
 }  // namespace sph
